@@ -1,0 +1,204 @@
+"""O2: the gamma-EigenGame iteration, written the way the paper states it.
+
+Test infrastructure only (see the package header).
+
+* `eg_step` is one iteration of the stochastic algorithm (Alg. 2) with M = 1
+  machine: for every player i it forms y_j and [By]_j of its parents with the
+  clipped denominator max(<v_j, [Bv]_j>, rho), the reward and penalty terms of
+  Eq. (update) with the minibatch estimates A_t and B_t, the player step
+  v_i + eta_t grad_i followed by the retraction to the unit sphere, and the
+  auxiliary step [Bv]_i + gamma_t (B_t v_i - [Bv]_i). All players read the
+  state of step t (the parfor of Alg. 2), so V and [Bv] are updated together.
+* `alg1_step` is the deterministic variant (Alg. 1) with exact A and B.
+* `utility` is Eq. util_new; `schedule_eta` is the warm-up plus harmonic decay
+  of App. H.2.2.
+* The operators `*_ops` build the minibatch mat-vecs U -> A_t U and U -> B_t U
+  from data rows without forming A_t or B_t (Sec. 1: A and B are expectations
+  of outer products, applied through matrix-vector products). "Independent
+  data batches" for A_t and B_t (Alg. 2) are read as: the first floor(b/2)
+  rows estimate A, the other rows estimate B. With B = I (PCA, PLS) no split
+  is needed and A uses every row.
+
+Pins (tests/test_oracle_eg.py): the update vanishes at the exact solution with
+[Bv] = B v (Lemma "right fixed point", App. C); with exact parents and exact
+[Bv] it is the utility gradient of Lemma "Gradient" (App. B) up to the positive
+factor <v_i, B v_i>^2 / 2, checked against central finite differences of
+Eq. util_new; with B = I and [Bv] = v it equals the projected mu-EigenGame
+direction (Prop. "Equivalence to EigenGame Unloaded"); the streamed operators
+equal the explicit block matrices of Sec. 1; averaged over many independent
+minibatches the update equals the update with population A and B (unbiased
+estimates, Sec. 3); Alg. 1 and Alg. 2 with full-batch estimates converge to O1.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+# ---------------------------------------------------------------------------
+# Minibatch operators A_t, B_t (never formed)
+
+def cca_ops(X: np.ndarray, Y: np.ndarray, split: bool = True, eps_B: float = 0.0):
+    """CCA minibatch operators (Sec. 1, CCA block form), optional B + eps I (App. G)."""
+    X = np.asarray(X, dtype=np.float64)
+    Y = np.asarray(Y, dtype=np.float64)
+    b, dx = X.shape
+    nA = b // 2 if split else b
+    XA, YA = X[:nA], Y[:nA]
+    XB, YB = (X[nA:], Y[nA:]) if split else (X, Y)
+    nB = XB.shape[0]
+
+    def Amv(U):
+        U = np.asarray(U, dtype=np.float64)
+        ux, uy = U[:dx], U[dx:]
+        return np.concatenate([XA.T @ (YA @ uy), YA.T @ (XA @ ux)], axis=0) / nA
+
+    def Bmv(U):
+        U = np.asarray(U, dtype=np.float64)
+        ux, uy = U[:dx], U[dx:]
+        out = np.concatenate([XB.T @ (XB @ ux), YB.T @ (YB @ uy)], axis=0) / nB
+        return out + eps_B * U
+
+    return Amv, Bmv
+
+
+def pls_ops(X: np.ndarray, Y: np.ndarray, eps_B: float = 0.0):
+    """PLS: A as for CCA over every row, B = I."""
+    Amv, _ = cca_ops(X, Y, split=False)
+    return Amv, (lambda U: (1.0 + eps_B) * np.asarray(U, dtype=np.float64))
+
+
+def pca_ops(X: np.ndarray, eps_B: float = 0.0):
+    """PCA: A = X^T X / b over every row, B = I (Sec. 1)."""
+    X = np.asarray(X, dtype=np.float64)
+    b = X.shape[0]
+
+    def Amv(U):
+        return X.T @ (X @ np.asarray(U, dtype=np.float64)) / b
+
+    return Amv, (lambda U: (1.0 + eps_B) * np.asarray(U, dtype=np.float64))
+
+
+def matrix_ops(A: np.ndarray, B: np.ndarray):
+    """Exact operators from explicit matrices (full-batch setting)."""
+    return (lambda U: A @ U), (lambda U: B @ U)
+
+
+def lda_ops(X: np.ndarray, labels: np.ndarray, class_mean: np.ndarray,
+            class_prior: np.ndarray, split: bool = True, eps_B: float = 0.0):
+    """LDA operators given running class means mu_c and priors pi_c (reading, see `form_lda_AB`).
+
+    A U = sum_c pi_c (mu_c - mu)(mu_c - mu)^T U with mu = sum_c pi_c mu_c;
+    B U = (1/n_B) sum_r x~_r x~_r^T U with x~_r = x_r - mu_{label r} over the B rows.
+    """
+    X = np.asarray(X, dtype=np.float64)
+    b = X.shape[0]
+    nA = b // 2 if split else b
+    XB = X[nA:] if split else X
+    lB = labels[nA:] if split else labels
+    mu = class_prior @ class_mean
+    Mc = class_mean - mu[None, :]
+    Xt = XB - class_mean[lB]
+
+    def Amv(U):
+        U = np.asarray(U, dtype=np.float64)
+        return Mc.T @ (class_prior[:, None] * (Mc @ U))
+
+    def Bmv(U):
+        U = np.asarray(U, dtype=np.float64)
+        return Xt.T @ (Xt @ U) / Xt.shape[0] + eps_B * U
+
+    return Amv, Bmv
+
+
+# ---------------------------------------------------------------------------
+# Alg. 2 and Alg. 1
+
+def eg_step(V: np.ndarray, S: np.ndarray, Amv, Bmv, eta: float, gamma: float,
+            rho: float, return_parts: bool = False):
+    """One iteration of Alg. 2 (M = 1). V, S are d x k: columns v_i and [Bv]_i.
+
+    Returns (V_next, S_next) or, with return_parts, also a dict holding
+    AV = A_t V, BV = B_t V and the update directions grad (d x k).
+    """
+    V = np.asarray(V, dtype=np.float64)
+    S = np.asarray(S, dtype=np.float64)
+    d, k = V.shape
+    AV = Amv(V)          # A_t v_i for every player
+    BV = Bmv(V)          # B_t v_i for every player
+    grad = np.zeros_like(V)
+    for i in range(k):
+        vi = V[:, i]
+        Avi = AV[:, i]
+        Bvi = BV[:, i]
+        vBv = vi @ Bvi
+        vAv = vi @ Avi
+        rewards = vBv * Avi - vAv * Bvi
+        penalties = np.zeros(d)
+        for j in range(i):
+            denom = np.sqrt(max(V[:, j] @ S[:, j], rho))
+            yj = V[:, j] / denom
+            Byj = S[:, j] / denom
+            # v_i^T A_t y_j, using the symmetry of A_t: (A_t v_i)^T y_j
+            vAy = Avi @ yj
+            penalties += vAy * (vBv * Byj - (vi @ Byj) * Bvi)
+        grad[:, i] = rewards - penalties
+    Vp = V + eta * grad
+    V_next = Vp / np.linalg.norm(Vp, axis=0, keepdims=True)
+    S_next = S + gamma * (BV - S)
+    if return_parts:
+        return V_next, S_next, {"AV": AV, "BV": BV, "grad": grad}
+    return V_next, S_next
+
+
+def alg1_step(V: np.ndarray, A: np.ndarray, B: np.ndarray, eta: float) -> np.ndarray:
+    """One iteration of the deterministic algorithm (Alg. 1) with exact A and B."""
+    V = np.asarray(V, dtype=np.float64)
+    d, k = V.shape
+    AV = A @ V
+    BV = B @ V
+    grad = np.zeros_like(V)
+    for i in range(k):
+        vi = V[:, i]
+        rewards = (vi @ BV[:, i]) * AV[:, i] - (vi @ AV[:, i]) * BV[:, i]
+        penalties = np.zeros(d)
+        for j in range(i):
+            nj = np.sqrt(V[:, j] @ BV[:, j])
+            yj = V[:, j] / nj
+            Byj = BV[:, j] / nj
+            penalties += (AV[:, i] @ yj) * ((vi @ BV[:, i]) * Byj - (vi @ Byj) * BV[:, i])
+        grad[:, i] = rewards - penalties
+    Vp = V + eta * grad
+    return Vp / np.linalg.norm(Vp, axis=0, keepdims=True)
+
+
+def utility(V: np.ndarray, i: int, A: np.ndarray, B: np.ndarray) -> float:
+    """u_i(v_i | v_{j<i}) of Eq. util_new: generalized Rayleigh quotient minus penalties."""
+    vi = V[:, i]
+    vBv = vi @ B @ vi
+    u = (vi @ A @ vi) / vBv
+    for j in range(i):
+        vj = V[:, j]
+        vjBvj = vj @ B @ vj
+        u -= (vj @ A @ vj) * (vi @ B @ vj) ** 2 / (vjBvj ** 2 * vBv)
+    return float(u)
+
+
+# ---------------------------------------------------------------------------
+# Step sizes (App. H.2.2)
+
+def schedule_eta(t: int, eta0: float, schedule: int, t_c: int = 0, T: int = 1,
+                 eta_T: float = 0.0) -> float:
+    """Player step size eta_t for iteration t = 1, 2, ...
+
+    schedule 0: constant eta0.
+    schedule 1: eta0 up to t_c, then proportional to 1/(t + Delta), reaching eta_T at T.
+    schedule 2: linear warm-up eta0 t / t_c up to t_c, then the same harmonic decay
+                (the schedule of App. H.2.2).
+    Delta solves eta0 (t_c + Delta) / (T + Delta) = eta_T.
+    """
+    if schedule == 0:
+        return float(eta0)
+    delta = (eta_T * T - eta0 * t_c) / (eta0 - eta_T)
+    if t <= t_c:
+        return float(eta0 if schedule == 1 else eta0 * t / t_c)
+    return float(eta0 * (t_c + delta) / (t + delta))

@@ -1,0 +1,207 @@
+"""Planted data models for the symmetric generalized eigenproblem workloads.
+
+All randomness comes from numpy's Philox-4x32-10 counter-based generator
+(Salmon et al., SC'11), keyed by (seed, stream). A stream id separates the
+model parameters, the initial player vectors and each minibatch, so any
+minibatch can be regenerated on its own.
+
+Models (all zero-mean, matching the paper's zero-mean assumption, Sec. 1):
+
+* PlantedCCA: x = Q_x diag(s) z + sigma e_x, y = Q_y diag(s) z + sigma e_y with
+  z ~ N(0, I_r), Q_x, Q_y orthonormal columns (QR of a Gaussian matrix). With
+  s_l^2 = sigma^2 rho_l / (1 - rho_l) the canonical correlations are exactly
+  rho_l (used for the 4- and 16-player CCA workloads).
+* PlantedLowRankCCA: x = D_x^{1/2} g_x + W_x z, y = D_y^{1/2} g_y + W_y z with a
+  power-law diagonal D (D_ii proportional to i^-alpha) and m planted shared
+  directions (the activation-like workload, d_x = d_y = 16384).
+* PCA: x = Q diag(sqrt(spectrum)) z + sigma e.
+* LDA: C Gaussian classes with means mu_c and a shared within-class covariance.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+# Stream ids: the key of each Philox generator is (seed, stream).
+_STREAM_MODEL = 1
+_STREAM_INIT = 2
+_STREAM_FINITE = 3
+_STREAM_INDEX_BASE = 1 << 20
+_STREAM_ROWS_BASE = 1 << 40
+
+
+def _rng(seed: int, stream: int) -> np.random.Generator:
+    return np.random.Generator(np.random.Philox(key=np.array([seed, stream], dtype=np.uint64)))
+
+
+def _orthonormal(rng: np.random.Generator, d: int, r: int) -> np.ndarray:
+    q, rr = np.linalg.qr(rng.standard_normal((d, r)))
+    return q * np.sign(np.diag(rr))[None, :]
+
+
+@dataclass
+class PlantedCCA:
+    Qx: np.ndarray      # d_x x r, orthonormal columns
+    Qy: np.ndarray      # d_y x r, orthonormal columns
+    s: np.ndarray       # r latent scales
+    sigma: float        # isotropic noise level
+    rhos: np.ndarray    # the planted canonical correlations (input, for reference)
+    seed: int
+
+    @property
+    def d_x(self) -> int:
+        return self.Qx.shape[0]
+
+    @property
+    def d_y(self) -> int:
+        return self.Qy.shape[0]
+
+    @property
+    def Wx(self) -> np.ndarray:
+        return self.Qx * self.s[None, :]
+
+    @property
+    def Wy(self) -> np.ndarray:
+        return self.Qy * self.s[None, :]
+
+
+@dataclass
+class PlantedLowRankCCA:
+    Dx: np.ndarray      # d_x diagonal noise variances
+    Dy: np.ndarray
+    Wx: np.ndarray      # d_x x m
+    Wy: np.ndarray      # d_y x m
+    seed: int
+
+    @property
+    def d_x(self) -> int:
+        return self.Wx.shape[0]
+
+    @property
+    def d_y(self) -> int:
+        return self.Wy.shape[0]
+
+
+def planted_cca(d_x: int, d_y: int, rhos, sigma: float = 0.5, seed: int = 0) -> PlantedCCA:
+    rhos = np.asarray(rhos, dtype=np.float64)
+    rng = _rng(seed, _STREAM_MODEL)
+    r = rhos.size
+    Qx = _orthonormal(rng, d_x, r)
+    Qy = _orthonormal(rng, d_y, r)
+    s = np.sqrt(sigma * sigma * rhos / (1.0 - rhos))
+    return PlantedCCA(Qx, Qy, s, float(sigma), rhos, seed)
+
+
+def planted_lowrank_cca(d_x: int, d_y: int, m: int = 64, alpha: float = 1.0,
+                        target_rhos=None, seed: int = 0) -> PlantedLowRankCCA:
+    """Activation-like CCA model: power-law per-coordinate noise plus m shared directions.
+
+    D_ii = i^-alpha (i = 1..d). The shared directions are W = Q diag(w) with Q a
+    random orthonormal d x m matrix. For such Q, H = W^T D^-1 W is close to
+    diag(w^2) mean(1/D), and the canonical correlations are close to
+    h_l / (1 + h_l); w is set from `target_rhos` (default 0.95 down to 0.3)
+    through that approximation. The exact correlations follow from the model
+    and are computed by the oracle's closed form, not taken from here.
+    """
+    rng = _rng(seed, _STREAM_MODEL)
+    Dx = np.arange(1, d_x + 1, dtype=np.float64) ** (-alpha)
+    Dy = np.arange(1, d_y + 1, dtype=np.float64) ** (-alpha)
+    if target_rhos is None:
+        target_rhos = np.linspace(0.95, 0.3, m)
+    h = np.asarray(target_rhos, dtype=np.float64)
+    h = h / (1.0 - h)
+    wx = np.sqrt(h / np.mean(1.0 / Dx))
+    wy = np.sqrt(h / np.mean(1.0 / Dy))
+    Wx = _orthonormal(rng, d_x, m) * wx[None, :]
+    Wy = _orthonormal(rng, d_y, m) * wy[None, :]
+    return PlantedLowRankCCA(Dx, Dy, Wx, Wy, seed)
+
+
+def planted_pca(d: int, spectrum, sigma: float = 0.1, seed: int = 0):
+    rng = _rng(seed, _STREAM_MODEL)
+    spectrum = np.asarray(spectrum, dtype=np.float64)
+    Q = _orthonormal(rng, d, spectrum.size)
+    return {"Q": Q, "spectrum": spectrum, "sigma": float(sigma), "seed": seed}
+
+
+def planted_lda(d: int, n_classes: int = 10, sigma_b: float = 1.0, seed: int = 0):
+    """C Gaussian classes, equal priors, means N(0, sigma_b^2 I), shared covariance L L^T."""
+    rng = _rng(seed, _STREAM_MODEL)
+    means = sigma_b * rng.standard_normal((n_classes, d))
+    means -= means.mean(axis=0, keepdims=True)   # zero overall mean
+    scales = np.linspace(1.0, 0.5, d)
+    L = _orthonormal(rng, d, d) * scales[None, :]
+    return {"means": means, "L": L, "seed": seed}
+
+
+def draw_rows(model, n: int, batch: int, dtype=np.float64):
+    """Rows of minibatch number `batch` (n paired samples) from a CCA model."""
+    rng = _rng(model.seed, _STREAM_ROWS_BASE + batch)
+    if isinstance(model, PlantedCCA):
+        z = rng.standard_normal((n, model.s.size))
+        X = z @ model.Wx.T + model.sigma * rng.standard_normal((n, model.d_x))
+        Y = z @ model.Wy.T + model.sigma * rng.standard_normal((n, model.d_y))
+    else:
+        z = rng.standard_normal((n, model.Wx.shape[1]))
+        X = z @ model.Wx.T + rng.standard_normal((n, model.d_x)) * np.sqrt(model.Dx)[None, :]
+        Y = z @ model.Wy.T + rng.standard_normal((n, model.d_y)) * np.sqrt(model.Dy)[None, :]
+    return X.astype(dtype), Y.astype(dtype)
+
+
+def draw_pca_rows(model, n: int, batch: int, dtype=np.float64):
+    rng = _rng(model["seed"], _STREAM_ROWS_BASE + batch)
+    z = rng.standard_normal((n, model["spectrum"].size)) * np.sqrt(model["spectrum"])[None, :]
+    X = z @ model["Q"].T + model["sigma"] * rng.standard_normal((n, model["Q"].shape[0]))
+    return X.astype(dtype)
+
+
+def draw_lda_rows(model, n: int, batch: int, dtype=np.float64):
+    rng = _rng(model["seed"], _STREAM_ROWS_BASE + batch)
+    C, d = model["means"].shape
+    labels = rng.integers(0, C, size=n).astype(np.int32)
+    X = model["means"][labels] + rng.standard_normal((n, d)) @ model["L"].T
+    return X.astype(dtype), labels
+
+
+def random_unit_columns(d: int, k: int, seed: int = 0, dtype=np.float64) -> np.ndarray:
+    """Initial strategies: v_i ~ N(0, I_d) then scaled to unit norm (Alg. 2 init)."""
+    V = _rng(seed, _STREAM_INIT).standard_normal((d, k))
+    V /= np.sqrt(np.sum(V * V, axis=0, keepdims=True))
+    return V.astype(dtype)
+
+
+def finite_dataset_indices(n_total: int, b: int, step: int, seed: int = 0) -> np.ndarray:
+    """Indices of minibatch `step`, drawn with replacement from a finite dataset."""
+    return _rng(seed, _STREAM_INDEX_BASE + step).integers(0, n_total, size=b)
+
+
+# ---------------------------------------------------------------------------
+# The named workloads. Each returns a plain dict of shapes and hyperparameters
+# plus the planted model.
+
+def config_c1(seed: int = 0):
+    """Plain CCA, d_x = d_y = 32, k = 4, a finite set of 10,000 paired rows, b = 256."""
+    rhos = np.array([0.9, 0.8, 0.7, 0.6, 0.5, 0.4, 0.3, 0.2])
+    model = planted_cca(32, 32, rhos, sigma=0.5, seed=seed)
+    X, Y = draw_rows(model, 10_000, batch=_STREAM_FINITE)
+    return {"name": "cca_d64_k4_b256", "model": model, "X": X, "Y": Y, "k": 4, "b": 256,
+            "steps": 2000, "eta0": 0.2, "gamma0": 0.3, "rho": 1e-6,
+            "schedule": 1, "t_c": 100, "T": 2000, "eta_T": 0.2 * 120.0 / 2020.0}
+
+
+def config_c2(seed: int = 0):
+    """Plain CCA, d_x = d_y = 512, k = 16, b = 1024, latent dim 32, rho 0.95..0.3."""
+    rhos = np.linspace(0.95, 0.3, 32)
+    model = planted_cca(512, 512, rhos, sigma=0.5, seed=seed)
+    return {"name": "cca_d1024_k16_b1024", "model": model, "k": 16, "b": 1024,
+            "n_samples": 1_000_000, "eta0": 0.3, "gamma0": 0.3, "rho": 1e-6,
+            "schedule": 1, "t_c": 100, "T": 20000, "eta_T": 0.3 * 120.0 / 20020.0}
+
+
+def config_c3(seed: int = 0):
+    """Activation-like CCA, d_x = d_y = 16384, k = 32, b = 4096, 64 planted directions."""
+    model = planted_lowrank_cca(16384, 16384, m=64, alpha=1.0, seed=seed)
+    return {"name": "cca_d32768_k32_b4096", "model": model, "k": 32, "b": 4096,
+            "n_samples": 10_000_000, "eta0": 0.3, "gamma0": 0.3, "rho": 1e-6,
+            "schedule": 1, "t_c": 100, "T": 2442, "eta_T": 0.3 * 120.0 / 2462.0}
