@@ -1,0 +1,338 @@
+"""Benchmark of the gamma-EigenGame step (Alg. 2) on GB300.
+
+Default workload: plain CCA in FP32, d_x = d_y = 512 (d = 1024), k = 16 players,
+minibatch b = 1024, rows from the planted model with 32 latent directions
+(canonical correlations 0.95..0.3). A pool of 1,000,000 rows (4 GB) is generated on
+the device before timing; timed steps stream consecutive minibatches through it, so the
+inputs exceed L2 and every step reads fresh rows from HBM.
+
+One JSON line is printed (rank 0). `value` is samples/s of the whole job with inputs
+resident in HBM; `e2e` is the same metric through the C ABI with the minibatch copied
+from pinned host memory and V read back every step; `roofline` relates the step's
+algorithmic bytes to the measured HBM peak; `cpu_baseline` is the FP64 oracle timed on
+this host's cores on a bounded sample.
+
+  python bench.py [--gpus N --steps K --warmup W] [--workload NAME] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "samples/s and time-to-1e-3 gen.-subspace error: plain FP32 vs BF16/batched/warm"
+
+WORKLOADS = {
+    # name: (synth config function, dtype, pool rows)
+    "cca_d1024_k16_b1024_f32": ("config_c2", "f32", 1_000_000),
+    "cca_d64_k4_b256_f32": ("config_c1", "f32", 10_000),
+}
+DEFAULT_WORKLOAD = "cca_d1024_k16_b1024_f32"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    p.add_argument("--impl", default="native", choices=["native", "reference"])
+    p.add_argument("--path", type=int, default=0, help="0 auto, 1 generic, 2 cluster, 3 tc")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.f = None
+
+    def __enter__(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.f is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for ln in fh:
+                parts = [x.strip() for x in ln.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "", 1).isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "", 1).isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if r[5 + j].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# data
+
+def make_pool(cfg, rows, dtype, device, seed=0):
+    """Rows of the planted CCA model generated on the device (torch RNG)."""
+    import torch
+    model = cfg["model"]
+    g = torch.Generator(device=device)
+    g.manual_seed(1000 + seed)
+    Wx = torch.from_numpy(model.Wx).float().to(device)
+    Wy = torch.from_numpy(model.Wy).float().to(device)
+    r = Wx.shape[1]
+    X = torch.empty(rows, model.d_x, device=device)
+    Y = torch.empty(rows, model.d_y, device=device)
+    chunk = 1 << 17
+    for r0 in range(0, rows, chunk):
+        n = min(chunk, rows - r0)
+        z = torch.randn(n, r, device=device, generator=g)
+        X[r0:r0 + n] = z @ Wx.T + model.sigma * torch.randn(n, model.d_x, device=device, generator=g)
+        Y[r0:r0 + n] = z @ Wy.T + model.sigma * torch.randn(n, model.d_y, device=device, generator=g)
+    if dtype == "bf16":
+        X, Y = X.to(torch.bfloat16), Y.to(torch.bfloat16)
+    return X, Y
+
+
+# ---------------------------------------------------------------------------
+# reference arm / CPU baseline: the FP64 oracle on host cores
+
+def oracle_rate(cfg, seconds: float):
+    """Samples/s of the oracle's Alg. 2 step (FP64, numpy, streamed operators) on
+    minibatches of the workload, over about `seconds` of work."""
+    from oracle import eg
+    model = cfg["model"]
+    b, k = cfg["b"], cfg["k"]
+    d = model.d_x + model.d_y
+    V = synth.random_unit_columns(d, k, seed=0)
+    S = V.copy()
+    batches = [synth.draw_rows(model, b, batch=i) for i in range(4)]
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        X, Y = batches[steps % 4]
+        V, S = eg.eg_step(V, S, *eg.cca_ops(X, Y), cfg["eta0"], cfg["gamma0"], cfg["rho"])
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds and steps >= 2:
+            break
+    return steps * b / el, steps, el
+
+
+def cpu_cores():
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(var):
+            return int(os.environ[var])
+    return os.cpu_count() or 1
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    cfg = getattr(synth, WORKLOADS[args.workload][0])()
+    per_step = max(1.0, 120.0 / max(1, args.steps + args.warmup))
+    rate, steps, el = oracle_rate(cfg, min(per_step * args.steps, 120.0))
+    sample = f"{steps} oracle steps of b={cfg['b']} rows ({el:.1f} s), FP64 numpy"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": "samples/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * el / steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic planted CCA",
+        "config": {"workload": args.workload},
+        "cpu_baseline": {"value": rate, "unit": "samples/s", "cores": cpu_cores(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": rate, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+
+def run_native(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2206_04993_gb300 import Solver, sgep
+
+    name, dtype, pool_rows = WORKLOADS[args.workload]
+    cfg = getattr(synth, name)(seed=rank)
+    model = cfg["model"]
+    b, k = cfg["b"], cfg["k"]
+    dx, dy = model.d_x, model.d_y
+    d = dx + dy
+    esz = 2 if dtype == "bf16" else 4
+    X, Y = make_pool(cfg, pool_rows, dtype, dev, seed=rank)
+    nb = pool_rows // b
+    solver = Solver(kind=sgep.SGEP_CCA, d_x=dx, d_y=dy, k=k,
+                    dtype=sgep.SGEP_BF16 if dtype == "bf16" else sgep.SGEP_F32,
+                    eta0=cfg["eta0"], gamma0=cfg["gamma0"], rho=cfg["rho"],
+                    schedule=cfg["schedule"], t_c=cfg["t_c"], T=cfg["T"], eta_T=cfg["eta_T"],
+                    max_b=b, path=args.path, seed=rank)
+    stream = torch.cuda.current_stream()
+
+    def run_steps(start, count):
+        s = start
+        left = count
+        while left > 0:
+            j = s % nb
+            n = min(left, nb - j)
+            solver.step_many(X[j * b:(j + n) * b], Y[j * b:(j + n) * b], b, n)
+            s += n
+            left -= n
+        return s
+
+    pos = run_steps(0, args.warmup)
+    solver.sync()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    launches0 = solver.launches
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        pos = run_steps(pos, args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    launches = solver.launches - launches0
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    solver.sync()
+    ms_step = ms / args.steps
+    value = world * b * args.steps / (ms / 1e3)
+
+    # roofline of the step (the minibatch is read once; V and [Bv] are read and written once)
+    peak, peak_kind = measured_peaks()
+    alg_bytes = b * d * esz + 16 * d * k
+    achieved = alg_bytes / (ms_step / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": f"sgep step, path {solver.path}", "peak_source": peak_kind,
+                "alg_bytes_per_launch": alg_bytes}
+
+    # e2e: through the C ABI with host buffers every step
+    e2e = None
+    if not args.no_e2e:
+        ne = min(args.steps, 200)
+        Xh = torch.empty((4, b, dx), dtype=X.dtype, pin_memory=True)
+        Yh = torch.empty((4, b, dy), dtype=Y.dtype, pin_memory=True)
+        for i in range(4):
+            Xh[i].copy_(X[i * b:(i + 1) * b])
+            Yh[i].copy_(Y[i * b:(i + 1) * b])
+        Xd = torch.empty((b, dx), dtype=X.dtype, device=dev)
+        Yd = torch.empty((b, dy), dtype=Y.dtype, device=dev)
+        Vh = np.empty((d, k), dtype=np.float32)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(ne):
+            Xd.copy_(Xh[i % 4], non_blocking=True)
+            Yd.copy_(Yh[i % 4], non_blocking=True)
+            solver.step(Xd, Yd)
+            sgep.sgep_get_V(solver.h, Vh, False, stream.cuda_stream)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        e2e = {"value": world * b * ne / el, "unit": "samples/s",
+               "h2d_bytes_per_step": b * d * esz, "d2h_bytes_per_step": d * k * 4,
+               "steps": ne}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        rate, steps, el = oracle_rate(cfg, args.cpu_seconds)
+        cpu = {"value": rate, "unit": "samples/s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"{steps} FP64 oracle steps of b={b} ({el:.1f} s) on this workload"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": dtype, "data": "synthetic planted CCA generated on device",
+            "config": {"workload": args.workload, "d_x": dx, "d_y": dy, "k": k, "b": b,
+                       "pool_rows": pool_rows, "l2": "inputs larger than L2 (pool streamed)",
+                       "parallelism": f"replicas{world}", "path": solver.path},
+            "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * sgep.h -- C ABI of libsgep: the minibatch gamma-EigenGame iteration for the
+ * top-k symmetric generalized eigenproblem  A v = lambda B v  on one GB300
+ * (sm_103a).
+ *
+ * Method: Gemp, Chen, McWilliams, "The Symmetric Generalized Eigenvalue
+ * Problem as a Nash Equilibrium" (arXiv 2206.04993), Alg. 2 ("Stochastic
+ * gamma-EigenGame") with M = 1 machine; the update direction is Eq. (update)
+ * of Sec. 3, A and B are expectations of outer products (Sec. 1) and are never
+ * formed: each step streams one minibatch through  X V  and  X^T (X V).
+ *
+ * Conventions shared by every entry point
+ *  - Every function returns SGEP_OK (0) or a negative status code below.
+ *    Nothing throws across the ABI. sgep_last_error() describes the most
+ *    recent failure of the calling thread.
+ *  - A handle owns all of its device state (V, [Bv], accumulators, scratch).
+ *    It is not thread-safe: calls on one handle must not overlap, and work
+ *    enqueued on different streams for one handle must not overlap on the GPU.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream). Device work is enqueued asynchronously on it; device-side
+ *    errors (non-finite values, exhausted spin limits) are recorded in a
+ *    device flag and reported by the next synchronising call (sgep_sync,
+ *    sgep_get_V, sgep_get_eigenvalues, sgep_get_state, sgep_debug_*).
+ *  - Data matrices are row-major, one sample per row: X is b x d_x, Y is
+ *    b x d_y, element (r, c) at X[r * d_x + c]. Their element type is the
+ *    handle's dtype (float for SGEP_F32, bfloat16 bit patterns for
+ *    SGEP_BF16). They are caller-owned DEVICE pointers and must stay valid
+ *    until the work on `stream` has completed.
+ *  - The player matrix V (and [Bv], called S here) is d x k row-major float:
+ *    element (c, i) at V[c * k + i], so column i is the player vector v_i
+ *    and d = d_x + d_y (d = d_x for PCA and LDA).
+ */
+#ifndef SGEP_H_
+#define SGEP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define SGEP_OK          0
+#define SGEP_EINVAL     (-1)  /* invalid argument or configuration            */
+#define SGEP_ENOMEM     (-2)  /* device or host allocation failed             */
+#define SGEP_ECUDA      (-3)  /* a CUDA runtime call failed                   */
+#define SGEP_ETIMEOUT   (-4)  /* a bounded device-side wait gave up           */
+#define SGEP_ENONFINITE (-5)  /* NaN or Inf appeared in the player vectors    */
+#define SGEP_ELAUNCH    (-6)  /* a kernel could not be launched as configured */
+#define SGEP_ESTATE     (-7)  /* state blob malformed / wrong shape / version */
+#define SGEP_ENOTSUP    (-8)  /* combination not supported by this build      */
+
+/* ---- problem kinds (Sec. 1) --------------------------------------------- */
+#define SGEP_PCA 0  /* A = E[x x^T], B = I                                       */
+#define SGEP_CCA 1  /* A = [[0, E xy^T], [E yx^T, 0]], B = blockdiag(E xx^T, E yy^T) */
+#define SGEP_PLS 2  /* A as CCA, B = I (reading of Sec. 1, which gives no formula) */
+#define SGEP_LDA 3  /* reserved: between-class A, within-class B (not built yet)  */
+
+/* ---- element type of X and Y ------------------------------------------- */
+#define SGEP_F32  0
+#define SGEP_BF16 1
+
+/* ---- step-size schedules (App. H.2.2) ----------------------------------- */
+#define SGEP_SCHED_CONST          0  /* eta_t = eta0                                   */
+#define SGEP_SCHED_HOLD_HARMONIC  1  /* eta0 up to t_c, then ~1/(t+Delta), eta_T at T  */
+#define SGEP_SCHED_WARMUP_HARMONIC 2 /* linear warm-up to eta0 at t_c, then as above   */
+
+/* ---- kernel path selection --------------------------------------------- */
+#define SGEP_PATH_AUTO    0  /* pick by shape and dtype                         */
+#define SGEP_PATH_GENERIC 1  /* multi-kernel SIMT path, any shape               */
+#define SGEP_PATH_CLUSTER 2  /* one fused cluster kernel per step, d <= 4096    */
+#define SGEP_PATH_TC      3  /* tcgen05 tensor-core fused path, BF16, large d   */
+
+typedef struct sgep_ctx* sgep_t;
+
+/* Configuration of one problem instance. Fill with sgep_config_default()
+ * and override fields; unknown future fields keep their defaults. */
+typedef struct {
+  int32_t  kind;       /* SGEP_PCA / SGEP_CCA / SGEP_PLS                          */
+  int32_t  dtype;      /* SGEP_F32 or SGEP_BF16 (element type of X, Y)            */
+  int64_t  d_x;        /* columns of X (>= 1)                                      */
+  int64_t  d_y;        /* columns of Y (>= 1 for CCA/PLS, must be 0 for PCA)       */
+  int32_t  k;          /* number of players, 1 <= k <= 64 and k <= d              */
+  int32_t  n_classes;  /* LDA only (reserved)                                      */
+  float    eta0;       /* player step size eta (Alg. 2 "step size sequence")      */
+  float    gamma0;     /* auxiliary step size gamma_t (constant; beta_t in App. H) */
+  float    rho;        /* clipping floor of <v_j, [Bv]_j> (Alg. 2), > 0           */
+  float    eps_B;      /* optional ridge: B_t + eps_B I (App. G); default 0        */
+  int32_t  schedule;   /* SGEP_SCHED_*                                              */
+  int32_t  split_AB;   /* 1: rows [0, b/2) estimate A, rows [b/2, b) estimate B   */
+                       /* (independent batches of Alg. 2); 0: all rows for both    */
+  int64_t  t_c;        /* schedule knee (App. H.2.2)                               */
+  int64_t  T;          /* schedule horizon: eta_t reaches eta_T at t = T           */
+  float    eta_T;      /* final step size                                          */
+  int32_t  path;       /* SGEP_PATH_*                                              */
+  uint64_t seed;       /* seed of the initial V (Philox-4x32-10 + Box-Muller)      */
+  int64_t  max_b;      /* largest minibatch (rows) a step or readout chunk may use */
+  int32_t  debug;      /* 1: keep update directions and k x k terms for sgep_debug_update */
+  int32_t  reserved[7];
+} sgep_config;
+
+/* Fill `cfg` with defaults: CCA, F32, k = 1, eta0 = 0.1, gamma0 = 1, rho = 1e-6,
+ * eps_B = 0, constant schedule, split_AB = 1, path AUTO, seed 0, max_b 4096.
+ * Returns SGEP_EINVAL if cfg is NULL. */
+int sgep_config_default(sgep_config* cfg);
+
+/* Create a handle (Alg. 2 initialisation): allocate device state on the
+ * current CUDA device, draw v_i ~ N(0, I_d) and scale each to unit norm
+ * (Alg. 2, line "v_i ~ S^{d-1}"), and set [Bv]_i = v_i (Alg. 2, auxiliary
+ * initialisation). Synchronous. On error *out is left NULL and nothing leaks.
+ * Errors: SGEP_EINVAL (bad shape/kind/dtype/rho/k), SGEP_ENOMEM, SGEP_ECUDA,
+ * SGEP_ENOTSUP (e.g. LDA, or a forced path that cannot run the shape). */
+int sgep_init(const sgep_config* cfg, sgep_t* out);
+
+/* Free every resource of the handle (synchronises the device first).
+ * NULL is accepted. */
+int sgep_destroy(sgep_t h);
+
+/* One iteration of Alg. 2 (M = 1) on the minibatch (X, Y) of b rows:
+ * A_t and B_t are the minibatch estimates (split per cfg.split_AB),
+ * the update direction is Eq. (update) with the clipped auxiliary terms,
+ * v_i <- (v_i + eta_t grad_i) / ||.||, [Bv]_i <- [Bv]_i + gamma_t (B_t v_i - [Bv]_i),
+ * all players reading the state of step t. Asynchronous on `stream`.
+ * X: device, b x d_x; Y: device, b x d_y (NULL for PCA); labels: reserved, NULL.
+ * Requires 2 <= b <= max_b when split_AB = 1 (1 <= b otherwise).
+ * The work of a step may be completed lazily by the next step or by the
+ * next synchronising call. Errors: SGEP_EINVAL, SGEP_ECUDA, SGEP_ELAUNCH. */
+int sgep_step(sgep_t h, const void* X, const void* Y, const int32_t* labels,
+              int64_t b, void* stream);
+
+/* `nsteps` consecutive iterations on minibatches stored back to back:
+ * step s reads rows [s*b, (s+1)*b) of X and Y. Same contract as sgep_step. */
+int sgep_step_many(sgep_t h, const void* X, const void* Y, const int32_t* labels,
+                   int64_t b, int64_t nsteps, void* stream);
+
+/* Wait for the handle's work on `stream` and report device-side errors
+ * (SGEP_ENONFINITE, SGEP_ETIMEOUT). Clears the recorded error. */
+int sgep_sync(sgep_t h, void* stream);
+
+/* Copy V (d x k row-major float) to `out` (device pointer if on_device,
+ * else host). Completes pending work and synchronises `stream`. */
+int sgep_get_V(sgep_t h, float* out, int on_device, void* stream);
+
+/* Copy the auxiliary variables [Bv] (d x k row-major float) to `out`. */
+int sgep_get_S(sgep_t h, float* out, int on_device, void* stream);
+
+/* Replace V by `V` (d x k row-major float, host or device) and reset
+ * [Bv] <- V (warm start, Alg. 2 auxiliary initialisation). Columns are used
+ * as given (callers pass unit-norm columns). Synchronous. */
+int sgep_set_V(sgep_t h, const float* V, int on_device, void* stream);
+
+/* Replace both V and [Bv] (S may not equal V). Synchronous. */
+int sgep_set_VS(sgep_t h, const float* V, const float* S, int on_device, void* stream);
+
+/* Generalized Rayleigh quotients lambda_i = <v_i, A v_i> / <v_i, B v_i>
+ * (Sec. 2, below Eq. util_new) with A and B estimated on the n evaluation
+ * rows (X, Y) (all rows for both; App. H.2.2 evaluates on a larger batch than
+ * it trains on). Sums are accumulated in double. out_k: host, k doubles.
+ * Synchronous. Any n >= 1 (processed in chunks of max_b rows). */
+int sgep_get_eigenvalues(sgep_t h, const void* X, const void* Y, const int32_t* labels,
+                         int64_t n, double* out_k, void* stream);
+
+/* Serialise the state (versioned header, V, [Bv], step counter) into `buf`.
+ * If buf is NULL, only writes the required size to *nbytes. Synchronous. */
+int sgep_get_state(sgep_t h, void* buf, size_t* nbytes);
+
+/* Restore a state written by sgep_get_state for the same kind, d_x, d_y, k.
+ * Errors: SGEP_ESTATE on a malformed or mismatched blob. Synchronous. */
+int sgep_set_state(sgep_t h, const void* buf, size_t nbytes);
+
+/* Number of iterations applied so far (t of Alg. 2). */
+int64_t sgep_step_count(sgep_t h);
+
+/* The step size eta_t the handle uses at iteration t (1-based). */
+double sgep_eta_at(sgep_t h, int64_t t);
+
+/* Kernel path the handle runs (SGEP_PATH_GENERIC / _CLUSTER / _TC). */
+int sgep_path(sgep_t h);
+
+/* Number of CUDA kernels the handle has launched since sgep_init (memsets and
+ * copies are not counted). Returns -1 for a NULL handle. */
+int64_t sgep_launch_count(sgep_t h);
+
+/* Diagnostics for parity tests. sgep_debug_products copies the minibatch
+ * products of the most recent step, A_t V and B_t V (each d x k row-major,
+ * host), before the update was applied (for PCA and PLS, where B = I, B_t V is
+ * not formed and BV is zero-filled). sgep_debug_update (needs cfg.debug=1)
+ * copies the update direction grad (d x k), and the k x k terms
+ * [a_ij = v_i^T A_t v_j (k*k), b_i = v_i^T B_t v_i (k), G_ij = <v_i, [Bv]_j> (k*k)]
+ * into `terms` (2 k^2 + k doubles) of the most recent completed step. Synchronous. */
+int sgep_debug_products(sgep_t h, float* AV, float* BV);
+int sgep_debug_update(sgep_t h, float* grad, double* terms);
+
+/* Human-readable name of a status code (static string). */
+const char* sgep_strerror(int status);
+
+/* Description of the most recent failure on the calling thread ("" if none). */
+const char* sgep_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SGEP_H_ */

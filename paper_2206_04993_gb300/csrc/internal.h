@@ -1,0 +1,87 @@
+// Internal declarations shared by the host-side ABI and the kernel files.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/sgep.h"
+
+namespace sgep {
+
+// Per-handle device state. All device buffers are allocated once by sgep_init.
+struct Ctx {
+  sgep_config cfg;
+  int64_t d_x = 0, d_y = 0, d = 0;
+  int k = 0;
+  int path = SGEP_PATH_GENERIC;
+  int device = 0;
+  int num_sms = 0;
+  bool b_is_identity = false;  // PCA, PLS
+  bool has_y = false;          // CCA, PLS
+
+  float* V = nullptr;      // d x k, player vectors v_i (columns)
+  float* S = nullptr;      // d x k, auxiliary variables [Bv]_i
+  float* Vtmp = nullptr;   // d x k, v_i + eta grad_i before the retraction
+  float* PQ = nullptr;     // max_b x 2k, row projections [X V_x | Y V_y]
+  float* acc = nullptr;    // 2 x d x k: A_t V then B_t V
+  float* gram = nullptr;   // k*k (a_ij), k*k (G_ij), k (b_i), k (norms^2)
+  float* grad = nullptr;   // d x k update directions (debug only)
+  double* rq = nullptr;    // 2k doubles: Rayleigh numerator / denominator sums
+  int* dflag = nullptr;    // device error word: bit 0 non-finite, bit 1 timeout
+
+  // cluster path
+  float* cl_state = nullptr;   // extra buffers owned by the cluster path
+  int cl_pending = 0;          // products of one step are waiting for their update
+  float cl_eta = 0.f, cl_gamma = 0.f;
+  int cl_parity = 0;           // which accumulator slot the next step writes
+
+  int64_t t = 0;       // iterations applied (Alg. 2's t)
+  int64_t launches = 0; // kernels launched
+  int debug_valid = 0; // sgep_debug_update has data
+};
+
+// Flag bits of Ctx::dflag.
+constexpr int kFlagNonFinite = 1;
+constexpr int kFlagTimeout = 2;
+
+// Error reporting (thread-local message).
+void set_error(const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define SGEP_CUDA_TRY(expr)                                   \
+  do {                                                        \
+    cudaError_t _e = (expr);                                  \
+    if (_e != cudaSuccess) return ::sgep::cuda_fail(_e, #expr); \
+  } while (0)
+
+// Step-size schedule (App. H.2.2), evaluated on the host.
+double schedule_eta(const sgep_config& c, int64_t t);
+
+// ---- generic SIMT path (kernels_generic.cu) ----
+// Products of one minibatch: acc <- [A_t V ; B_t V], PQ scratch.
+int generic_products(Ctx& c, const void* X, const void* Y, int64_t b, cudaStream_t s);
+// Update from acc: grams, update, retraction. eta/gamma of this step.
+int generic_update(Ctx& c, float eta, float gamma, cudaStream_t s);
+// Row projections of n rows into PQ (n <= max_b), zeroing PQ first.
+int generic_project(Ctx& c, const void* X, const void* Y, int64_t n, cudaStream_t s);
+// Rayleigh sums of the n rows in PQ accumulated into rq (double).
+int generic_rayleigh_sums(Ctx& c, int64_t n, cudaStream_t s);
+
+// ---- cluster path (kernels_cluster.cu) ----
+bool cluster_supported(const Ctx& c, const char** why);
+int cluster_alloc(Ctx& c);
+void cluster_free(Ctx& c);
+// One fused launch: pending update (if any) then the products of (X, Y).
+int cluster_step(Ctx& c, const void* X, const void* Y, int64_t b, float eta, float gamma,
+                 cudaStream_t s);
+// Apply a pending update (no new minibatch).
+int cluster_flush(Ctx& c, cudaStream_t s);
+// Copy the pending products into acc layout (d x k AV, d x k BV) for debugging.
+int cluster_products(Ctx& c, float* AV, float* BV, cudaStream_t s);
+
+}  // namespace sgep
+
+// The opaque handle type of the ABI is the context itself.
+struct sgep_ctx : public sgep::Ctx {};

@@ -1,0 +1,523 @@
+// Host side of the C ABI declared in include/sgep.h: handle lifetime,
+// argument checks, the step-size schedule, path dispatch, state blobs.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace sgep {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+int cuda_fail(cudaError_t e, const char* what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? SGEP_ENOMEM : SGEP_ECUDA;
+}
+
+static int fail(int code, const std::string& msg) {
+  set_error(msg);
+  return code;
+}
+
+// App. H.2.2: warm-up (or hold) until t_c, then eta proportional to 1/(t + Delta) with
+// Delta chosen so that eta_T is reached at t = T.
+double schedule_eta(const sgep_config& c, int64_t t) {
+  const double eta0 = c.eta0;
+  if (c.schedule == SGEP_SCHED_CONST) return eta0;
+  const double tc = (double)c.t_c, T = (double)c.T, etaT = c.eta_T;
+  const double delta = (etaT * T - eta0 * tc) / (eta0 - etaT);
+  if ((double)t <= tc) return c.schedule == SGEP_SCHED_HOLD_HARMONIC ? eta0 : eta0 * (double)t / tc;
+  return eta0 * (tc + delta) / ((double)t + delta);
+}
+
+// Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) for the initial V.
+static void philox4x32(uint32_t ctr[4], uint32_t key[2]) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)M0 * ctr[0];
+    const uint64_t p1 = (uint64_t)M1 * ctr[2];
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    const uint32_t c0 = hi1 ^ ctr[1] ^ k0, c2 = hi0 ^ ctr[3] ^ k1;
+    ctr[0] = c0;
+    ctr[1] = lo1;
+    ctr[2] = c2;
+    ctr[3] = lo0;
+    k0 += W0;
+    k1 += W1;
+  }
+}
+
+static void gaussian_init(std::vector<float>& V, int64_t d, int k, uint64_t seed) {
+  // column i gets Philox counters (i, c/2, 0, 0); Box-Muller pairs.
+  std::vector<double> col(d);
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int i = 0; i < k; ++i) {
+    double nrm = 0.0;
+    for (int64_t c = 0; c < d; c += 2) {
+      uint32_t ctr[4] = {(uint32_t)i, (uint32_t)(c >> 1), (uint32_t)((uint64_t)c >> 33), 0u};
+      uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+      philox4x32(ctr, key);
+      const double u1 = ((double)ctr[0] + 1.0) / 4294967296.0;  // (0, 1]
+      const double u2 = (double)ctr[1] / 4294967296.0;
+      const double r = std::sqrt(-2.0 * std::log(u1));
+      col[c] = r * std::cos(two_pi * u2);
+      if (c + 1 < d) col[c + 1] = r * std::sin(two_pi * u2);
+    }
+    for (int64_t c = 0; c < d; ++c) nrm += col[c] * col[c];
+    nrm = std::sqrt(nrm);
+    for (int64_t c = 0; c < d; ++c) V[c * k + i] = (float)(col[c] / nrm);
+  }
+}
+
+static void free_ctx(sgep_ctx* c) {
+  if (!c) return;
+  cluster_free(*c);
+  cudaFree(c->V);
+  cudaFree(c->S);
+  cudaFree(c->Vtmp);
+  cudaFree(c->PQ);
+  cudaFree(c->acc);
+  cudaFree(c->gram);
+  cudaFree(c->grad);
+  cudaFree(c->rq);
+  cudaFree(c->dflag);
+  delete c;
+}
+
+static int check_flag(Ctx& c) {
+  int flag = 0;
+  SGEP_CUDA_TRY(cudaMemcpy(&flag, c.dflag, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag) {
+    SGEP_CUDA_TRY(cudaMemset(c.dflag, 0, sizeof(int)));
+    if (flag & kFlagTimeout) return fail(SGEP_ETIMEOUT, "a bounded device-side wait gave up");
+    if (flag & kFlagNonFinite) return fail(SGEP_ENONFINITE, "non-finite values in V");
+  }
+  return SGEP_OK;
+}
+
+// Completes a step whose update is still pending (cluster path) and synchronises.
+static int complete(Ctx& c, cudaStream_t s) {
+  if (c.path == SGEP_PATH_CLUSTER && c.cl_pending) {
+    int rc = cluster_flush(c, s);
+    if (rc) return rc;
+  }
+  SGEP_CUDA_TRY(cudaStreamSynchronize(s));
+  return check_flag(c);
+}
+
+}  // namespace sgep
+
+using namespace sgep;
+
+static_assert(sizeof(sgep_config) == 128, "sgep_config layout changed: update the bindings");
+
+extern "C" {
+
+int sgep_config_default(sgep_config* cfg) {
+  if (!cfg) return fail(SGEP_EINVAL, "cfg is NULL");
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->kind = SGEP_CCA;
+  cfg->dtype = SGEP_F32;
+  cfg->d_x = 1;
+  cfg->d_y = 1;
+  cfg->k = 1;
+  cfg->eta0 = 0.1f;
+  cfg->gamma0 = 1.0f;
+  cfg->rho = 1e-6f;
+  cfg->eps_B = 0.0f;
+  cfg->schedule = SGEP_SCHED_CONST;
+  cfg->split_AB = 1;
+  cfg->t_c = 1;
+  cfg->T = 2;
+  cfg->eta_T = 0.1f;
+  cfg->path = SGEP_PATH_AUTO;
+  cfg->seed = 0;
+  cfg->max_b = 4096;
+  cfg->debug = 0;
+  return SGEP_OK;
+}
+
+int sgep_init(const sgep_config* cfg, sgep_t* out) {
+  if (!out) return fail(SGEP_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!cfg) return fail(SGEP_EINVAL, "cfg is NULL");
+  const sgep_config& g = *cfg;
+  if (g.kind == SGEP_LDA) return fail(SGEP_ENOTSUP, "LDA is not built yet");
+  if (g.kind != SGEP_PCA && g.kind != SGEP_CCA && g.kind != SGEP_PLS)
+    return fail(SGEP_EINVAL, "unknown kind");
+  if (g.dtype != SGEP_F32 && g.dtype != SGEP_BF16) return fail(SGEP_EINVAL, "unknown dtype");
+  if (g.d_x < 1) return fail(SGEP_EINVAL, "d_x must be >= 1");
+  if (g.kind == SGEP_PCA && g.d_y != 0) return fail(SGEP_EINVAL, "PCA requires d_y = 0");
+  if (g.kind != SGEP_PCA && g.d_y < 1) return fail(SGEP_EINVAL, "CCA/PLS require d_y >= 1");
+  const int64_t d = g.d_x + g.d_y;
+  if (g.k < 1 || g.k > 64 || g.k > d) return fail(SGEP_EINVAL, "k must satisfy 1 <= k <= min(64, d)");
+  if (!(g.rho > 0.f) || !std::isfinite(g.rho)) return fail(SGEP_EINVAL, "rho must be > 0");
+  if (!std::isfinite(g.eta0) || !std::isfinite(g.gamma0) || !std::isfinite(g.eps_B) || g.eps_B < 0.f)
+    return fail(SGEP_EINVAL, "eta0, gamma0 must be finite and eps_B >= 0");
+  if (g.schedule < 0 || g.schedule > 2) return fail(SGEP_EINVAL, "unknown schedule");
+  if (g.schedule != SGEP_SCHED_CONST &&
+      (g.t_c < 1 || g.T <= g.t_c || !(g.eta_T > 0.f) || !(g.eta_T < g.eta0)))
+    return fail(SGEP_EINVAL, "schedule needs 1 <= t_c < T and 0 < eta_T < eta0");
+  if (g.max_b < 2 || g.max_b > (1LL << 24)) return fail(SGEP_EINVAL, "max_b out of range");
+  if (g.path < 0 || g.path > 3) return fail(SGEP_EINVAL, "unknown path");
+
+  sgep_ctx* c = new (std::nothrow) sgep_ctx();
+  if (!c) return fail(SGEP_ENOMEM, "host allocation failed");
+  c->cfg = g;
+  c->d_x = g.d_x;
+  c->d_y = g.d_y;
+  c->d = d;
+  c->k = g.k;
+  c->b_is_identity = (g.kind == SGEP_PCA || g.kind == SGEP_PLS);
+  c->has_y = (g.kind != SGEP_PCA);
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (e != cudaSuccess) {
+    free_ctx(c);
+    return cuda_fail(e, "cudaGetDevice");
+  }
+  const size_t dk = (size_t)d * g.k;
+  const size_t kk = (size_t)g.k * g.k;
+  struct {
+    void** p;
+    size_t n;
+  } allocs[] = {
+      {(void**)&c->V, dk * sizeof(float)},
+      {(void**)&c->S, dk * sizeof(float)},
+      {(void**)&c->Vtmp, dk * sizeof(float)},
+      {(void**)&c->PQ, (size_t)g.max_b * 2 * g.k * sizeof(float)},
+      {(void**)&c->acc, 2 * dk * sizeof(float)},
+      {(void**)&c->gram, (2 * kk + 2 * g.k) * sizeof(float)},
+      {(void**)&c->rq, 2 * g.k * sizeof(double)},
+      {(void**)&c->dflag, sizeof(int)},
+  };
+  for (auto& a : allocs) {
+    e = cudaMalloc(a.p, a.n);
+    if (e != cudaSuccess) {
+      free_ctx(c);
+      return cuda_fail(e, "cudaMalloc (state)");
+    }
+  }
+  if (g.debug) {
+    e = cudaMalloc((void**)&c->grad, dk * sizeof(float));
+    if (e != cudaSuccess) {
+      free_ctx(c);
+      return cuda_fail(e, "cudaMalloc (debug)");
+    }
+  }
+  cudaMemset(c->dflag, 0, sizeof(int));
+  cudaMemset(c->acc, 0, 2 * dk * sizeof(float));
+
+  // Path selection.
+  const char* why = nullptr;
+  const bool cl_ok = cluster_supported(*c, &why);
+  if (g.path == SGEP_PATH_AUTO) {
+    c->path = cl_ok ? SGEP_PATH_CLUSTER : SGEP_PATH_GENERIC;
+  } else if (g.path == SGEP_PATH_CLUSTER) {
+    if (!cl_ok) {
+      free_ctx(c);
+      return fail(SGEP_ENOTSUP, std::string("cluster path: ") + (why ? why : "unsupported"));
+    }
+    c->path = SGEP_PATH_CLUSTER;
+  } else if (g.path == SGEP_PATH_TC) {
+    free_ctx(c);
+    return fail(SGEP_ENOTSUP, "tensor-core path is not built yet");
+  } else {
+    c->path = SGEP_PATH_GENERIC;
+  }
+  if (c->path == SGEP_PATH_CLUSTER) {
+    int rc = cluster_alloc(*c);
+    if (rc) {
+      free_ctx(c);
+      return rc;
+    }
+  }
+
+  std::vector<float> V0(dk);
+  gaussian_init(V0, d, g.k, g.seed);
+  e = cudaMemcpy(c->V, V0.data(), dk * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->S, V0.data(), dk * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    free_ctx(c);
+    return cuda_fail(e, "initialising V");
+  }
+  *out = c;
+  return SGEP_OK;
+}
+
+int sgep_destroy(sgep_t h) {
+  if (!h) return SGEP_OK;
+  cudaDeviceSynchronize();
+  free_ctx(h);
+  return SGEP_OK;
+}
+
+static int step_checks(Ctx& c, const void* X, const void* Y, int64_t b) {
+  if (!X) return fail(SGEP_EINVAL, "X is NULL");
+  if (c.has_y && !Y) return fail(SGEP_EINVAL, "Y is NULL");
+  const bool split = c.cfg.kind == SGEP_CCA && c.cfg.split_AB;
+  if (b < (split ? 2 : 1)) return fail(SGEP_EINVAL, "b too small (split batches need b >= 2)");
+  if (b > c.cfg.max_b) return fail(SGEP_EINVAL, "b exceeds max_b");
+  return SGEP_OK;
+}
+
+static int do_step(Ctx& c, const void* X, const void* Y, int64_t b, cudaStream_t s) {
+  const int64_t t = c.t + 1;
+  const float eta = (float)schedule_eta(c.cfg, t);
+  const float gamma = c.cfg.gamma0;
+  int rc;
+  if (c.path == SGEP_PATH_CLUSTER) {
+    rc = cluster_step(c, X, Y, b, eta, gamma, s);
+  } else {
+    rc = generic_products(c, X, Y, b, s);
+    if (!rc) rc = generic_update(c, eta, gamma, s);
+    if (!rc) c.debug_valid = c.cfg.debug;
+  }
+  if (!rc) c.t = t;
+  return rc;
+}
+
+int sgep_step(sgep_t h, const void* X, const void* Y, const int32_t* labels, int64_t b, void* stream) {
+  (void)labels;
+  if (!h) return fail(SGEP_EINVAL, "handle is NULL");
+  int rc = step_checks(*h, X, Y, b);
+  if (rc) return rc;
+  return do_step(*h, X, Y, b, (cudaStream_t)stream);
+}
+
+int sgep_step_many(sgep_t h, const void* X, const void* Y, const int32_t* labels, int64_t b,
+                   int64_t nsteps, void* stream) {
+  (void)labels;
+  if (!h) return fail(SGEP_EINVAL, "handle is NULL");
+  if (nsteps < 0) return fail(SGEP_EINVAL, "nsteps < 0");
+  int rc = step_checks(*h, X, Y, b);
+  if (rc) return rc;
+  const size_t esz = h->cfg.dtype == SGEP_BF16 ? 2 : 4;
+  for (int64_t s = 0; s < nsteps; ++s) {
+    const char* xs = (const char*)X + (size_t)s * b * h->d_x * esz;
+    const char* ys = Y ? (const char*)Y + (size_t)s * b * h->d_y * esz : nullptr;
+    rc = do_step(*h, xs, ys, b, (cudaStream_t)stream);
+    if (rc) return rc;
+  }
+  return SGEP_OK;
+}
+
+int sgep_sync(sgep_t h, void* stream) {
+  if (!h) return fail(SGEP_EINVAL, "handle is NULL");
+  return complete(*h, (cudaStream_t)stream);
+}
+
+static int copy_out(Ctx& c, const float* src, float* out, int on_device, void* stream) {
+  if (!out) return fail(SGEP_EINVAL, "out is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = complete(c, s);
+  if (rc) return rc;
+  SGEP_CUDA_TRY(cudaMemcpyAsync(out, src, sizeof(float) * c.d * c.k,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  SGEP_CUDA_TRY(cudaStreamSynchronize(s));
+  return SGEP_OK;
+}
+
+int sgep_get_V(sgep_t h, float* out, int on_device, void* stream) {
+  if (!h) return fail(SGEP_EINVAL, "handle is NULL");
+  return copy_out(*h, h->V, out, on_device, stream);
+}
+
+int sgep_get_S(sgep_t h, float* out, int on_device, void* stream) {
+  if (!h) return fail(SGEP_EINVAL, "handle is NULL");
+  return copy_out(*h, h->S, out, on_device, stream);
+}
+
+int sgep_set_VS(sgep_t h, const float* V, const float* S, int on_device, void* stream) {
+  if (!h) return fail(SGEP_EINVAL, "handle is NULL");
+  if (!V || !S) return fail(SGEP_EINVAL, "V or S is NULL");
+  Ctx& c = *h;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = complete(c, s);
+  if (rc) return rc;
+  const cudaMemcpyKind kd = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  SGEP_CUDA_TRY(cudaMemcpyAsync(c.V, V, sizeof(float) * c.d * c.k, kd, s));
+  SGEP_CUDA_TRY(cudaMemcpyAsync(c.S, S, sizeof(float) * c.d * c.k, kd, s));
+  SGEP_CUDA_TRY(cudaStreamSynchronize(s));
+  c.debug_valid = 0;
+  return SGEP_OK;
+}
+
+int sgep_set_V(sgep_t h, const float* V, int on_device, void* stream) {
+  return sgep_set_VS(h, V, V, on_device, stream);
+}
+
+int sgep_get_eigenvalues(sgep_t h, const void* X, const void* Y, const int32_t* labels, int64_t n,
+                         double* out_k, void* stream) {
+  (void)labels;
+  if (!h) return fail(SGEP_EINVAL, "handle is NULL");
+  Ctx& c = *h;
+  if (!X || (c.has_y && !Y) || !out_k) return fail(SGEP_EINVAL, "NULL argument");
+  if (n < 1) return fail(SGEP_EINVAL, "n must be >= 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = complete(c, s);
+  if (rc) return rc;
+  const int k = c.k;
+  SGEP_CUDA_TRY(cudaMemsetAsync(c.rq, 0, sizeof(double) * 2 * k, s));
+  const size_t esz = c.cfg.dtype == SGEP_BF16 ? 2 : 4;
+  for (int64_t r0 = 0; r0 < n; r0 += c.cfg.max_b) {
+    const int64_t m = std::min<int64_t>(c.cfg.max_b, n - r0);
+    const char* xs = (const char*)X + (size_t)r0 * c.d_x * esz;
+    const char* ys = c.has_y ? (const char*)Y + (size_t)r0 * c.d_y * esz : nullptr;
+    rc = generic_project(c, xs, ys, m, s);
+    if (!rc) rc = generic_rayleigh_sums(c, m, s);
+    if (rc) return rc;
+  }
+  std::vector<double> sums(2 * k);
+  std::vector<float> V((size_t)c.d * k);
+  SGEP_CUDA_TRY(cudaMemcpyAsync(sums.data(), c.rq, sizeof(double) * 2 * k, cudaMemcpyDeviceToHost, s));
+  SGEP_CUDA_TRY(cudaMemcpyAsync(V.data(), c.V, sizeof(float) * V.size(), cudaMemcpyDeviceToHost, s));
+  SGEP_CUDA_TRY(cudaStreamSynchronize(s));
+  for (int i = 0; i < k; ++i) {
+    double vv = 0.0;
+    for (int64_t r = 0; r < c.d; ++r) vv += (double)V[r * k + i] * V[r * k + i];
+    double num = sums[i] / (double)n;
+    double den = c.b_is_identity ? vv : sums[k + i] / (double)n;
+    den += (double)c.cfg.eps_B * vv;
+    out_k[i] = num / den;
+  }
+  return SGEP_OK;
+}
+
+// State blob: header then V and S (float, d x k each).
+struct StateHeader {
+  char magic[8];
+  int32_t version;
+  int32_t kind;
+  int64_t d_x, d_y;
+  int32_t k;
+  int32_t pad;
+  int64_t t;
+};
+
+int sgep_get_state(sgep_t h, void* buf, size_t* nbytes) {
+  if (!h || !nbytes) return fail(SGEP_EINVAL, "NULL argument");
+  Ctx& c = *h;
+  const size_t dk = (size_t)c.d * c.k;
+  const size_t need = sizeof(StateHeader) + 2 * dk * sizeof(float);
+  if (!buf) {
+    *nbytes = need;
+    return SGEP_OK;
+  }
+  if (*nbytes < need) return fail(SGEP_EINVAL, "buffer too small");
+  int rc = complete(c, (cudaStream_t)0);
+  if (rc) return rc;
+  StateHeader hd;
+  std::memset(&hd, 0, sizeof(hd));
+  std::memcpy(hd.magic, "SGEPSTAT", 8);
+  hd.version = 1;
+  hd.kind = c.cfg.kind;
+  hd.d_x = c.d_x;
+  hd.d_y = c.d_y;
+  hd.k = c.k;
+  hd.t = c.t;
+  char* p = (char*)buf;
+  std::memcpy(p, &hd, sizeof(hd));
+  SGEP_CUDA_TRY(cudaMemcpy(p + sizeof(hd), c.V, dk * sizeof(float), cudaMemcpyDeviceToHost));
+  SGEP_CUDA_TRY(cudaMemcpy(p + sizeof(hd) + dk * sizeof(float), c.S, dk * sizeof(float),
+                           cudaMemcpyDeviceToHost));
+  *nbytes = need;
+  return SGEP_OK;
+}
+
+int sgep_set_state(sgep_t h, const void* buf, size_t nbytes) {
+  if (!h || !buf) return fail(SGEP_EINVAL, "NULL argument");
+  Ctx& c = *h;
+  const size_t dk = (size_t)c.d * c.k;
+  if (nbytes < sizeof(StateHeader)) return fail(SGEP_ESTATE, "state blob too short");
+  StateHeader hd;
+  std::memcpy(&hd, buf, sizeof(hd));
+  if (std::memcmp(hd.magic, "SGEPSTAT", 8) != 0 || hd.version != 1)
+    return fail(SGEP_ESTATE, "not a state blob of this version");
+  if (hd.kind != c.cfg.kind || hd.d_x != c.d_x || hd.d_y != c.d_y || hd.k != c.k)
+    return fail(SGEP_ESTATE, "state blob has a different kind or shape");
+  if (nbytes != sizeof(StateHeader) + 2 * dk * sizeof(float))
+    return fail(SGEP_ESTATE, "state blob has the wrong size");
+  int rc = complete(c, (cudaStream_t)0);
+  if (rc) return rc;
+  const char* p = (const char*)buf + sizeof(hd);
+  SGEP_CUDA_TRY(cudaMemcpy(c.V, p, dk * sizeof(float), cudaMemcpyHostToDevice));
+  SGEP_CUDA_TRY(cudaMemcpy(c.S, p + dk * sizeof(float), dk * sizeof(float), cudaMemcpyHostToDevice));
+  c.t = hd.t;
+  c.debug_valid = 0;
+  return SGEP_OK;
+}
+
+int64_t sgep_step_count(sgep_t h) { return h ? h->t : -1; }
+
+double sgep_eta_at(sgep_t h, int64_t t) { return h ? schedule_eta(h->cfg, t) : 0.0; }
+
+int sgep_path(sgep_t h) { return h ? h->path : SGEP_EINVAL; }
+
+int64_t sgep_launch_count(sgep_t h) { return h ? h->launches : -1; }
+
+int sgep_debug_products(sgep_t h, float* AV, float* BV) {
+  if (!h || !AV || !BV) return fail(SGEP_EINVAL, "NULL argument");
+  Ctx& c = *h;
+  const size_t dk = (size_t)c.d * c.k;
+  if (c.path == SGEP_PATH_CLUSTER) {
+    if (!c.cl_pending) return fail(SGEP_ESTATE, "no pending products (call right after sgep_step)");
+    SGEP_CUDA_TRY(cudaDeviceSynchronize());
+    return cluster_products(c, AV, BV, (cudaStream_t)0);
+  }
+  SGEP_CUDA_TRY(cudaDeviceSynchronize());
+  SGEP_CUDA_TRY(cudaMemcpy(AV, c.acc, dk * sizeof(float), cudaMemcpyDeviceToHost));
+  if (c.b_is_identity) {
+    std::memset(BV, 0, dk * sizeof(float));  // B = I: B_t V is not formed
+  } else {
+    SGEP_CUDA_TRY(cudaMemcpy(BV, c.acc + dk, dk * sizeof(float), cudaMemcpyDeviceToHost));
+  }
+  return SGEP_OK;
+}
+
+int sgep_debug_update(sgep_t h, float* grad, double* terms) {
+  if (!h || !grad || !terms) return fail(SGEP_EINVAL, "NULL argument");
+  Ctx& c = *h;
+  if (!c.cfg.debug) return fail(SGEP_ESTATE, "handle was created with debug = 0");
+  int rc = complete(c, (cudaStream_t)0);
+  if (rc) return rc;
+  if (!c.debug_valid) return fail(SGEP_ESTATE, "no completed step since the state was set");
+  const size_t dk = (size_t)c.d * c.k;
+  const int k = c.k;
+  SGEP_CUDA_TRY(cudaMemcpy(grad, c.grad, dk * sizeof(float), cudaMemcpyDeviceToHost));
+  std::vector<float> g(2 * k * k + 2 * k);
+  SGEP_CUDA_TRY(cudaMemcpy(g.data(), c.gram, g.size() * sizeof(float), cudaMemcpyDeviceToHost));
+  for (int i = 0; i < 2 * k * k + k; ++i) terms[i] = g[i];
+  return SGEP_OK;
+}
+
+const char* sgep_strerror(int status) {
+  switch (status) {
+    case SGEP_OK: return "ok";
+    case SGEP_EINVAL: return "invalid argument";
+    case SGEP_ENOMEM: return "out of memory";
+    case SGEP_ECUDA: return "CUDA error";
+    case SGEP_ETIMEOUT: return "device wait timed out";
+    case SGEP_ENONFINITE: return "non-finite values";
+    case SGEP_ELAUNCH: return "launch configuration not possible";
+    case SGEP_ESTATE: return "bad state";
+    case SGEP_ENOTSUP: return "not supported";
+    default: return "unknown status";
+  }
+}
+
+const char* sgep_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,224 @@
+"""ctypes binding of libsgep (include/sgep.h): the same entry points, argument
+marshalling only. Every step of the method runs in the library's CUDA kernels;
+there is no Python or CPU fallback. If libsgep.so is missing the first call
+raises RuntimeError.
+
+Tensors are passed as raw pointers: `data_ptr()` of torch tensors (device
+memory) or numpy arrays (host memory), and streams as
+`torch.cuda.current_stream().cuda_stream`.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsgep.so")
+HEADER = os.path.join(os.path.dirname(_PKG), "include", "sgep.h")
+
+SGEP_OK, SGEP_EINVAL, SGEP_ENOMEM, SGEP_ECUDA = 0, -1, -2, -3
+SGEP_ETIMEOUT, SGEP_ENONFINITE, SGEP_ELAUNCH, SGEP_ESTATE, SGEP_ENOTSUP = -4, -5, -6, -7, -8
+SGEP_PCA, SGEP_CCA, SGEP_PLS, SGEP_LDA = 0, 1, 2, 3
+SGEP_F32, SGEP_BF16 = 0, 1
+SGEP_SCHED_CONST, SGEP_SCHED_HOLD_HARMONIC, SGEP_SCHED_WARMUP_HARMONIC = 0, 1, 2
+SGEP_PATH_AUTO, SGEP_PATH_GENERIC, SGEP_PATH_CLUSTER, SGEP_PATH_TC = 0, 1, 2, 3
+
+
+class sgep_config(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int32), ("dtype", ctypes.c_int32),
+        ("d_x", ctypes.c_int64), ("d_y", ctypes.c_int64),
+        ("k", ctypes.c_int32), ("n_classes", ctypes.c_int32),
+        ("eta0", ctypes.c_float), ("gamma0", ctypes.c_float),
+        ("rho", ctypes.c_float), ("eps_B", ctypes.c_float),
+        ("schedule", ctypes.c_int32), ("split_AB", ctypes.c_int32),
+        ("t_c", ctypes.c_int64), ("T", ctypes.c_int64), ("eta_T", ctypes.c_float),
+        ("path", ctypes.c_int32), ("seed", ctypes.c_uint64), ("max_b", ctypes.c_int64),
+        ("debug", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7),
+    ]
+
+
+class SgepError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        super().__init__(f"{where}: status {status} ({detail})")
+        self.status = status
+
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "sgep_config_default": (ctypes.c_int, [ctypes.POINTER(sgep_config)]),
+    "sgep_init": (ctypes.c_int, [ctypes.POINTER(sgep_config), ctypes.POINTER(_P)]),
+    "sgep_destroy": (ctypes.c_int, [_P]),
+    "sgep_step": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, _P]),
+    "sgep_step_many": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int64, _P]),
+    "sgep_sync": (ctypes.c_int, [_P, _P]),
+    "sgep_get_V": (ctypes.c_int, [_P, _P, ctypes.c_int, _P]),
+    "sgep_get_S": (ctypes.c_int, [_P, _P, ctypes.c_int, _P]),
+    "sgep_set_V": (ctypes.c_int, [_P, _P, ctypes.c_int, _P]),
+    "sgep_set_VS": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
+    "sgep_get_eigenvalues": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, _P, _P]),
+    "sgep_get_state": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_size_t)]),
+    "sgep_set_state": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
+    "sgep_step_count": (ctypes.c_int64, [_P]),
+    "sgep_eta_at": (ctypes.c_double, [_P, ctypes.c_int64]),
+    "sgep_path": (ctypes.c_int, [_P]),
+    "sgep_launch_count": (ctypes.c_int64, [_P]),
+    "sgep_debug_products": (ctypes.c_int, [_P, _P, _P]),
+    "sgep_debug_update": (ctypes.c_int, [_P, _P, _P]),
+    "sgep_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "sgep_last_error": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libsgep.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def header_functions() -> list[str]:
+    """Names of every function declared in include/sgep.h."""
+    with open(HEADER) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sgep_[a-zA-Z_0-9]+)\s*\(", text)))
+
+
+def check(status: int, where: str) -> int:
+    if status < 0:
+        detail = lib().sgep_last_error().decode() or lib().sgep_strerror(status).decode()
+        raise SgepError(status, where, detail)
+    return status
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):          # torch.Tensor
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):            # numpy.ndarray
+        return x.ctypes.data
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+# ---- thin wrappers with the ABI's names --------------------------------------
+
+def sgep_config_default(**overrides) -> sgep_config:
+    cfg = sgep_config()
+    check(lib().sgep_config_default(ctypes.byref(cfg)), "sgep_config_default")
+    for k, v in overrides.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def sgep_init(cfg: sgep_config) -> int:
+    h = _P()
+    check(lib().sgep_init(ctypes.byref(cfg), ctypes.byref(h)), "sgep_init")
+    return h.value
+
+
+def sgep_destroy(h) -> None:
+    check(lib().sgep_destroy(h), "sgep_destroy")
+
+
+def sgep_step(h, X, Y=None, labels=None, b=None, stream=None) -> None:
+    if b is None:
+        b = X.shape[0]
+    check(lib().sgep_step(h, _ptr(X), _ptr(Y), _ptr(labels), int(b), _stream(stream)), "sgep_step")
+
+
+def sgep_step_many(h, X, Y, b, nsteps, labels=None, stream=None) -> None:
+    check(lib().sgep_step_many(h, _ptr(X), _ptr(Y), _ptr(labels), int(b), int(nsteps),
+                               _stream(stream)), "sgep_step_many")
+
+
+def sgep_sync(h, stream=None) -> None:
+    check(lib().sgep_sync(h, _stream(stream)), "sgep_sync")
+
+
+def sgep_get_V(h, out, on_device: bool, stream=None) -> None:
+    check(lib().sgep_get_V(h, _ptr(out), int(on_device), _stream(stream)), "sgep_get_V")
+
+
+def sgep_get_S(h, out, on_device: bool, stream=None) -> None:
+    check(lib().sgep_get_S(h, _ptr(out), int(on_device), _stream(stream)), "sgep_get_S")
+
+
+def sgep_set_V(h, V, on_device: bool, stream=None) -> None:
+    check(lib().sgep_set_V(h, _ptr(V), int(on_device), _stream(stream)), "sgep_set_V")
+
+
+def sgep_set_VS(h, V, S, on_device: bool, stream=None) -> None:
+    check(lib().sgep_set_VS(h, _ptr(V), _ptr(S), int(on_device), _stream(stream)), "sgep_set_VS")
+
+
+def sgep_get_eigenvalues(h, X, Y, n, out, labels=None, stream=None) -> None:
+    check(lib().sgep_get_eigenvalues(h, _ptr(X), _ptr(Y), _ptr(labels), int(n), _ptr(out),
+                                     _stream(stream)), "sgep_get_eigenvalues")
+
+
+def sgep_get_state(h) -> bytes:
+    n = ctypes.c_size_t(0)
+    check(lib().sgep_get_state(h, None, ctypes.byref(n)), "sgep_get_state")
+    buf = ctypes.create_string_buffer(n.value)
+    check(lib().sgep_get_state(h, buf, ctypes.byref(n)), "sgep_get_state")
+    return buf.raw[: n.value]
+
+
+def sgep_set_state(h, blob: bytes) -> None:
+    check(lib().sgep_set_state(h, blob, len(blob)), "sgep_set_state")
+
+
+def sgep_step_count(h) -> int:
+    return int(lib().sgep_step_count(h))
+
+
+def sgep_eta_at(h, t: int) -> float:
+    return float(lib().sgep_eta_at(h, int(t)))
+
+
+def sgep_path(h) -> int:
+    return check(lib().sgep_path(h), "sgep_path")
+
+
+def sgep_launch_count(h) -> int:
+    return int(lib().sgep_launch_count(h))
+
+
+def sgep_debug_products(h, AV, BV) -> None:
+    check(lib().sgep_debug_products(h, _ptr(AV), _ptr(BV)), "sgep_debug_products")
+
+
+def sgep_debug_update(h, grad, terms) -> None:
+    check(lib().sgep_debug_update(h, _ptr(grad), _ptr(terms)), "sgep_debug_update")
+
+
+def sgep_strerror(status: int) -> str:
+    return lib().sgep_strerror(status).decode()
+
+
+def sgep_last_error() -> str:
+    return lib().sgep_last_error().decode()

@@ -1,0 +1,101 @@
+"""A small object wrapper around the C handle (marshalling only)."""
+from __future__ import annotations
+
+import numpy as np
+
+from . import sgep as _s
+
+
+class Solver:
+    """Owns one sgep handle. Inputs are torch CUDA tensors (row-major samples)."""
+
+    def __init__(self, **cfg):
+        self.cfg = _s.sgep_config_default(**cfg)
+        self.h = _s.sgep_init(self.cfg)
+        self.d = self.cfg.d_x + self.cfg.d_y
+        self.k = self.cfg.k
+
+    def close(self):
+        if self.h:
+            _s.sgep_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @staticmethod
+    def _cur_stream():
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+
+    def step(self, X, Y=None, b=None):
+        _s.sgep_step(self.h, X, Y, None, X.shape[0] if b is None else b, self._cur_stream())
+
+    def step_many(self, X, Y, b, nsteps):
+        _s.sgep_step_many(self.h, X, Y, b, nsteps, None, self._cur_stream())
+
+    def sync(self):
+        _s.sgep_sync(self.h, self._cur_stream())
+
+    def V(self) -> np.ndarray:
+        out = np.empty((self.d, self.k), dtype=np.float32)
+        _s.sgep_get_V(self.h, out, False, self._cur_stream())
+        return out
+
+    def S(self) -> np.ndarray:
+        out = np.empty((self.d, self.k), dtype=np.float32)
+        _s.sgep_get_S(self.h, out, False, self._cur_stream())
+        return out
+
+    def set_V(self, V, S=None):
+        V = np.ascontiguousarray(V, dtype=np.float32)
+        if S is None:
+            _s.sgep_set_V(self.h, V, False, self._cur_stream())
+        else:
+            S = np.ascontiguousarray(S, dtype=np.float32)
+            _s.sgep_set_VS(self.h, V, S, False, self._cur_stream())
+
+    def eigenvalues(self, X, Y=None) -> np.ndarray:
+        out = np.empty(self.k, dtype=np.float64)
+        _s.sgep_get_eigenvalues(self.h, X, Y, X.shape[0], out, None, self._cur_stream())
+        return out
+
+    def products(self):
+        AV = np.empty((self.d, self.k), dtype=np.float32)
+        BV = np.empty((self.d, self.k), dtype=np.float32)
+        _s.sgep_debug_products(self.h, AV, BV)
+        return AV, BV
+
+    def update_terms(self):
+        grad = np.empty((self.d, self.k), dtype=np.float32)
+        terms = np.empty(2 * self.k * self.k + self.k, dtype=np.float64)
+        _s.sgep_debug_update(self.h, grad, terms)
+        k = self.k
+        return grad, terms[:k * k].reshape(k, k), terms[k * k:2 * k * k].reshape(k, k), terms[2 * k * k:]
+
+    @property
+    def t(self) -> int:
+        return _s.sgep_step_count(self.h)
+
+    @property
+    def launches(self) -> int:
+        return _s.sgep_launch_count(self.h)
+
+    @property
+    def path(self) -> int:
+        return _s.sgep_path(self.h)
+
+    def state(self) -> bytes:
+        return _s.sgep_get_state(self.h)
+
+    def load_state(self, blob: bytes):
+        _s.sgep_set_state(self.h, blob)

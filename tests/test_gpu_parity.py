@@ -1,0 +1,127 @@
+"""GPU parity: the library's CUDA path against the FP64 oracle on identical seeded inputs.
+
+One step from an identical, unconverged state (so the update is not dominated by
+cancellation) is compared term by term: A_t V and B_t V (the minibatch products), the
+k x k terms, the update direction and the new V and [Bv]. The bar for FP32 is a relative
+error of 1e-5 (update direction relative to the magnitude of its reward and penalty
+terms). Shapes cover several tiles with ragged tails, single players, odd batch sizes and
+the full 1024-dimensional workload."""
+import numpy as np
+import pytest
+
+import synth
+from gpu_util import STEP_TOL, step_errors
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+from paper_2206_04993_gb300 import Solver, sgep as S  # noqa: E402
+
+KINDS = {"pca": S.SGEP_PCA, "cca": S.SGEP_CCA, "pls": S.SGEP_PLS}
+
+
+def _data(kind, dx, dy, b, seed):
+    rng = np.random.default_rng(seed)
+    if kind == "pca":
+        model = synth.planted_pca(dx, np.linspace(4, 1, min(8, dx)), seed=seed)
+        return synth.draw_pca_rows(model, b, batch=seed), None
+    r = max(1, min(8, dx, dy))
+    model = synth.planted_cca(dx, dy, np.linspace(0.9, 0.3, r), seed=seed)
+    X, Y = synth.draw_rows(model, b, batch=seed)
+    return X + 0.1 * rng.standard_normal(X.shape), Y
+
+
+def _state(d, k, seed, kind):
+    V = synth.random_unit_columns(d, k, seed=seed)
+    # [Bv] away from B v so that every clipped and penalty term is exercised
+    S_ = V * 0.8 + 0.05 * synth.random_unit_columns(d, k, seed=seed + 1)
+    return V, S_
+
+
+def _solver(kind, dx, dy, k, path, dtype="f32", **kw):
+    return Solver(kind=KINDS[kind], d_x=dx, d_y=(0 if kind == "pca" else dy), k=k,
+                  dtype=S.SGEP_BF16 if dtype == "bf16" else S.SGEP_F32, path=path,
+                  debug=1, max_b=kw.pop("max_b", 4096), **kw)
+
+
+SHAPES = [
+    # kind, d_x, d_y, k, b
+    ("cca", 32, 32, 4, 256),
+    ("cca", 512, 512, 16, 1024),
+    ("cca", 37, 29, 3, 101),
+    ("cca", 5, 3, 1, 2),
+    ("cca", 70, 130, 17, 333),
+    ("cca", 300, 200, 64, 64),
+    ("cca", 1000, 24, 8, 67),
+    ("pca", 100, 0, 5, 77),
+    ("pca", 1, 0, 1, 9),
+    ("pls", 40, 60, 6, 50),
+]
+
+
+@pytest.mark.parametrize("path", [S.SGEP_PATH_GENERIC])
+@pytest.mark.parametrize("kind,dx,dy,k,b", SHAPES)
+def test_single_step_matches_oracle(kind, dx, dy, k, b, path):
+    X, Y = _data(kind, dx, dy, b, seed=dx + 7 * k + b)
+    d = dx + (0 if kind == "pca" else dy)
+    V0, S0 = _state(d, k, seed=b, kind=kind)
+    with _solver(kind, dx, dy, k, path, eta0=0.3, gamma0=0.4, rho=1e-3) as s:
+        err = step_errors(s, V0, S0, X, Y, kind, 0.3, 0.4, 1e-3)
+    for name, e in err.items():
+        assert e <= STEP_TOL, (name, e, err)
+
+
+@pytest.mark.parametrize("path", [S.SGEP_PATH_GENERIC])
+def test_single_step_shared_batch_and_ridge(path):
+    X, Y = _data("cca", 48, 40, 200, seed=3)
+    V0, S0 = _state(88, 6, seed=5, kind="cca")
+    with _solver("cca", 48, 40, 6, path, eta0=0.2, gamma0=1.0, rho=1e-6, split_AB=0, eps_B=0.05) as s:
+        err = step_errors(s, V0, S0, X, Y, "cca", 0.2, 1.0, 1e-6, split=False, eps_B=0.05)
+    for name, e in err.items():
+        assert e <= STEP_TOL, (name, e, err)
+
+
+@pytest.mark.parametrize("path", [S.SGEP_PATH_GENERIC])
+def test_single_step_bf16_inputs(path):
+    """BF16 minibatch values (the GPU reads bf16, the oracle the same values in FP64);
+    accumulation is FP32, so the same bar applies."""
+    X, Y = _data("cca", 96, 80, 160, seed=9)
+    V0, S0 = _state(176, 8, seed=2, kind="cca")
+    with _solver("cca", 96, 80, 8, path, dtype="bf16", eta0=0.3, gamma0=0.5, rho=1e-4) as s:
+        err = step_errors(s, V0, S0, X, Y, "cca", 0.3, 0.5, 1e-4, dtype="bf16")
+    for name, e in err.items():
+        assert e <= STEP_TOL, (name, e, err)
+
+
+@pytest.mark.parametrize("path", [S.SGEP_PATH_GENERIC])
+def test_clipping_active(path):
+    """<v_j, [Bv]_j> below rho for some players: the clipped denominator is used."""
+    X, Y = _data("cca", 20, 20, 64, seed=4)
+    V0, _ = _state(40, 5, seed=8, kind="cca")
+    S0 = -0.5 * V0
+    with _solver("cca", 20, 20, 5, path, eta0=0.05, gamma0=0.3, rho=0.2) as s:
+        err = step_errors(s, V0, S0, X, Y, "cca", 0.05, 0.3, 0.2)
+    for name, e in err.items():
+        assert e <= STEP_TOL, (name, e, err)
+
+
+@pytest.mark.parametrize("path", [S.SGEP_PATH_GENERIC])
+def test_twenty_steps_track_oracle(path):
+    """Twenty consecutive steps on the 64-dimensional workload stay within 1e-4 of the
+    oracle run on the same minibatch sequence (FP32 rounding compounds slowly)."""
+    from oracle import eg
+    cfg = synth.config_c1()
+    Xall, Yall = cfg["X"].astype(np.float32), cfg["Y"].astype(np.float32)
+    V = synth.random_unit_columns(64, 4, seed=0)
+    Vr, Sr = V.astype(np.float64), V.astype(np.float64)
+    with _solver("cca", 32, 32, 4, path, eta0=cfg["eta0"], gamma0=cfg["gamma0"], rho=cfg["rho"]) as s:
+        s.set_V(V.astype(np.float32))
+        for t in range(1, 21):
+            idx = synth.finite_dataset_indices(10_000, 256, t)
+            X, Y = Xall[idx], Yall[idx]
+            s.step(torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda())
+            Vr, Sr = eg.eg_step(Vr, Sr, *eg.cca_ops(X, Y), cfg["eta0"], cfg["gamma0"], cfg["rho"])
+        Vg, Sg = s.V(), s.S()
+        assert s.t == 20
+    assert np.linalg.norm(Vg - Vr) / np.linalg.norm(Vr) < 1e-4
+    assert np.linalg.norm(Sg - Sr) / np.linalg.norm(Sr) < 1e-4
