@@ -192,6 +192,40 @@ int64_t sgep_launch_count(sgep_t h);
 int sgep_debug_products(sgep_t h, float* AV, float* BV);
 int sgep_debug_update(sgep_t h, float* grad, double* terms);
 
+/* ---- allocation-free step ----------------------------------------------- */
+/* The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory themselves: plugins inside a host application
+ * that owns the GPU's memory through its own pool and only hands out fixed
+ * buffers, services that must keep their device footprint constant after
+ * start-up, and tight loops where cudaMalloc/cudaFree (which can synchronise
+ * the whole device) are not allowed.
+ *
+ * sgep_step_noalloc performs the same iteration as sgep_step on the generic
+ * path, for a problem described by `cfg` (kind, dtype, d_x, d_y, k, rho,
+ * eps_B, split_AB, step-size schedule; path, seed, max_b and debug are
+ * ignored), starting from the caller's state V and S = [Bv] (device, d x k
+ * row-major float) and writing the new state to V_out and S_out (device,
+ * d x k; they may be the same buffers as V and S). `t` (>= 1) is the
+ * iteration number that selects eta_t from the schedule. X and Y are as for
+ * sgep_step. It never calls cudaMalloc or cudaFree: the temporaries of the
+ * step live in one fixed array of SGEP_NOALLOC_SCRATCH_BYTES in device memory,
+ * which every GPU that loads this library keeps until the process exits.
+ * A shape needs 4*(2k^2 + 2k + 2bk + 3dk) bytes plus a few hundred bytes of
+ * alignment; larger shapes are rejected with SGEP_EINVAL and a message.
+ *  - The first call on each device looks up the device address of the array
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before starting any stream capture.
+ *  - Every call on a device shares the one array, which keeps the contents
+ *    of the previous call (the call clears what must start at zero). Calls
+ *    whose work overlaps on the GPU (other streams, other host threads) race
+ *    on it and corrupt each other's results: serialise them.
+ *  - Asynchronous on `stream`; non-finite values are not reported (inspect
+ *    V_out). Errors: SGEP_EINVAL, SGEP_ECUDA. */
+#define SGEP_NOALLOC_SCRATCH_BYTES 4194304
+int sgep_step_noalloc(const sgep_config* cfg, const void* X, const void* Y, int64_t b,
+                      const float* V, const float* S, float* V_out, float* S_out,
+                      int64_t t, void* stream);
+
 /* Human-readable name of a status code (static string). */
 const char* sgep_strerror(int status);
 

@@ -66,6 +66,8 @@ _SIGS = {
     "sgep_launch_count": (ctypes.c_int64, [_P]),
     "sgep_debug_products": (ctypes.c_int, [_P, _P, _P]),
     "sgep_debug_update": (ctypes.c_int, [_P, _P, _P]),
+    "sgep_step_noalloc": (ctypes.c_int, [ctypes.POINTER(sgep_config), _P, _P, ctypes.c_int64,
+                                         _P, _P, _P, _P, ctypes.c_int64, _P]),
     "sgep_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "sgep_last_error": (ctypes.c_char_p, []),
 }
@@ -214,6 +216,12 @@ def sgep_debug_products(h, AV, BV) -> None:
 
 def sgep_debug_update(h, grad, terms) -> None:
     check(lib().sgep_debug_update(h, _ptr(grad), _ptr(terms)), "sgep_debug_update")
+
+
+def sgep_step_noalloc(cfg: sgep_config, X, Y, b, V, S, V_out, S_out, t, stream=None) -> None:
+    check(lib().sgep_step_noalloc(ctypes.byref(cfg), _ptr(X), _ptr(Y), int(b), _ptr(V), _ptr(S),
+                                  _ptr(V_out), _ptr(S_out), int(t), _stream(stream)),
+          "sgep_step_noalloc")
 
 
 def sgep_strerror(status: int) -> str:
