@@ -52,6 +52,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--pool-rows", type=int, default=0, help="override the resident row pool")
     return p.parse_args()
 
 
@@ -217,6 +218,8 @@ def run_native(args):
     from paper_2206_04993_gb300 import Solver, sgep
 
     name, dtype, pool_rows = WORKLOADS[args.workload]
+    if args.pool_rows:
+        pool_rows = args.pool_rows
     cfg = getattr(synth, name)(seed=rank)
     model = cfg["model"]
     b, k = cfg["b"], cfg["k"]

@@ -31,11 +31,18 @@ struct Ctx {
   double* rq = nullptr;    // 2k doubles: Rayleigh numerator / denominator sums
   int* dflag = nullptr;    // device error word: bit 0 non-finite, bit 1 timeout
 
-  // cluster path
-  float* cl_state = nullptr;   // extra buffers owned by the cluster path
+  // cluster path: ping-pong state buffers and three accumulator slots
+  float* cl_V[2] = {nullptr, nullptr};
+  float* cl_S[2] = {nullptr, nullptr};
+  float* cl_acc = nullptr;     // 3 slots of 2 x d x k
+  int cl_cur = 0;              // state buffer holding V_t, [Bv]_t
+  int cl_slot = 0;             // accumulator slot written by the most recent step
   int cl_pending = 0;          // products of one step are waiting for their update
-  float cl_eta = 0.f, cl_gamma = 0.f;
-  int cl_parity = 0;           // which accumulator slot the next step writes
+  float cl_eta = 0.f, cl_gamma = 0.f;  // step sizes of the pending update
+  int cl_size = 8;             // CTAs per cluster
+  int cl_x = 4;                // CTAs of a cluster on X columns (rest on Y)
+  int cl_wx = 0, cl_wy = 0, cl_wmax = 0;  // column-slice widths
+  size_t cl_smem = 0;
 
   int64_t t = 0;       // iterations applied (Alg. 2's t)
   int64_t launches = 0; // kernels launched

@@ -12,6 +12,7 @@
 
 #include <algorithm>
 
+#include "eg_math.cuh"
 #include "internal.h"
 
 namespace sgep {
@@ -247,30 +248,6 @@ __global__ void __launch_bounds__(kThreads) k_gram(const float* __restrict__ V,
   if (tid < k) atomicAdd(&gram[2 * kk + tid], gb);
 }
 
-// Coefficients of the matrix form of Eq. (update), from the k x k terms:
-//   s_j = max(G_jj, rho); c_i = sum_{j<i} a_ij G_ij / s_j; T_ji = b_i a_ij / s_j (j < i)
-//   grad_i = b_i A_t v_i - (a_i - c_i) B_t v_i - sum_{j<i} T_ji [Bv]_j
-// (reward minus penalty with y_j = v_j / sqrt(s_j) and [By]_j = [Bv]_j / sqrt(s_j)).
-__device__ void coefficients(const float* __restrict__ gram, int k, float rho, float* coef_b,
-                             float* coef_ac, float* T) {
-  const int kk = k * k;
-  const float* a = gram;
-  const float* G = gram + kk;
-  const float* bd = gram + 2 * kk;
-  for (int p = threadIdx.x; p < kk; p += blockDim.x) {
-    const int j = p / k, i = p % k;  // T[j*k + i]
-    float t = 0.f;
-    if (j < i) t = bd[i] * a[i * k + j] / fmaxf(G[j * k + j], rho);
-    T[p] = t;
-  }
-  for (int i = threadIdx.x; i < k; i += blockDim.x) {
-    float c = 0.f;
-    for (int j = 0; j < i; ++j) c += a[i * k + j] * G[i * k + j] / fmaxf(G[j * k + j], rho);
-    coef_b[i] = bd[i];
-    coef_ac[i] = a[i * k + i] - c;
-  }
-}
-
 // k_update: grad, V' = V + eta grad (into Vtmp), S <- S + gamma (B_t V - S), norms^2 of V'.
 __global__ void __launch_bounds__(kThreads) k_update(const float* __restrict__ V, float* __restrict__ S,
                                                      const float* __restrict__ AV,
@@ -286,7 +263,7 @@ __global__ void __launch_bounds__(kThreads) k_update(const float* __restrict__ V
   float* nrm = cac + k;          // k
   const int rows = max(1, kThreads / k);
   float* Ss = nrm + k;           // rows x k
-  coefficients(gram, k, rho, cb, cac, T);
+  eg_coefficients(gram, k, rho, cb, cac, T);
   for (int i = threadIdx.x; i < k; i += blockDim.x) nrm[i] = 0.f;
   __syncthreads();
   const int tid = threadIdx.x;

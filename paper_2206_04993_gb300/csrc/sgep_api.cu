@@ -319,11 +319,14 @@ int sgep_sync(sgep_t h, void* stream) {
   return complete(*h, (cudaStream_t)stream);
 }
 
-static int copy_out(Ctx& c, const float* src, float* out, int on_device, void* stream) {
+// Completes pending work first: the cluster path swaps its state buffers when it does,
+// so the source pointer is read only afterwards.
+static int copy_out(Ctx& c, bool want_S, float* out, int on_device, void* stream) {
   if (!out) return fail(SGEP_EINVAL, "out is NULL");
   cudaStream_t s = (cudaStream_t)stream;
   int rc = complete(c, s);
   if (rc) return rc;
+  const float* src = want_S ? c.S : c.V;
   SGEP_CUDA_TRY(cudaMemcpyAsync(out, src, sizeof(float) * c.d * c.k,
                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
   SGEP_CUDA_TRY(cudaStreamSynchronize(s));
@@ -332,12 +335,12 @@ static int copy_out(Ctx& c, const float* src, float* out, int on_device, void* s
 
 int sgep_get_V(sgep_t h, float* out, int on_device, void* stream) {
   if (!h) return fail(SGEP_EINVAL, "handle is NULL");
-  return copy_out(*h, h->V, out, on_device, stream);
+  return copy_out(*h, false, out, on_device, stream);
 }
 
 int sgep_get_S(sgep_t h, float* out, int on_device, void* stream) {
   if (!h) return fail(SGEP_EINVAL, "handle is NULL");
-  return copy_out(*h, h->S, out, on_device, stream);
+  return copy_out(*h, true, out, on_device, stream);
 }
 
 int sgep_set_VS(sgep_t h, const float* V, const float* S, int on_device, void* stream) {
