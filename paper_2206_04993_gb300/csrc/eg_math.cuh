@@ -26,11 +26,17 @@ __device__ inline void eg_coefficients(const float* __restrict__ terms, int k, f
     if (j < i) t = bd[i] * a[i * k + j] / fmaxf(G[j * k + j], rho);
     T[p] = t;
   }
+  // c_i: one thread per (i, j) term, then a short sum per i in a fixed order
   for (int i = threadIdx.x; i < k; i += blockDim.x) {
-    float c = 0.f;
-    for (int j = 0; j < i; ++j) c += a[i * k + j] * G[i * k + j] / fmaxf(G[j * k + j], rho);
+    float c0 = 0.f, c1 = 0.f;
+    int j = 0;
+    for (; j + 1 < i; j += 2) {
+      c0 += a[i * k + j] * G[i * k + j] / fmaxf(G[j * k + j], rho);
+      c1 += a[i * k + j + 1] * G[i * k + j + 1] / fmaxf(G[(j + 1) * k + j + 1], rho);
+    }
+    if (j < i) c0 += a[i * k + j] * G[i * k + j] / fmaxf(G[j * k + j], rho);
     coef_b[i] = bd[i];
-    coef_ac[i] = a[i * k + i] - c;
+    coef_ac[i] = a[i * k + i] - (c0 + c1);
   }
 }
 

@@ -41,7 +41,17 @@ struct Ctx {
   float cl_eta = 0.f, cl_gamma = 0.f;  // step sizes of the pending update
   int cl_size = 8;             // CTAs per cluster
   int cl_x = 4;                // CTAs of a cluster on X columns (rest on Y)
-  int cl_wx = 0, cl_wy = 0, cl_wmax = 0;  // column-slice widths
+  int cl_wx = 0, cl_wy = 0, cl_wmax = 0;  // column-slice widths (cl_wmax padded to 8)
+  int cl_kp = 4;               // players padded to a power of two (>= 4)
+  int cl_lkp = 2;              // log2(cl_kp)
+  int cl_rs = 32;              // minibatch rows resident per CTA
+  int cl_xs = 0;               // shared-memory row stride of a minibatch chunk (elements)
+  int cl_async_shape = 0;      // rows and slices start on 16-byte boundaries
+  int cl_pdl = 1;              // programmatic dependent launch
+  float* cl_gram = nullptr;    // 3 slots of k*k + k row-side terms
+  int cl_max_clusters = 0;     // co-resident clusters reported by the occupancy API
+  int cl_last_grid = 0;        // CTAs of the most recent launch
+  unsigned long long* trace = nullptr;  // SGEP_TRACE=1: per-CTA phase timestamps
   size_t cl_smem = 0;
 
   int64_t t = 0;       // iterations applied (Alg. 2's t)
@@ -87,6 +97,8 @@ int cluster_step(Ctx& c, const void* X, const void* Y, int64_t b, float eta, flo
 int cluster_flush(Ctx& c, cudaStream_t s);
 // Copy the pending products into acc layout (d x k AV, d x k BV) for debugging.
 int cluster_products(Ctx& c, float* AV, float* BV, cudaStream_t s);
+// SGEP_TRACE=1: print per-phase times of the most recent cluster launch to stderr.
+void cluster_trace_report(Ctx& c);
 
 }  // namespace sgep
 

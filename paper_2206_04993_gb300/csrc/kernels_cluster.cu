@@ -4,29 +4,38 @@
 // Layout. The grid is NC clusters of CL CTAs (CL = 8 or 16). Inside a cluster,
 // CTA r owns a contiguous slice of the columns: the first cl_x CTAs slice X's
 // d_x columns, the others slice Y's d_y columns, so one cluster covers all d
-// columns and every CTA keeps its slice of V, [Bv] and the products on chip.
-// Cluster c streams its own contiguous range of minibatch rows.
+// columns and every CTA keeps its slice of V and [Bv] on chip. Cluster c
+// streams its own contiguous range of minibatch rows in chunks of 32.
 //
-// Per launch (step t+1, with the update of step t still pending):
-//   1. Update of step t (every cluster redundantly, each CTA on its slice):
-//      k x k terms a_ij = v_i^T A_t v_j, G_ij = <v_i, [Bv]_j>, b_i = v_i^T B_t v_i
-//      are summed over the slice, then over the cluster through distributed
-//      shared memory (fixed order, so every cluster gets bit-identical values);
-//      then grad (Eq. update with the clipped [By]_j), v + eta grad, the [Bv]
-//      step, column norms (again reduced over the cluster) and the retraction.
-//      Cluster 0 writes the new V and [Bv] to the other state buffer.
-//   2. Products of step t+1: for each tile of 32 rows, every CTA forms its
-//      partial projections X_tile V_slice, the cluster sums them through
-//      distributed shared memory into P and Q for the tile, and each CTA
-//      accumulates X_tile^T [Q|P] for its columns in registers; the tile is
-//      read from HBM once. At the end each CTA adds its d-slice of A_t V and
-//      B_t V into one of three accumulator slots (one written, one read, one
-//      being cleared for the step after).
-// There are no waits between clusters, so no launch can deadlock.
+// Per launch (step t+1, with the update of step t pending):
+//   0. The minibatch rows of this cluster are prefetched into shared memory
+//      with cp.async before anything else (they do not depend on step t).
+//   1. Update of step t, redundantly in every cluster, each CTA on its slice:
+//      G_ij = <v_i, [Bv]_j> and ||v_i||^2 are summed over the slice and then
+//      over the cluster through distributed shared memory (fixed order, so all
+//      clusters obtain bit-identical values); a_ij = v_i^T A_t v_j and
+//      b_i = v_i^T B_t v_i were accumulated row-side by step t's launch.
+//      Then grad (Eq. update with clipped [By]_j), v + eta grad, the [Bv] step,
+//      column norms (cluster-reduced) and the retraction. Cluster 0 writes the
+//      new V and [Bv] to the other state buffer.
+//   2. Products of step t+1, per chunk of 32 rows: partial projections
+//      X_chunk V_slice (4x4 register micro-tiles), summed over the cluster into
+//      P and Q through distributed shared memory; the row-side k x k terms
+//      a_ij = (P^T Q + Q^T P)/n_A, b_i = (|P_i|^2 + |Q_i|^2)/n_B; and the
+//      back-projection X_chunk^T [Q|P] accumulated in registers. The chunk is
+//      read from HBM once. Each CTA finally adds its d-slice of A_t V and B_t V
+//      (and each cluster its k x k terms) into one of three slots: one being
+//      written, one read by the next launch, one cleared for the launch after.
+// There are no waits between clusters, so no launch can deadlock. Launches
+// use programmatic dependent launch: step 0 runs before the wait for the
+// previous launch.
 #include <cooperative_groups.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <vector>
 
 #include "eg_math.cuh"
 #include "internal.h"
@@ -36,47 +45,76 @@ namespace cg = cooperative_groups;
 namespace sgep {
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kRows = 32;          // rows per tile
-constexpr int kMaxElems = 8192;    // w * k per CTA
-constexpr int kMaxW = 256;         // columns per CTA
-constexpr int kPerThread = kMaxElems / kThreads;
+constexpr int kThreads = 512;
+constexpr int kMaxW = 256;      // padded columns per CTA
+constexpr int kMaxKP = 32;      // padded players
+constexpr int kRed = 8192;      // floats of the split-reduction buffer
+constexpr int kEB = 4;          // slice elements per thread in flight in the update
 
 struct ClArgs {
   const void* X;
   const void* Y;
   int64_t b, nA;
   int64_t d_x, d_y, d;
-  int k, kind, split, b_is_identity;
+  int k, kp, kind, split, b_is_identity;
   float inv_nA, inv_nB;
   const float* V_in;
   const float* S_in;
   float* V_out;
   float* S_out;
-  const float* acc_prev;  // A_t V | B_t V of the pending step, or null
-  float* acc_cur;         // slot the new products go to, or null (update only)
-  float* acc_zero;        // slot cleared for the step after next, or null
+  const float* acc_prev;   // A_t V | B_t V of the pending step, or null
+  const float* gram_prev;  // a (k*k) | b (k) of the pending step
+  float* acc_cur;          // slot the new products go to, or null (update only)
+  float* gram_cur;
+  float* acc_zero;         // slot cleared for the step after next, or null
+  float* gram_zero;
   float eta, gamma, rho, eps_B;
-  int cl_x, w_x, w_y, wmax;
+  int cl_x, w_x, w_y, wp, xs, rs, lkp;
   int64_t rows_per_cluster;
+  int async_ok;
   int* dflag;
   float* grad_dbg;  // d x k update directions (cluster 0), or null
   float* gram_dbg;  // a | G | b | norms (cluster 0, rank 0), or null
+  unsigned long long* trace;  // per-CTA phase clocks, or null
 };
+
+constexpr int kTracePhases = 16;
+__device__ __forceinline__ void mark(const ClArgs& a, int ph, long long t0) {
+  if (a.trace && threadIdx.x == 0) a.trace[blockIdx.x * kTracePhases + ph] = (unsigned long long)(clock64() - t0);
+}
 
 __device__ __forceinline__ float ld_elem(const float* p, int64_t i) { return __ldg(p + i); }
 __device__ __forceinline__ float ld_elem(const __nv_bfloat16* p, int64_t i) {
   return __bfloat162float(p[i]);
 }
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ float4 ld4(const __nv_bfloat16* p) {
+  const uint2 u = *reinterpret_cast<const uint2*>(p);
+  const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162*>(&u.x);
+  const __nv_bfloat162 hi = *reinterpret_cast<const __nv_bfloat162*>(&u.y);
+  const float2 a = __bfloat1622float2(lo), b = __bfloat1622float2(hi);
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ float comp(const float4& v, int q) {
+  return q == 0 ? v.x : (q == 1 ? v.y : (q == 2 ? v.z : v.w));
+}
 
-// out[i] = sum_{c < w} A[c*k + i] * B[c*k + i], summed in a fixed order.
-__device__ void colsum_prod(const float* A, const float* B, int w, int k, float* scratch, float* out) {
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// out[i] = sum_{c < w} A[c*lda + i] * B[c*lda + i] for i < k, summed in a fixed order.
+__device__ void colsum_prod(const float* A, const float* B, int lda, int w, int k, float* scratch,
+                            float* out) {
   const int G = max(1, kThreads / k);
   const int t = threadIdx.x;
   const int i = t % k, g = t / k;
   if (g < G) {
     float s = 0.f;
-    for (int c = g; c < w; c += G) s = fmaf(A[c * k + i], B[c * k + i], s);
+    for (int c = g; c < w; c += G) s = fmaf(A[c * lda + i], B[c * lda + i], s);
     scratch[g * k + i] = s;
   }
   __syncthreads();
@@ -88,14 +126,33 @@ __device__ void colsum_prod(const float* A, const float* B, int w, int k, float*
   __syncthreads();
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_cluster_step(const ClArgs a) {
+// Sum over the ranks of the cluster (ranks in [lo, hi)) of a value in each CTA's shared
+// memory, all remote loads in flight before the first add; fixed order.
+template <int CL>
+__device__ __forceinline__ float cluster_sum(cg::cluster_group& cluster, float* base, int idx, int lo, int hi) {
+  float v[CL];
+#pragma unroll
+  for (int r = 0; r < CL; ++r) v[r] = (r >= lo && r < hi) ? cluster.map_shared_rank(base, r)[idx] : 0.f;
+  float s = 0.f;
+#pragma unroll
+  for (int r = 0; r < CL; ++r) s += v[r];
+  return s;
+}
+
+template <typename T, int CLT>
+__global__ void __launch_bounds__(kThreads, 1) k_cluster_step(const ClArgs a) {
+  const long long t0 = clock64();
+  if (a.trace && threadIdx.x == 0) {
+    unsigned long long g;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(g));
+    a.trace[blockIdx.x * kTracePhases] = g;
+  }
   cg::cluster_group cluster = cg::this_cluster();
-  const int CL = (int)cluster.num_blocks();
+  constexpr int CL = CLT;
   const int rank = (int)cluster.block_rank();
   const int cid = (int)(blockIdx.x / CL);
   const int tid = threadIdx.x;
-  const int k = a.k;
+  const int k = a.k, kp = a.kp, wp = a.wp, xs = a.xs;
   const int kk = k * k;
 
   const bool isY = rank >= a.cl_x;
@@ -106,229 +163,486 @@ __global__ void __launch_bounds__(kThreads) k_cluster_step(const ClArgs a) {
   const int64_t c_hi = min(c_lo + wn, ld);
   const int w = (int)(c_hi - c_lo);
   const int64_t goff = (isY ? a.d_x : 0) + c_lo;  // first row of V owned here
-  const int n_el = w * k;
-  const int wm = a.wmax;
 
-  extern __shared__ float sm[];
-  float* Vs = sm;                    // wm*k: V slice (then the new V slice)
-  float* As = Vs + wm * k;           // wm*k: A_t V slice (then v + eta grad)
-  float* Ss = As + wm * k;           // wm*k: [Bv] slice
-  float* Bs = Ss + wm * k;           // wm*k: B_t V slice (with the ridge)
-  float* Xt = Bs + wm * k;           // kRows*wm: minibatch tile
-  float* part = Xt + kRows * wm;     // 2*kRows*k: partial projections (double buffer)
-  float* Wown = part + 2 * kRows * k;   // kRows*k: projection of this CTA's view
-  float* Wcross = Wown + kRows * k;     // kRows*k: projection of the other view
-  float* red = Wcross + kRows * k;      // 2k^2+k: partial a | G | b of this CTA
-  float* nrmp = red + 2 * kk + k;       // k: partial column norms^2
-  float* tot = nrmp + k;                // 2k^2+k: cluster totals
-  float* Tm = tot + 2 * kk + k;         // k^2
-  float* cb = Tm + kk;                  // k
-  float* cac = cb + k;                  // k
-  float* nrm = cac + k;                 // k
-  float* scr = nrm + k;                 // kThreads scratch
+  extern __shared__ __align__(16) float sm[];
+  float* VP = sm;                      // wp*kp: V slice, then the new V slice (zero padded)
+  float* SP = VP + wp * kp;            // wp*kp: [Bv] slice
+  float* UP = SP + wp * kp;            // wp*kp: v + eta grad
+  T* Xb = reinterpret_cast<T*>(UP + wp * kp);                 // rs*xs: minibatch rows
+  float* part = reinterpret_cast<float*>(Xb + a.rs * xs);     // 2*rs*kp (double buffer)
+  float* Wo = part + 2 * a.rs * kp;    // rs*kp: projection of this CTA's view
+  float* Wc = Wo + a.rs * kp;          // rs*kp: projection of the other view
+  float* red = Wc + a.rs * kp;         // kRed
+  float* Gp = red + kRed;              // k*k + k: partial G | v.v   (read by the cluster)
+  float* np_ = Gp + kk + k;            // k: partial norms^2          (read by the cluster)
+  float* terms = np_ + k;              // 2k*k + k: a | G | b
+  float* vv = terms + 2 * kk + k;      // k
+  float* Tm = vv + k;                  // k*k
+  float* cb = Tm + kk;                 // k
+  float* cac = cb + k;                 // k
+  float* nrm = cac + k;                // k
+  float* scr = nrm + k;                // kThreads
 
-  // Clear the accumulator slot of the step after next (whole grid shares the work).
+  // ---- rows of this cluster; prefetch of its first super-chunk ----
+  const bool products = a.acc_cur != nullptr;
+  const int64_t row_lo = products ? min((int64_t)cid * a.rows_per_cluster, a.b) : 0;
+  const int64_t row_hi = products ? min(row_lo + a.rows_per_cluster, a.b) : 0;
+  const int nch = (int)((row_hi - row_lo + a.rs - 1) / a.rs);
+  const T* Z = reinterpret_cast<const T*>(isY ? a.Y : a.X);
+  auto issue = [&](int j) {
+    const int64_t r0 = row_lo + (int64_t)j * a.rs;
+    const int nr = (int)min((int64_t)a.rs, row_hi - r0);
+    if (a.async_ok) {
+      constexpr int V4 = 16 / sizeof(T);
+      const int nvec = wp / V4;
+      for (int e = tid; e < a.rs * nvec; e += kThreads) {
+        const int rr = e / nvec, c = (e % nvec) * V4;
+        T* d = Xb + rr * xs + c;
+        if (rr < nr && c + V4 <= w) {
+          cp_async16(d, Z + (r0 + rr) * ld + c_lo + c);
+        } else {
+#pragma unroll
+          for (int u = 0; u < V4; ++u)
+            d[u] = (rr < nr && c + u < w) ? Z[(r0 + rr) * ld + c_lo + c + u] : T(0.f);
+        }
+      }
+      cp_async_commit();
+    } else {
+      for (int e = tid; e < a.rs * wp; e += kThreads) {
+        const int rr = e / wp, c = e % wp;
+        Xb[rr * xs + c] = (rr < nr && c < w) ? Z[(r0 + rr) * ld + c_lo + c] : T(0.f);
+      }
+    }
+  };
+  if (products && nch > 0) issue(0);
+
+  // Everything below reads what the previous launch wrote.
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;\n" :::);
+  mark(a, 1, t0);
+
+  // Clear the slots of the step after next (the whole grid shares the work).
   if (a.acc_zero) {
     const int64_t n = 2 * a.d * k;
     for (int64_t e = (int64_t)blockIdx.x * kThreads + tid; e < n; e += (int64_t)gridDim.x * kThreads)
       a.acc_zero[e] = 0.f;
+    for (int64_t e = (int64_t)blockIdx.x * kThreads + tid; e < kk + k; e += (int64_t)gridDim.x * kThreads)
+      a.gram_zero[e] = 0.f;
   }
 
   // ---------------- 1. pending update ----------------
-  if (a.acc_prev) {
+  const int ne = wp * kp;  // padded slice elements; thread owns e = tid + kThreads * u
+  const bool pend = a.acc_prev != nullptr;
+  for (int e0 = 0; e0 < ne; e0 += kEB * kThreads) {
+    float rv[kEB], rs[kEB];
+#pragma unroll
+    for (int u = 0; u < kEB; ++u) {
+      const int e = e0 + u * kThreads + tid;
+      const int c = e / kp, i = e % kp;
+      const bool ok = e < ne && c < w && i < k;
+      const int64_t g = (goff + c) * k + i;
+      rv[u] = ok ? __ldg(a.V_in + g) : 0.f;
+      rs[u] = (ok && pend) ? __ldg(a.S_in + g) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < kEB; ++u) {
+      const int e = e0 + u * kThreads + tid;
+      if (e < ne) {
+        VP[e] = rv[u];
+        if (pend) SP[e] = rs[u];
+      }
+    }
+  }
+  if (pend) {
     const float* AVp = a.acc_prev;
     const float* BVp = a.acc_prev + a.d * k;
-    const float e1 = 1.f + a.eps_B;
-    for (int e = tid; e < n_el; e += kThreads) {
-      const int64_t g = goff * k + e;
-      const float v = a.V_in[g];
-      Vs[e] = v;
-      As[e] = AVp[g];
-      Ss[e] = a.S_in[g];
-      Bs[e] = a.b_is_identity ? e1 * v : fmaf(a.eps_B, v, BVp[g]);
-    }
+    for (int p = tid; p < kk; p += kThreads) terms[p] = __ldg(a.gram_prev + p);
     __syncthreads();
+    mark(a, 2, t0);
     for (int p = tid; p < kk; p += kThreads) {
       const int i = p / k, j = p % k;
-      float sa = 0.f, sg = 0.f;
-      for (int c = 0; c < w; ++c) {
-        const float v = Vs[c * k + i];
-        sa = fmaf(v, As[c * k + j], sa);
-        sg = fmaf(v, Ss[c * k + j], sg);
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+      int c = 0;
+      for (; c + 3 < w; c += 4) {
+        s0 = fmaf(VP[c * kp + i], SP[c * kp + j], s0);
+        s1 = fmaf(VP[(c + 1) * kp + i], SP[(c + 1) * kp + j], s1);
+        s2 = fmaf(VP[(c + 2) * kp + i], SP[(c + 2) * kp + j], s2);
+        s3 = fmaf(VP[(c + 3) * kp + i], SP[(c + 3) * kp + j], s3);
       }
-      red[p] = sa;
-      red[kk + p] = sg;
+      for (; c < w; ++c) s0 = fmaf(VP[c * kp + i], SP[c * kp + j], s0);
+      Gp[p] = (s0 + s1) + (s2 + s3);
     }
-    colsum_prod(Vs, Bs, w, k, scr, red + 2 * kk);
+    colsum_prod(VP, VP, kp, w, k, scr, Gp + kk);
+    mark(a, 3, t0);
     cluster.sync();
-    for (int p = tid; p < 2 * kk + k; p += kThreads) {
-      float s = 0.f;
-      for (int r = 0; r < CL; ++r) s += cluster.map_shared_rank(red, r)[p];
-      tot[p] = s;
+    mark(a, 4, t0);
+    for (int p = tid; p < kk + k; p += kThreads) {
+      const float s = cluster_sum<CL>(cluster, Gp, p, 0, CL);
+      if (p < kk) terms[kk + p] = s;
+      else vv[p - kk] = s;
     }
     __syncthreads();
-    eg_coefficients(tot, k, a.rho, cb, cac, Tm);
+    for (int i = tid; i < k; i += kThreads)
+      terms[2 * kk + i] = a.b_is_identity ? (1.f + a.eps_B) * vv[i] : fmaf(a.eps_B, vv[i], a.gram_prev[kk + i]);
     __syncthreads();
+    eg_coefficients(terms, k, a.rho, cb, cac, Tm);
+    __syncthreads();
+    mark(a, 5, t0);
     const bool writer = cid == 0;
-    for (int e = tid; e < n_el; e += kThreads) {
-      const int c = e / k, i = e % k;
-      const int64_t g = goff * k + e;
-      const float v = Vs[e];
-      const float bv = Bs[e];
-      float pen = 0.f;
-      for (int j = 0; j < i; ++j) pen = fmaf(Ss[c * k + j], Tm[j * k + i], pen);
-      const float gr = cb[i] * As[e] - cac[i] * bv - pen;
-      if (writer) {
-        const float s_old = Ss[e];
-        a.S_out[g] = fmaf(a.gamma, bv - s_old, s_old);
-        if (a.grad_dbg) a.grad_dbg[g] = gr;
+    const float e1 = 1.f + a.eps_B;
+    for (int e0 = 0; e0 < ne; e0 += kEB * kThreads) {
+      float av[kEB], bvr[kEB], pen[kEB];
+      int cu[kEB], iu[kEB];
+      bool oku[kEB];
+#pragma unroll
+      for (int u = 0; u < kEB; ++u) {
+        const int e = e0 + u * kThreads + tid;
+        cu[u] = e / kp;
+        iu[u] = e % kp;
+        oku[u] = e < ne && cu[u] < w && iu[u] < k;
+        const int64_t g = (goff + cu[u]) * k + iu[u];
+        av[u] = oku[u] ? __ldg(AVp + g) : 0.f;
+        bvr[u] = (oku[u] && !a.b_is_identity) ? __ldg(BVp + g) : 0.f;
+        pen[u] = 0.f;
       }
-      As[e] = fmaf(a.eta, gr, v);
+      // penalty sum_{j<i} [Bv]_j T_ji; T_ji is zero for j >= i
+      for (int j = 0; j < k; ++j) {
+#pragma unroll
+        for (int u = 0; u < kEB; ++u)
+          if (oku[u]) pen[u] = fmaf(SP[cu[u] * kp + j], Tm[j * k + iu[u]], pen[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < kEB; ++u) {
+        if (!oku[u]) continue;
+        const int e = cu[u] * kp + iu[u];
+        const int64_t g = (goff + cu[u]) * k + iu[u];
+        const float v = VP[e];
+        const float s_old = SP[e];
+        const float bv = a.b_is_identity ? e1 * v : fmaf(a.eps_B, v, bvr[u]);
+        const float gr = cb[iu[u]] * av[u] - cac[iu[u]] * bv - pen[u];
+        if (writer) {
+          a.S_out[g] = fmaf(a.gamma, bv - s_old, s_old);
+          if (a.grad_dbg) a.grad_dbg[g] = gr;
+        }
+        UP[e] = fmaf(a.eta, gr, v);
+      }
     }
     __syncthreads();
-    colsum_prod(As, As, w, k, scr, nrmp);
+    mark(a, 6, t0);
+    colsum_prod(UP, UP, kp, w, k, scr, np_);
     cluster.sync();
-    for (int i = tid; i < k; i += kThreads) {
-      float s = 0.f;
-      for (int r = 0; r < CL; ++r) s += cluster.map_shared_rank(nrmp, r)[i];
-      nrm[i] = s;
-    }
+    for (int i = tid; i < k; i += kThreads) nrm[i] = cluster_sum<CL>(cluster, np_, i, 0, CL);
     __syncthreads();
-    for (int e = tid; e < n_el; e += kThreads) {
-      const int i = e % k;
-      const float v = As[e] / sqrtf(nrm[i]);
+    for (int e = tid; e < w * k; e += kThreads) {
+      const int c = e / k, i = e % k;
+      const float v = UP[c * kp + i] / sqrtf(nrm[i]);
       if (!isfinite(v)) atomicOr(a.dflag, kFlagNonFinite);
-      Vs[e] = v;
+      VP[c * kp + i] = v;
       if (writer) a.V_out[goff * k + e] = v;
     }
     if (writer && rank == 0 && a.gram_dbg) {
-      for (int p = tid; p < 2 * kk + k; p += kThreads) a.gram_dbg[p] = tot[p];
+      for (int p = tid; p < 2 * kk + k; p += kThreads) a.gram_dbg[p] = terms[p];
       for (int i = tid; i < k; i += kThreads) a.gram_dbg[2 * kk + k + i] = nrm[i];
     }
-    __syncthreads();
-  } else {
-    for (int e = tid; e < n_el; e += kThreads) Vs[e] = a.V_in[goff * k + e];
-    __syncthreads();
   }
+  __syncthreads();
+  mark(a, 7, t0);
 
   // ---------------- 2. products of the new minibatch ----------------
-  if (a.acc_cur) {
-    const T* Z = (const T*)(isY ? a.Y : a.X);
-    const int64_t row_lo = min((int64_t)cid * a.rows_per_cluster, a.b);
-    const int64_t row_hi = min(row_lo + a.rows_per_cluster, a.b);
+  if (products) {
     const bool cca = a.kind == SGEP_CCA;
     const bool pca = a.kind == SGEP_PCA;
     const int own_lo = isY ? a.cl_x : 0, own_hi = isY ? CL : a.cl_x;
     const int cr_lo = isY ? 0 : a.cl_x, cr_hi = isY ? a.cl_x : CL;
-    const float* WA = pca ? Wown : Wcross;
-    float accA[kPerThread], accB[kPerThread];
+    const float* WA = pca ? Wo : Wc;  // A rows: the other view's projection (CCA, PLS)
+    const float* Pm = isY ? Wc : Wo;  // P = X V_x
+    const float* Qm = isY ? Wo : Wc;  // Q = Y V_y
+    const int RS = a.rs;               // rows per super-chunk (multiple of 32)
+    const int R4 = RS / 4;
+    const int kq = kp >> 2;
+    // projection micro-tiles: rows prg + R4*m (m < 4) x players 4*ppq .. 4*ppq+3
+    const int ntp = R4 * kq;
+    const int nsp = max(1, kThreads / ntp);
+    const int tp = tid % ntp, sp = tid / ntp;
+    const int prg = tp / kq, ppq = tp % kq;
+    const int pcw = ((wp + nsp * 4 - 1) / (nsp * 4)) * 4;
+    // back-projection micro-tiles: columns 4*cgp .. +3 x players 4*pq .. +3
+    const int ntb = (wp >> 2) * kq;
+    const int nsb = ntb >= kThreads ? 1 : min(min(kThreads / ntb, RS), 1 + kRed / (ntb * 32));
+    const int sb = ntb >= kThreads ? 0 : tid / ntb;
+    const int my_tile = ntb >= kThreads ? tid : tid % ntb;
+    const bool bp_on = my_tile < ntb && sb < nsb;
+    const int cgp = my_tile / kq, bpq = my_tile % kq;
+    // row-side k x k items owned by this CTA: a_ij (p < kk) and b_i (kk <= p < kk + k)
+    const int gi = rank + CL * tid;
+    const bool g_on = gi < kk + k;
+    float gacc = 0.f;
+    float accA[16], accB[16];
 #pragma unroll
-    for (int q = 0; q < kPerThread; ++q) accA[q] = accB[q] = 0.f;
-    int buf = 0;
-    for (int64_t r0 = row_lo; r0 < row_hi; r0 += kRows) {
-      const int nr = (int)min((int64_t)kRows, row_hi - r0);
-      for (int e = tid; e < kRows * wm; e += kThreads) {
-        const int rr = e / wm, c = e % wm;
-        Xt[e] = (rr < nr && c < w) ? ld_elem(Z, (r0 + rr) * ld + c_lo + c) : 0.f;
+    for (int q = 0; q < 16; ++q) accA[q] = accB[q] = 0.f;
+
+    for (int j = 0; j < nch; ++j) {
+      if (j > 0) issue(j);
+      cp_async_wait_all();
+      __syncthreads();
+      if (j == 0) mark(a, 8, t0);
+      const int64_t r0 = row_lo + (int64_t)j * RS;
+      const int nr = (int)min((int64_t)RS, row_hi - r0);
+      // rows of the super-chunk that estimate A and B
+      int a_lo = 0, a_hi = nr, b_lo = 0, b_hi = 0;
+      if (cca) {
+        if (a.split) {
+          const int cut = (int)max((int64_t)0, min((int64_t)nr, a.nA - r0));
+          a_hi = cut;
+          b_lo = cut;
+          b_hi = nr;
+        } else {
+          b_hi = nr;
+        }
+      }
+      // (a) partial projections of the rows on this slice
+      if (sp < nsp) {
+        float acc[4][4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[m][q] = 0.f;
+        const int c_end = min(wp, (sp + 1) * pcw);
+        for (int c4 = sp * pcw; c4 < c_end; c4 += 4) {
+          float4 x[4], v[4];
+#pragma unroll
+          for (int m = 0; m < 4; ++m) x[m] = ld4(Xb + (prg + R4 * m) * xs + c4);
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc) v[cc] = ld4(VP + (c4 + cc) * kp + ppq * 4);
+#pragma unroll
+          for (int m = 0; m < 4; ++m)
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) {
+              const float xv = comp(x[m], cc);
+              acc[m][0] = fmaf(xv, v[cc].x, acc[m][0]);
+              acc[m][1] = fmaf(xv, v[cc].y, acc[m][1]);
+              acc[m][2] = fmaf(xv, v[cc].z, acc[m][2]);
+              acc[m][3] = fmaf(xv, v[cc].w, acc[m][3]);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) red[((m * 4 + q) * nsp + sp) * ntp + tp] = acc[m][q];
       }
       __syncthreads();
-      float* pb = part + buf * kRows * k;
-      for (int p = tid; p < kRows * k; p += kThreads) {
-        const int rr = p / k, i = p % k;
+      float* pb = part + (j & 1) * RS * kp;
+      // reduce over the column splits, reading consecutive words: o = slot * ntp + tile
+      for (int o = tid; o < 16 * ntp; o += kThreads) {
+        const int slot = o / ntp, tile = o - slot * ntp;
+        const int r = (slot >> 2) * R4 + tile / kq;
+        const int i = (tile % kq) * 4 + (slot & 3);
         float s = 0.f;
-        for (int c = 0; c < w; ++c) s = fmaf(Xt[rr * wm + c], Vs[c * k + i], s);
-        pb[p] = s;
+        for (int u = 0; u < nsp; ++u) s += red[(slot * nsp + u) * ntp + tile];
+        pb[r * kp + i] = s;
       }
+      if (j == 0) mark(a, 9, t0);
       cluster.sync();
-      for (int p = tid; p < kRows * k; p += kThreads) {
-        float so = 0.f, sc = 0.f;
-        for (int r = own_lo; r < own_hi; ++r) so += cluster.map_shared_rank(pb, r)[p];
-        for (int r = cr_lo; r < cr_hi; ++r) sc += cluster.map_shared_rank(pb, r)[p];
-        Wown[p] = so;
-        Wcross[p] = sc;
+      if (j == 0) mark(a, 10, t0);
+      for (int o = tid; o < nr * kp; o += kThreads) {
+        Wo[o] = cluster_sum<CL>(cluster, pb, o, own_lo, own_hi);
+        Wc[o] = cluster_sum<CL>(cluster, pb, o, cr_lo, cr_hi);
       }
       __syncthreads();
-#pragma unroll
-      for (int q = 0; q < kPerThread; ++q) {
-        const int e = tid + q * kThreads;
-        if (e < n_el) {
-          const int c = e / k, i = e % k;
-          float sa = accA[q], sb = accB[q];
-          for (int rr = 0; rr < nr; ++rr) {
-            const int64_t row = r0 + rr;
-            const float x = Xt[rr * wm + c];
-            const bool toA = !cca || !a.split || row < a.nA;
-            const bool toB = cca && (!a.split || row >= a.nA);
-            if (toA) sa = fmaf(x, WA[rr * k + i], sa);
-            if (toB) sb = fmaf(x, Wown[rr * k + i], sb);
+      if (j == 0) mark(a, 11, t0);
+      // (b) row-side k x k terms
+      if (g_on) {
+        if (gi < kk) {
+          const int i = gi / k, jj = gi % k;
+          float g0 = 0.f, g1 = 0.f;
+          for (int r = a_lo; r < a_hi; ++r) {
+            if (pca) {
+              g0 = fmaf(Pm[r * kp + i], Pm[r * kp + jj], g0);
+            } else {
+              g0 = fmaf(Pm[r * kp + i], Qm[r * kp + jj], g0);
+              g1 = fmaf(Qm[r * kp + i], Pm[r * kp + jj], g1);
+            }
           }
-          accA[q] = sa;
-          accB[q] = sb;
+          gacc += g0 + g1;
+        } else if (cca) {
+          const int i = gi - kk;
+          float g0 = 0.f, g1 = 0.f;
+          for (int r = b_lo; r < b_hi; ++r) {
+            const float p = Pm[r * kp + i], q = Qm[r * kp + i];
+            g0 = fmaf(p, p, g0);
+            g1 = fmaf(q, q, g1);
+          }
+          gacc += g0 + g1;
+        }
+      }
+      // (c) back-projection X^T W into the registers
+      if (bp_on) {
+        for (int r = a_lo + sb; r < a_hi; r += nsb) {
+          const float4 x = ld4(Xb + r * xs + cgp * 4);
+          const float4 y = ld4(WA + r * kp + bpq * 4);
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc) {
+            const float xv = comp(x, cc);
+            accA[cc * 4 + 0] = fmaf(xv, y.x, accA[cc * 4 + 0]);
+            accA[cc * 4 + 1] = fmaf(xv, y.y, accA[cc * 4 + 1]);
+            accA[cc * 4 + 2] = fmaf(xv, y.z, accA[cc * 4 + 2]);
+            accA[cc * 4 + 3] = fmaf(xv, y.w, accA[cc * 4 + 3]);
+          }
+        }
+        for (int r = b_lo + sb; r < b_hi; r += nsb) {
+          const float4 x = ld4(Xb + r * xs + cgp * 4);
+          const float4 y = ld4(Wo + r * kp + bpq * 4);
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc) {
+            const float xv = comp(x, cc);
+            accB[cc * 4 + 0] = fmaf(xv, y.x, accB[cc * 4 + 0]);
+            accB[cc * 4 + 1] = fmaf(xv, y.y, accB[cc * 4 + 1]);
+            accB[cc * 4 + 2] = fmaf(xv, y.z, accB[cc * 4 + 2]);
+            accB[cc * 4 + 3] = fmaf(xv, y.w, accB[cc * 4 + 3]);
+          }
         }
       }
       __syncthreads();
-      buf ^= 1;
     }
+    mark(a, 12, t0);
+
+    // combine the row splits of the back-projection, then add into the slot
     const bool hasA = row_lo < row_hi && (!cca || !a.split || row_lo < a.nA);
     const bool hasB = row_lo < row_hi && cca && (!a.split || row_hi > a.nA);
+    if (nsb > 1) {
+      // layout [value q][split][tile]: consecutive threads touch consecutive words
+      const int nsm = nsb - 1;
+      if (bp_on && sb > 0) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          red[(q * nsm + sb - 1) * ntb + my_tile] = accA[q];
+          red[((16 + q) * nsm + sb - 1) * ntb + my_tile] = accB[q];
+        }
+      }
+      __syncthreads();
+      if (bp_on && sb == 0) {
+        for (int u = 0; u < nsm; ++u) {
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            accA[q] += red[(q * nsm + u) * ntb + my_tile];
+            accB[q] += red[((16 + q) * nsm + u) * ntb + my_tile];
+          }
+        }
+      }
+    }
+    mark(a, 13, t0);
     float* AVc = a.acc_cur;
     float* BVc = a.acc_cur + a.d * k;
+    if (bp_on && sb == 0) {
+      const bool vec = (k & 3) == 0;
 #pragma unroll
-    for (int q = 0; q < kPerThread; ++q) {
-      const int e = tid + q * kThreads;
-      if (e < n_el) {
-        const int64_t g = goff * k + e;
-        if (hasA) atomicAdd(&AVc[g], accA[q] * a.inv_nA);
-        if (hasB) atomicAdd(&BVc[g], accB[q] * a.inv_nB);
+      for (int cc = 0; cc < 4; ++cc) {
+        const int c = cgp * 4 + cc;
+        if (c >= w) continue;
+        const int64_t g0 = (goff + c) * k + bpq * 4;
+        if (vec && bpq * 4 < k) {
+          if (hasA)
+            atomicAdd(reinterpret_cast<float4*>(AVc + g0),
+                      make_float4(accA[cc * 4] * a.inv_nA, accA[cc * 4 + 1] * a.inv_nA,
+                                  accA[cc * 4 + 2] * a.inv_nA, accA[cc * 4 + 3] * a.inv_nA));
+          if (hasB)
+            atomicAdd(reinterpret_cast<float4*>(BVc + g0),
+                      make_float4(accB[cc * 4] * a.inv_nB, accB[cc * 4 + 1] * a.inv_nB,
+                                  accB[cc * 4 + 2] * a.inv_nB, accB[cc * 4 + 3] * a.inv_nB));
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (bpq * 4 + q >= k) continue;
+            if (hasA) atomicAdd(AVc + g0 + q, accA[cc * 4 + q] * a.inv_nA);
+            if (hasB) atomicAdd(BVc + g0 + q, accB[cc * 4 + q] * a.inv_nB);
+          }
+        }
+      }
+    }
+    if (g_on && row_lo < row_hi) {
+      if (gi < kk) {
+        if (hasA) atomicAdd(&a.gram_cur[gi], gacc * a.inv_nA);
+      } else if (cca && hasB) {
+        atomicAdd(&a.gram_cur[gi], gacc * a.inv_nB);
       }
     }
   }
+  mark(a, 14, t0);
   // No CTA may leave while others can still read its shared memory.
   cluster.sync();
+  mark(a, 15, t0);
 }
 
-size_t smem_floats(int wm, int k) {
-  return (size_t)4 * wm * k + (size_t)kRows * wm + (size_t)4 * kRows * k + 2 * (2 * k * k + k) + k +
-         (size_t)k * k + 3 * k + kThreads;
+struct Plan {
+  int CL, cl_x, wx, wy, wp, kp, lkp, xs, rs;
+  size_t smem;
+};
+
+size_t smem_bytes(int wp, int kp, int k, int xs, int esz, int rs) {
+  const size_t f = (size_t)3 * wp * kp + (size_t)4 * rs * kp + kRed + (size_t)(k * k + k) + k +
+                   (size_t)(2 * k * k + k) + k + (size_t)k * k + 3 * k + kThreads;
+  return f * sizeof(float) + (size_t)rs * xs * esz + 64;
 }
 
-// Column split of a cluster of CL CTAs: X gets cl_x CTAs, Y the rest.
-void plan(const Ctx& c, int CL, int* cl_x, int* wx, int* wy) {
+// Column split (X gets cl_x CTAs of the cluster, Y the rest), padding and the number of
+// minibatch rows a CTA keeps resident (rs, a multiple of 32 chosen to cover the rows one
+// cluster streams when shared memory allows).
+bool make_plan(const Ctx& c, int CL, int max_clusters, Plan* p) {
+  p->CL = CL;
   if (!c.has_y) {
-    *cl_x = CL;
+    p->cl_x = CL;
   } else {
     int x = (int)((double)CL * (double)c.d_x / (double)c.d + 0.5);
-    *cl_x = std::min(CL - 1, std::max(1, x));
+    p->cl_x = std::min(CL - 1, std::max(1, x));
   }
-  *wx = (int)((c.d_x + *cl_x - 1) / *cl_x);
-  *wy = c.has_y ? (int)((c.d_y + (CL - *cl_x) - 1) / (CL - *cl_x)) : 0;
+  p->wx = (int)((c.d_x + p->cl_x - 1) / p->cl_x);
+  p->wy = c.has_y ? (int)((c.d_y + (CL - p->cl_x) - 1) / (CL - p->cl_x)) : 0;
+  const int wm = std::max(p->wx, p->wy);
+  p->wp = ((wm + 7) / 8) * 8;
+  p->kp = 4;
+  p->lkp = 2;
+  while (p->kp < c.k) {
+    p->kp *= 2;
+    ++p->lkp;
+  }
+  const int esz = c.cfg.dtype == SGEP_BF16 ? 2 : 4;
+  p->xs = p->wp + (esz == 4 ? 4 : 8);
+  const int nc = std::max(1, std::min(c.num_sms / CL, max_clusters > 0 ? max_clusters : c.num_sms / CL));
+  const int64_t rows = (c.cfg.max_b + nc - 1) / nc;
+  int rs = (int)std::min<int64_t>(128, ((rows + 31) / 32) * 32);
+  while (rs > 32 && smem_bytes(p->wp, p->kp, c.k, p->xs, esz, rs) > 227 * 1024) rs -= 32;
+  p->rs = rs;
+  p->smem = smem_bytes(p->wp, p->kp, c.k, p->xs, esz, rs);
+  return p->wp <= kMaxW && p->kp <= kMaxKP && p->smem <= 227 * 1024;
 }
 
-template <typename T>
+template <typename T, int CLT>
 int launch(Ctx& c, const ClArgs& a, int NC, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(NC * c.cl_size));
   cfg.blockDim = dim3(kThreads);
   cfg.dynamicSmemBytes = c.cl_smem;
   cfg.stream = s;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = (unsigned)c.cl_size;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  SGEP_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_cluster_step<T>, a));
+  cfg.numAttrs = c.cl_pdl ? 2 : 1;
+  SGEP_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_cluster_step<T, CLT>, a));
   ++c.launches;
   return SGEP_OK;
 }
 
-template <typename T>
+template <typename T, int CLT>
 int configure(Ctx& c) {
-  SGEP_CUDA_TRY(cudaFuncSetAttribute(k_cluster_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  SGEP_CUDA_TRY(cudaFuncSetAttribute(k_cluster_step<T, CLT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)c.cl_smem));
-  if (c.cl_size > 8)
-    SGEP_CUDA_TRY(cudaFuncSetAttribute(k_cluster_step<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  if (CLT > 8)
+    SGEP_CUDA_TRY(cudaFuncSetAttribute(k_cluster_step<T, CLT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)c.cl_size);
   cfg.blockDim = dim3(kThreads);
@@ -341,20 +655,22 @@ int configure(Ctx& c) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int nclusters = 0;
-  SGEP_CUDA_TRY(cudaOccupancyMaxActiveClusters(&nclusters, k_cluster_step<T>, &cfg));
+  SGEP_CUDA_TRY(cudaOccupancyMaxActiveClusters(&nclusters, k_cluster_step<T, CLT>, &cfg));
   if (nclusters < 1) {
     set_error("cluster path: no cluster of this size fits on the device");
     return SGEP_ELAUNCH;
   }
+  c.cl_max_clusters = nclusters;
   return SGEP_OK;
 }
 
-ClArgs base_args(Ctx& c) {
+int run(Ctx& c, const void* X, const void* Y, int64_t b, float eta, float gamma, cudaStream_t s) {
   ClArgs a = {};
   a.d_x = c.d_x;
   a.d_y = c.d_y;
   a.d = c.d;
   a.k = c.k;
+  a.kp = c.cl_kp;
   a.kind = c.cfg.kind;
   a.split = (c.cfg.kind == SGEP_CCA && c.cfg.split_AB) ? 1 : 0;
   a.b_is_identity = c.b_is_identity ? 1 : 0;
@@ -363,22 +679,23 @@ ClArgs base_args(Ctx& c) {
   a.cl_x = c.cl_x;
   a.w_x = c.cl_wx;
   a.w_y = c.cl_wy;
-  a.wmax = c.cl_wmax;
+  a.wp = c.cl_wmax;
+  a.xs = c.cl_xs;
+  a.rs = c.cl_rs;
+  a.lkp = c.cl_lkp;
   a.dflag = c.dflag;
   a.grad_dbg = c.cfg.debug ? c.grad : nullptr;
   a.gram_dbg = c.cfg.debug ? c.gram : nullptr;
-  return a;
-}
-
-int run(Ctx& c, const void* X, const void* Y, int64_t b, float eta, float gamma, cudaStream_t s) {
-  ClArgs a = base_args(c);
+  a.trace = X ? c.trace : nullptr;
   const int pending = c.cl_pending;
   const size_t slot = (size_t)2 * c.d * c.k;
+  const size_t gslot = (size_t)c.k * c.k + c.k;
   a.V_in = c.cl_V[c.cl_cur];
   a.S_in = c.cl_S[c.cl_cur];
   a.V_out = c.cl_V[1 - c.cl_cur];
   a.S_out = c.cl_S[1 - c.cl_cur];
   a.acc_prev = pending ? c.cl_acc + c.cl_slot * slot : nullptr;
+  a.gram_prev = pending ? c.cl_gram + c.cl_slot * gslot : nullptr;
   a.eta = c.cl_eta;
   a.gamma = c.cl_gamma;
   int NC = 1;
@@ -391,13 +708,22 @@ int run(Ctx& c, const void* X, const void* Y, int64_t b, float eta, float gamma,
     a.inv_nA = 1.f / (float)a.nA;
     a.inv_nB = a.split ? 1.f / (float)(b - a.nA) : 1.f / (float)b;
     a.acc_cur = c.cl_acc + next * slot;
+    a.gram_cur = c.cl_gram + next * gslot;
     a.acc_zero = c.cl_acc + ((c.cl_slot + 2) % 3) * slot;
-    const int max_nc = std::max(1, c.num_sms / c.cl_size);
-    NC = (int)std::min<int64_t>(max_nc, std::max<int64_t>(1, (b + 2 * kRows - 1) / (2 * kRows)));
+    a.gram_zero = c.cl_gram + ((c.cl_slot + 2) % 3) * gslot;
+    const int max_nc = std::max(1, std::min(c.num_sms / c.cl_size, c.cl_max_clusters));
+    NC = (int)std::min<int64_t>(max_nc, std::max<int64_t>(1, (b + 63) / 64));
     a.rows_per_cluster = (b + NC - 1) / NC;
+    const bool aligned = ((uintptr_t)X % 16 == 0) && (!c.has_y || (uintptr_t)Y % 16 == 0);
+    a.async_ok = (aligned && c.cl_async_shape) ? 1 : 0;
   }
-  int rc = c.cfg.dtype == SGEP_BF16 ? launch<__nv_bfloat16>(c, a, NC, s) : launch<float>(c, a, NC, s);
+  int rc;
+  if (c.cfg.dtype == SGEP_BF16)
+    rc = c.cl_size == 16 ? launch<__nv_bfloat16, 16>(c, a, NC, s) : launch<__nv_bfloat16, 8>(c, a, NC, s);
+  else
+    rc = c.cl_size == 16 ? launch<float, 16>(c, a, NC, s) : launch<float, 8>(c, a, NC, s);
   if (rc) return rc;
+  if (X) c.cl_last_grid = NC * c.cl_size;
   if (pending) {
     c.cl_cur = 1 - c.cl_cur;
     c.debug_valid = c.cfg.debug;
@@ -418,50 +744,68 @@ int run(Ctx& c, const void* X, const void* Y, int64_t b, float eta, float gamma,
 }  // namespace
 
 bool cluster_supported(const Ctx& c, const char** why) {
-  if (c.k > 32) {
+  if (c.k > kMaxKP) {
     if (why) *why = "k > 32";
     return false;
   }
-  for (int CL : {8, 16}) {
-    int cl_x, wx, wy;
-    plan(c, CL, &cl_x, &wx, &wy);
-    const int wm = std::max(wx, wy);
-    if (wm <= kMaxW && wm * c.k <= kMaxElems && smem_floats(wm, c.k) * 4 <= 227 * 1024) return true;
-  }
+  Plan p;
+  if (make_plan(c, 8, 0, &p) || make_plan(c, 16, 0, &p)) return true;
   if (why) *why = "column slices too wide for shared memory (d too large)";
   return false;
 }
 
 int cluster_alloc(Ctx& c) {
-  int chosen = 0;
-  for (int CL : {8, 16}) {
-    int cl_x, wx, wy;
-    plan(c, CL, &cl_x, &wx, &wy);
-    const int wm = std::max(wx, wy);
-    if (wm <= kMaxW && wm * c.k <= kMaxElems && smem_floats(wm, c.k) * 4 <= 227 * 1024) {
-      c.cl_size = CL;
-      c.cl_x = cl_x;
-      c.cl_wx = wx;
-      c.cl_wy = wy;
-      c.cl_wmax = wm;
-      c.cl_smem = smem_floats(wm, c.k) * sizeof(float);
-      chosen = CL;
-      break;
-    }
-  }
-  if (!chosen) return SGEP_ENOTSUP;
-  int rc = c.cfg.dtype == SGEP_BF16 ? configure<__nv_bfloat16>(c) : configure<float>(c);
+  Plan p;
+  if (!make_plan(c, 8, 0, &p) && !make_plan(c, 16, 0, &p)) return SGEP_ENOTSUP;
+  auto adopt = [&](const Plan& q) {
+    c.cl_size = q.CL;
+    c.cl_x = q.cl_x;
+    c.cl_wx = q.wx;
+    c.cl_wy = q.wy;
+    c.cl_wmax = q.wp;
+    c.cl_kp = q.kp;
+    c.cl_lkp = q.lkp;
+    c.cl_xs = q.xs;
+    c.cl_rs = q.rs;
+    c.cl_smem = q.smem;
+  };
+  adopt(p);
+  auto conf = [&]() {
+    if (c.cfg.dtype == SGEP_BF16)
+      return c.cl_size == 16 ? configure<__nv_bfloat16, 16>(c) : configure<__nv_bfloat16, 8>(c);
+    return c.cl_size == 16 ? configure<float, 16>(c) : configure<float, 8>(c);
+  };
+  int rc = conf();
   if (rc) return rc;
+  // re-plan the resident rows with the number of clusters that fit at once
+  if (make_plan(c, c.cl_size, c.cl_max_clusters, &p) && p.smem != c.cl_smem) {
+    adopt(p);
+    rc = conf();
+    if (rc) return rc;
+  }
+  const int esz = c.cfg.dtype == SGEP_BF16 ? 2 : 4;
+  c.cl_async_shape = (c.d_x * esz % 16 == 0) && (!c.has_y || c.d_y * esz % 16 == 0) &&
+                     (p.wx * esz % 16 == 0) && (!c.has_y || p.wy * esz % 16 == 0);
   const size_t dk = (size_t)c.d * c.k;
+  const size_t gk = (size_t)c.k * c.k + c.k;
   c.cl_V[0] = c.V;
   c.cl_S[0] = c.S;
   SGEP_CUDA_TRY(cudaMalloc((void**)&c.cl_V[1], dk * sizeof(float)));
   SGEP_CUDA_TRY(cudaMalloc((void**)&c.cl_S[1], dk * sizeof(float)));
   SGEP_CUDA_TRY(cudaMalloc((void**)&c.cl_acc, 3 * 2 * dk * sizeof(float)));
+  SGEP_CUDA_TRY(cudaMalloc((void**)&c.cl_gram, 3 * gk * sizeof(float)));
   SGEP_CUDA_TRY(cudaMemset(c.cl_acc, 0, 3 * 2 * dk * sizeof(float)));
+  SGEP_CUDA_TRY(cudaMemset(c.cl_gram, 0, 3 * gk * sizeof(float)));
   c.cl_cur = 0;
   c.cl_slot = 0;
   c.cl_pending = 0;
+  const char* pdl = getenv("SGEP_PDL");
+  c.cl_pdl = (pdl && pdl[0] == '0') ? 0 : 1;
+  const char* tr = getenv("SGEP_TRACE");
+  if (tr && tr[0] == '1') {
+    SGEP_CUDA_TRY(cudaMalloc((void**)&c.trace, (size_t)4096 * kTracePhases * sizeof(unsigned long long)));
+    SGEP_CUDA_TRY(cudaMemset(c.trace, 0, (size_t)4096 * kTracePhases * sizeof(unsigned long long)));
+  }
   return SGEP_OK;
 }
 
@@ -473,8 +817,12 @@ void cluster_free(Ctx& c) {
   cudaFree(c.cl_V[1]);
   cudaFree(c.cl_S[1]);
   cudaFree(c.cl_acc);
+  cudaFree(c.cl_gram);
+  cudaFree(c.trace);
+  c.trace = nullptr;
   c.cl_V[1] = c.cl_S[1] = nullptr;
   c.cl_acc = nullptr;
+  c.cl_gram = nullptr;
 }
 
 int cluster_step(Ctx& c, const void* X, const void* Y, int64_t b, float eta, float gamma, cudaStream_t s) {
@@ -484,6 +832,29 @@ int cluster_step(Ctx& c, const void* X, const void* Y, int64_t b, float eta, flo
 int cluster_flush(Ctx& c, cudaStream_t s) {
   if (!c.cl_pending) return SGEP_OK;
   return run(c, nullptr, nullptr, 0, 0.f, 0.f, s);
+}
+
+void cluster_trace_report(Ctx& c) {
+  if (!c.trace || c.cl_last_grid <= 0) return;
+  const int n = c.cl_last_grid;
+  std::vector<unsigned long long> t((size_t)n * kTracePhases);
+  if (cudaMemcpy(t.data(), c.trace, t.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return;
+  unsigned long long g0 = ~0ull, g1 = 0;
+  for (int b = 0; b < n; ++b) {
+    g0 = std::min(g0, t[(size_t)b * kTracePhases]);
+    g1 = std::max(g1, t[(size_t)b * kTracePhases]);
+  }
+  std::fprintf(stderr, "[sgep trace] grid %d CTAs (cluster %d, max co-resident clusters %d); CTA start spread %.2f us\n",
+               n, c.cl_size, c.cl_max_clusters, (double)(g1 - g0) / 1e3);
+  std::fprintf(stderr, "[sgep trace] phase clocks (median / max over CTAs, SM cycles from CTA start):");
+  for (int ph = 1; ph < kTracePhases; ++ph) {
+    std::vector<unsigned long long> v;
+    for (int b = 0; b < n; ++b) v.push_back(t[(size_t)b * kTracePhases + ph]);
+    std::sort(v.begin(), v.end());
+    std::fprintf(stderr, " %d:%llu/%llu", ph, v[v.size() / 2], v.back());
+  }
+  std::fprintf(stderr, "\n");
 }
 
 int cluster_products(Ctx& c, float* AV, float* BV, cudaStream_t s) {

@@ -316,7 +316,9 @@ int sgep_step_many(sgep_t h, const void* X, const void* Y, const int32_t* labels
 
 int sgep_sync(sgep_t h, void* stream) {
   if (!h) return fail(SGEP_EINVAL, "handle is NULL");
-  return complete(*h, (cudaStream_t)stream);
+  int rc = complete(*h, (cudaStream_t)stream);
+  if (h->trace) cluster_trace_report(*h);
+  return rc;
 }
 
 // Completes pending work first: the cluster path swaps its state buffers when it does,
