@@ -37,6 +37,9 @@ WORKLOADS = {
     # name: (synth config function, dtype, pool rows)
     "cca_d1024_k16_b1024_f32": ("config_c2", "f32", 1_000_000),
     "cca_d64_k4_b256_f32": ("config_c1", "f32", 10_000),
+    # activation-like CCA, d_x = d_y = 16384, k = 32, b = 4096, BF16 rows (8 minibatches = 2.1 GB)
+    "cca_d32768_k32_b4096_bf16": ("config_c3", "bf16", 32_768),
+    "cca_d32768_k32_b4096_f32": ("config_c3", "f32", 16_384),
 }
 DEFAULT_WORKLOAD = "cca_d1024_k16_b1024_f32"
 
@@ -139,16 +142,26 @@ def make_pool(cfg, rows, dtype, device, seed=0):
     Wx = torch.from_numpy(model.Wx).float().to(device)
     Wy = torch.from_numpy(model.Wy).float().to(device)
     r = Wx.shape[1]
-    X = torch.empty(rows, model.d_x, device=device)
-    Y = torch.empty(rows, model.d_y, device=device)
-    chunk = 1 << 17
+    tdt = torch.bfloat16 if dtype == "bf16" else torch.float32
+    X = torch.empty(rows, model.d_x, device=device, dtype=tdt)
+    Y = torch.empty(rows, model.d_y, device=device, dtype=tdt)
+    if hasattr(model, "sigma"):
+        sx = sy = None
+    else:
+        sx = torch.from_numpy(np.sqrt(model.Dx)).float().to(device)
+        sy = torch.from_numpy(np.sqrt(model.Dy)).float().to(device)
+    chunk = max(1, min(1 << 17, (1 << 28) // max(model.d_x, 1)))
     for r0 in range(0, rows, chunk):
         n = min(chunk, rows - r0)
         z = torch.randn(n, r, device=device, generator=g)
-        X[r0:r0 + n] = z @ Wx.T + model.sigma * torch.randn(n, model.d_x, device=device, generator=g)
-        Y[r0:r0 + n] = z @ Wy.T + model.sigma * torch.randn(n, model.d_y, device=device, generator=g)
-    if dtype == "bf16":
-        X, Y = X.to(torch.bfloat16), Y.to(torch.bfloat16)
+        ex = torch.randn(n, model.d_x, device=device, generator=g)
+        ey = torch.randn(n, model.d_y, device=device, generator=g)
+        if sx is None:
+            X[r0:r0 + n] = (z @ Wx.T + model.sigma * ex).to(tdt)
+            Y[r0:r0 + n] = (z @ Wy.T + model.sigma * ey).to(tdt)
+        else:
+            X[r0:r0 + n] = (z @ Wx.T + ex * sx).to(tdt)
+            Y[r0:r0 + n] = (z @ Wy.T + ey * sy).to(tdt)
     return X, Y
 
 

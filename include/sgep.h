@@ -192,6 +192,14 @@ int64_t sgep_launch_count(sgep_t h);
 int sgep_debug_products(sgep_t h, float* AV, float* BV);
 int sgep_debug_update(sgep_t h, float* grad, double* terms);
 
+/* Diagnostic of the tensor-core building blocks (TMA loads with 128-byte
+ * swizzle, tcgen05.mma BF16 -> FP32 in tensor memory, tcgen05.ld): runs one
+ * 128 x 64 x 64 product on the current device and writes the largest error
+ * relative to a SIMT FP32 reference into *max_rel_err. mode 0: A K-major;
+ * modes 1 and 2: A MN-major (transposed) with the two descriptor strides in
+ * either order. Allocates its own buffers; synchronous. */
+int sgep_tc_selftest(int mode, double* max_rel_err);
+
 /* ---- allocation-free step ----------------------------------------------- */
 /* The paper has no counterpart to this entry point; it serves callers that
  * cannot allocate device memory themselves: plugins inside a host application

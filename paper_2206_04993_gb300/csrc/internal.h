@@ -1,6 +1,7 @@
 // Internal declarations shared by the host-side ABI and the kernel files.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -54,6 +55,15 @@ struct Ctx {
   unsigned long long* trace = nullptr;  // SGEP_TRACE=1: per-CTA phase timestamps
   size_t cl_smem = 0;
 
+  // tensor-core path
+  __nv_bfloat16* tc_Vt = nullptr;  // 64 x d: BF16 hi/lo pairs of V (transposed)
+  float* tc_PQ = nullptr;          // 2 x max_b x 32: row projections P, Q
+  __nv_bfloat16* tc_Pt = nullptr;  // 64 x max_b: BF16 hi/lo pairs of P (transposed)
+  __nv_bfloat16* tc_Qt = nullptr;
+  float* tc_coef = nullptr;        // k*k + 2k update coefficients
+  int tc_generic_step = 0;         // the last step's shape needed the generic products
+  size_t tc_smem_p = 0, tc_smem_b = 0;
+
   int64_t t = 0;       // iterations applied (Alg. 2's t)
   int64_t launches = 0; // kernels launched
   int debug_valid = 0; // sgep_debug_update has data
@@ -83,8 +93,19 @@ int generic_products(Ctx& c, const void* X, const void* Y, int64_t b, cudaStream
 int generic_update(Ctx& c, float eta, float gamma, cudaStream_t s);
 // Row projections of n rows into PQ (n <= max_b), zeroing PQ first.
 int generic_project(Ctx& c, const void* X, const void* Y, int64_t n, cudaStream_t s);
+// Retraction V <- Vtmp / ||Vtmp|| with the norms in gram (counts the update launch too).
+int generic_normalize(Ctx& c, cudaStream_t s);
 // Rayleigh sums of the n rows in PQ accumulated into rq (double).
 int generic_rayleigh_sums(Ctx& c, int64_t n, cudaStream_t s);
+
+// ---- tensor-core path (kernels_tc.cu) ----
+bool tc_supported(const Ctx& c, const char** why);
+int tc_alloc(Ctx& c);
+void tc_free(Ctx& c);
+// acc <- [A_t V ; B_t V] of a BF16 minibatch on the tensor cores.
+int tc_products(Ctx& c, const void* X, const void* Y, int64_t b, cudaStream_t s);
+// Update from acc with the k x k terms the tensor-core products accumulated.
+int tc_update(Ctx& c, float eta, float gamma, cudaStream_t s);
 
 // ---- cluster path (kernels_cluster.cu) ----
 bool cluster_supported(const Ctx& c, const char** why);

@@ -419,6 +419,14 @@ int generic_update(Ctx& c, float eta, float gamma, cudaStream_t s) {
   return SGEP_OK;
 }
 
+int generic_normalize(Ctx& c, cudaStream_t s) {
+  const int nblocks = (int)std::min<int64_t>((c.d * c.k + 255) / 256, grid_cap(c, 4));
+  k_normalize<<<nblocks, 256, 0, s>>>(c.Vtmp, c.gram, c.V, c.d, c.k, c.dflag);
+  SGEP_CUDA_TRY(cudaGetLastError());
+  c.launches += 2;
+  return SGEP_OK;
+}
+
 int generic_rayleigh_sums(Ctx& c, int64_t n, cudaStream_t s) {
   const int k = c.k;
   const int lanes = std::max(1, 256 / k);

@@ -1,0 +1,836 @@
+// Tensor-core (tcgen05) path of the gamma-EigenGame products for BF16 minibatches
+// with large d, plus a self-test of the MMA operand layouts it relies on.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "eg_math.cuh"
+#include "internal.h"
+#include "tc_common.cuh"
+
+namespace sgep {
+
+// ---------------------------------------------------------------------------
+// Tensor maps (cuTensorMapEncodeTiled through the runtime's driver entry point)
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  });
+  return fn;
+}
+
+// 2-D BF16 row-major matrix [rows][cols] (row stride `ld` elements); boxes of
+// box_rows x box_cols with 128-byte swizzle (box_cols * 2 must be 128).
+int make_map_bf16(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows,
+                  int box_cols) {
+  auto fn = encode_fn();
+  if (!fn) {
+    set_error("cuTensorMapEncodeTiled is not available");
+    return SGEP_ECUDA;
+  }
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return SGEP_ECUDA;
+  }
+  return SGEP_OK;
+}
+
+namespace {
+
+using namespace tc;
+
+__device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
+  return (uint8_t*)(((uintptr_t)p + 1023) & ~(uintptr_t)1023);
+}
+
+// ---------------------------------------------------------------------------
+// Self-test: one 128 x 64 x 64 product through TMA + tcgen05 + TMEM.
+//  mode 0: D[r][n] = sum_k A[r][k] Bt[n][k], A K-major ([128][64] row-major)
+//  mode 1: D[c][n] = sum_r T[r][c] Bt[n][r], A = T^T MN-major (T [64][128] row-major),
+//          descriptor LBO = stride between 64-column groups, SBO = 8-row groups
+//  mode 2: as mode 1 with the two strides exchanged
+// Every address the descriptors can reach stays inside the 32 KB A region.
+__global__ void __launch_bounds__(128) k_tc_selftest(const __grid_constant__ CUtensorMap mapA,
+                                                     const __grid_constant__ CUtensorMap mapB, int mode,
+                                                     float* __restrict__ out, int* flag) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = align1024(smem_raw);
+  uint8_t* As = base;               // 32 KB
+  uint8_t* Bs = base + 32768;       // 8 KB
+  uint64_t* full = (uint64_t*)(base + 40960);
+  uint64_t* done = full + 1;
+  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  int* issued = (int*)(tmem_slot + 1);
+  const int tid = threadIdx.x, warp = tid / 32;
+  if (warp == 0) {
+    tmem_alloc(tmem_slot, 64);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    mbar_init(full, 1);
+    mbar_init(done, 1);
+    fence_mbar_init();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  bool ok = true;
+  if (tid == 0) {
+    mbar_arrive_expect_tx(full, 16384 + 8192);
+    if (mode == 0) {
+      tma_load_2d(As, &mapA, 0, 0, full);
+    } else {
+      tma_load_2d(As, &mapA, 0, 0, full);
+      tma_load_2d(As + 8192, &mapA, 64, 0, full);
+    }
+    tma_load_2d(Bs, &mapB, 0, 0, full);
+    ok = mbar_wait(full, 0);
+    if (ok) {
+      tc_fence_after();
+      const uint32_t idesc = idesc_bf16(128, 64, mode == 0 ? 0 : 1, 0);
+      for (int kk = 0; kk < 4; ++kk) {
+        uint64_t a;
+        if (mode == 0) a = desc_sw128(As + kk * 32, 16, 1024);
+        else if (mode == 1) a = desc_sw128(As + kk * 2048, 8192, 1024);
+        else a = desc_sw128(As + kk * 2048, 1024, 8192);
+        const uint64_t b = desc_sw128(Bs + kk * 32, 16, 1024);
+        mma_bf16(tmem, a, b, idesc, kk > 0 ? 1u : 0u);
+      }
+      mma_commit(done);
+    } else {
+      atomicOr(flag, kFlagTimeout);
+    }
+    *issued = ok ? 1 : 0;
+  }
+  __syncthreads();
+  if (*issued) {
+    const bool ready = mbar_wait(done, 0, 500000000ull);
+    if (!ready) {
+      if ((tid & 31) == 0) atomicOr(flag, kFlagTimeout);
+    } else {
+      tc_fence_after();
+      const int q = warp & 3;
+      float v[32];
+      const int row = 32 * q + (tid & 31);
+      tmem_ld32(tmem + ((uint32_t)(32 * q) << 16), v);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) out[row * 64 + j] = v[j];
+      tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + 32, v);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) out[row * 64 + 32 + j] = v[j];
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 64);
+}
+
+__global__ void k_fill_bf16(__nv_bfloat16* p, int n, uint32_t seed) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    uint32_t h = (uint32_t)i * 2654435761u ^ seed;
+    h ^= h >> 15;
+    h *= 2246822519u;
+    h ^= h >> 13;
+    p[i] = __float2bfloat16(((float)(h & 0xFFFF) / 32768.f) - 1.f);
+  }
+}
+
+__global__ void k_selftest_ref(const __nv_bfloat16* A, const __nv_bfloat16* Bt, int mode, float* ref) {
+  const int m = blockIdx.x, n = threadIdx.x;  // 128 x 64
+  float s = 0.f;
+  for (int kx = 0; kx < 64; ++kx) {
+    const float a = mode == 0 ? __bfloat162float(A[m * 64 + kx]) : __bfloat162float(A[kx * 128 + m]);
+    s = fmaf(a, __bfloat162float(Bt[n * 64 + kx]), s);
+  }
+  ref[m * 64 + n] = s;
+}
+
+
+// ---------------------------------------------------------------------------
+// Products of one BF16 minibatch on the tensor cores.
+//
+// V (FP32) is split per element into a BF16 pair v = hi + lo (hi = bf16(v),
+// lo = bf16(v - hi)), so X V is computed from 2k BF16 columns and summed in FP32;
+// the pair keeps about 16 significant bits of V. The same split is used for the
+// row projections P and Q that feed the back-projection.
+//
+//   k_tc_prep_v   Vt = [hi(V)^T ; lo(V)^T]  (64 x d BF16, players padded to 32)
+//   k_tc_project  P = X V_x, Q = Y V_y      (tcgen05, rows in tiles of 128,
+//                 columns split in S parts; partial tiles added with float4 atomics)
+//   k_tc_prep_w   Pt = [hi(P)^T ; lo(P)^T], Qt likewise (64 x b BF16)
+//   k_tc_backproject  A_t V = [X_A^T Q_A ; Y_A^T P_A] / n_A, B_t V = [X_B^T P_B ; Y_B^T Q_B] / n_B
+//                 (tcgen05 with the row-major minibatch tile read transposed,
+//                 CTAs own 256-column slices, accumulators stay in tensor memory,
+//                 rows streamed last-first so the rows the projection read last are
+//                 still in L2)
+
+constexpr int kTcThreads = 192;     // warp 0: TMA, warp 1: MMA, warps 2-5: epilogue
+constexpr int kP_Stages = 8;        // projection: 24 KB per stage
+constexpr int kB_Stages = 5;        // back-projection: 40 KB per stage
+constexpr int kTcKP = 32;           // players padded to 32 (N = 64 with hi/lo)
+
+struct TcProjArgs {
+  int64_t b, d_x, d_y;
+  int splits;        // column splits per view
+  int64_t cols_per_split;
+  float* P;          // b x 32
+  float* Q;          // b x 32
+  int* dflag;
+};
+
+// V split into BF16 pairs (transposed, players padded to 32) and the d-side terms
+// G_ij = <v_i, [Bv]_j>, vv_i = |v_i|^2 of the update, accumulated per block of 64 rows of V.
+// grid: d/64 blocks of 256 threads. gram layout: a (k*k) | G (k*k) | b (k) | norms (k) | vv (k)
+__global__ void __launch_bounds__(256) k_tc_prep_v(const float* __restrict__ V, const float* __restrict__ S,
+                                                   int64_t d, int k, __nv_bfloat16* __restrict__ Vt,
+                                                   float* __restrict__ gram) {
+  __shared__ float vs[64][kTcKP + 1];
+  __shared__ float ss[64][kTcKP + 1];
+  const int tid = threadIdx.x;
+  const int64_t c0 = (int64_t)blockIdx.x * 64;
+  for (int e = tid; e < 64 * kTcKP; e += 256) {
+    const int r = e / kTcKP, i = e % kTcKP;
+    const bool ok = c0 + r < d && i < k;
+    vs[r][i] = ok ? V[(c0 + r) * k + i] : 0.f;
+    ss[r][i] = ok ? S[(c0 + r) * k + i] : 0.f;
+  }
+  __syncthreads();
+  // transposed BF16 pairs: consecutive threads write consecutive columns
+  for (int e = tid; e < 2 * kTcKP * 64; e += 256) {
+    const int n = e / 64, r = e % 64;
+    if (c0 + r >= d) continue;
+    const float v = vs[r][n % kTcKP];
+    const __nv_bfloat16 hi = __float2bfloat16(v);
+    Vt[(int64_t)n * d + c0 + r] = n < kTcKP ? hi : __float2bfloat16(v - __bfloat162float(hi));
+  }
+  const int kk = k * k;
+  for (int p = tid; p < kk + k; p += 256) {
+    float s0 = 0.f, s1 = 0.f;
+    if (p < kk) {
+      const int i = p / k, j = p % k;
+      for (int r = 0; r < 64; r += 2) {
+        s0 = fmaf(vs[r][i], ss[r][j], s0);
+        s1 = fmaf(vs[r + 1][i], ss[r + 1][j], s1);
+      }
+      atomicAdd(&gram[kk + p], s0 + s1);
+    } else {
+      const int i = p - kk;
+      for (int r = 0; r < 64; r += 2) {
+        s0 = fmaf(vs[r][i], vs[r][i], s0);
+        s1 = fmaf(vs[r + 1][i], vs[r + 1][i], s1);
+      }
+      atomicAdd(&gram[2 * kk + 2 * k + i], s0 + s1);
+    }
+  }
+}
+
+// P, Q split into BF16 pairs (transposed, row stride ldt) and the row-side terms
+// a_ij = sum_A (P_i Q_j + Q_i P_j) / n_A, b_i = sum_B (P_i^2 + Q_i^2) / n_B.
+// grid: b/64 blocks of 256 threads.
+__global__ void __launch_bounds__(256) k_tc_prep_w(const float* __restrict__ P, const float* __restrict__ Q,
+                                                   int64_t b, int64_t ldt, int64_t nA, int k, float inv_nA,
+                                                   float inv_nB, __nv_bfloat16* __restrict__ Pt,
+                                                   __nv_bfloat16* __restrict__ Qt, float* __restrict__ gram) {
+  __shared__ float ps[64][kTcKP + 1];
+  __shared__ float qs[64][kTcKP + 1];
+  const int tid = threadIdx.x;
+  const int64_t r0 = (int64_t)blockIdx.x * 64;
+  for (int e = tid; e < 64 * kTcKP; e += 256) {
+    const int r = e / kTcKP, i = e % kTcKP;
+    const bool ok = r0 + r < b;
+    ps[r][i] = ok ? P[(r0 + r) * kTcKP + i] : 0.f;
+    qs[r][i] = ok ? Q[(r0 + r) * kTcKP + i] : 0.f;
+  }
+  __syncthreads();
+  for (int e = tid; e < 2 * kTcKP * 64; e += 256) {
+    const int n = e / 64, r = e % 64;
+    if (r0 + r >= b) continue;
+    const float p = ps[r][n % kTcKP], q = qs[r][n % kTcKP];
+    const __nv_bfloat16 ph = __float2bfloat16(p), qh = __float2bfloat16(q);
+    Pt[(int64_t)n * ldt + r0 + r] = n < kTcKP ? ph : __float2bfloat16(p - __bfloat162float(ph));
+    Qt[(int64_t)n * ldt + r0 + r] = n < kTcKP ? qh : __float2bfloat16(q - __bfloat162float(qh));
+  }
+  // rows of this block that estimate A and B (the split point is a multiple of 64)
+  const bool rowsA = r0 < nA;
+  const int kk = k * k;
+  for (int p = tid; p < kk + k; p += 256) {
+    float s0 = 0.f, s1 = 0.f;
+    if (p < kk && rowsA) {
+      const int i = p / k, j = p % k;
+      for (int r = 0; r < 64; ++r) {
+        s0 = fmaf(ps[r][i], qs[r][j], s0);
+        s1 = fmaf(qs[r][i], ps[r][j], s1);
+      }
+      atomicAdd(&gram[p], (s0 + s1) * inv_nA);
+    } else if (p >= kk && !rowsA) {
+      const int i = p - kk;
+      for (int r = 0; r < 64; ++r) {
+        s0 = fmaf(ps[r][i], ps[r][i], s0);
+        s1 = fmaf(qs[r][i], qs[r][i], s1);
+      }
+      atomicAdd(&gram[2 * kk + i], (s0 + s1) * inv_nB);
+    }
+  }
+}
+
+// Update of large-d problems (k <= 32): one warp per row c of V, lane i = player i, so every
+// load and store is one 128-byte row; [Bv]_j of the row reach lane i by shuffles. Each block
+// forms the coefficients of Eq. (update) from the k x k terms (with 1/max(G_jj, rho) once per j).
+// Writes v + eta grad to Vtmp, the [Bv] step to S, and adds per-block column sums of
+// (v + eta grad)^2 into the norms. gram: a | G | b | norms | vv.
+__global__ void __launch_bounds__(256) k_tc_update(const float* __restrict__ V, float* __restrict__ S,
+                                                   const float* __restrict__ AV, const float* __restrict__ BV,
+                                                   float* __restrict__ gram, int64_t d, int k, float rho,
+                                                   float eta, float gamma, float eps_B,
+                                                   float* __restrict__ Vtmp, float* __restrict__ grad_out) {
+  __shared__ float T[kTcKP * kTcKP];
+  __shared__ float cb[kTcKP], cac[kTcKP], inv_s[kTcKP];
+  __shared__ float red[8][kTcKP];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int kk = k * k;
+  const float* a = gram;
+  const float* G = gram + kk;
+  if (tid < k) {
+    inv_s[tid] = 1.f / fmaxf(G[tid * k + tid], rho);
+    cb[tid] = fmaf(eps_B, gram[2 * kk + 2 * k + tid], gram[2 * kk + tid]);
+  }
+  __syncthreads();
+  for (int p = tid; p < kk; p += 256) {
+    const int j = p / k, i = p % k;
+    T[j * kTcKP + i] = j < i ? cb[i] * a[i * k + j] * inv_s[j] : 0.f;
+  }
+  if (tid < k) {
+    float c = 0.f;
+    for (int j = 0; j < tid; ++j) c = fmaf(a[tid * k + j] * G[tid * k + j], inv_s[j], c);
+    cac[tid] = a[tid * k + tid] - c;
+  }
+  __syncthreads();
+  const bool on = lane < k;
+  float nr = 0.f;
+  constexpr int U = 4;
+  float v[U], sv[U], av[U], bv[U];
+  int64_t g[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int64_t c = (int64_t)blockIdx.x * (8 * U) + wid + 8 * u;
+    g[u] = c * k + lane;
+    const bool ok = on && c < d;
+    v[u] = ok ? V[g[u]] : 0.f;
+    sv[u] = ok ? S[g[u]] : 0.f;
+    av[u] = ok ? AV[g[u]] : 0.f;
+    bv[u] = ok ? BV[g[u]] : 0.f;
+  }
+  float pen[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) pen[u] = 0.f;
+  for (int j = 0; j < k; ++j) {
+    const float t = T[j * kTcKP + lane];
+#pragma unroll
+    for (int u = 0; u < U; ++u) pen[u] = fmaf(__shfl_sync(0xffffffffu, sv[u], j), t, pen[u]);
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int64_t c = (int64_t)blockIdx.x * (8 * U) + wid + 8 * u;
+    if (!on || c >= d) continue;
+    const float bve = fmaf(eps_B, v[u], bv[u]);
+    const float gr = cb[lane] * av[u] - cac[lane] * bve - pen[u];
+    const float vn = fmaf(eta, gr, v[u]);
+    Vtmp[g[u]] = vn;
+    S[g[u]] = fmaf(gamma, bve - sv[u], sv[u]);
+    if (grad_out) grad_out[g[u]] = gr;
+    nr = fmaf(vn, vn, nr);
+  }
+  red[wid][lane] = nr;
+  __syncthreads();
+  if (tid < k) {
+    float s2 = 0.f;
+    for (int w = 0; w < 8; ++w) s2 += red[w][tid];
+    atomicAdd(&gram[2 * kk + k + tid], s2);
+  }
+}
+
+// v_i <- v'_i / |v'_i|, four elements per thread (k is a multiple of 4 here).
+__global__ void k_tc_normalize(const float* __restrict__ Vtmp, const float* __restrict__ norms,
+                               float* __restrict__ V, int64_t n4, int k, int* dflag) {
+  __shared__ float inv[kTcKP];
+  if (threadIdx.x < k) inv[threadIdx.x] = 1.f / sqrtf(norms[threadIdx.x]);
+  __syncthreads();
+  const float4* src = reinterpret_cast<const float4*>(Vtmp);
+  float4* dst = reinterpret_cast<float4*>(V);
+  bool bad = false;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n4; e += (int64_t)gridDim.x * blockDim.x) {
+    float4 v = src[e];
+    const int i = (int)((e * 4) % k);
+    v.x *= inv[i];
+    v.y *= inv[i + 1];
+    v.z *= inv[i + 2];
+    v.w *= inv[i + 3];
+    bad |= !(isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w));
+    dst[e] = v;
+  }
+  if (bad) atomicOr(dflag, kFlagNonFinite);
+}
+
+// grid: (b/128 row tiles, 2 views, splits)
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_tc_project(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapY,
+                 const __grid_constant__ CUtensorMap mapVt, const TcProjArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = align1024(smem_raw);
+  constexpr int kA = 16384, kB = 8192, kStage = kA + kB;
+  uint64_t* full = (uint64_t*)(base + kP_Stages * kStage);
+  uint64_t* empty = full + kP_Stages;
+  uint64_t* done = empty + kP_Stages;
+  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  int* abort_flag = (int*)(tmem_slot + 1);
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid & 31;
+  const int view = blockIdx.y;
+  const int64_t row0 = (int64_t)blockIdx.x * 128;
+  const int64_t c0 = (int64_t)blockIdx.z * a.cols_per_split;
+  const int nk = (int)(a.cols_per_split / 64);
+  const CUtensorMap* mZ = view ? &mapY : &mapX;
+  const int64_t voff = view ? a.d_x : 0;
+
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, 64);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    for (int s = 0; s < kP_Stages; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, 1);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+    prefetch_tensormap(mZ);
+    prefetch_tensormap(&mapVt);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    const uint64_t keep = policy_evict_last();
+    for (int ks = 0; ks < nk; ++ks) {
+      const int st = ks % kP_Stages;
+      if (ks >= kP_Stages && !mbar_wait(empty + st, ((ks / kP_Stages) - 1) & 1)) {
+        atomicOr(a.dflag, kFlagTimeout);
+        *(volatile int*)abort_flag = 1;
+        break;
+      }
+      if (*(volatile int*)abort_flag) break;
+      uint8_t* sa = base + st * kStage;
+      mbar_arrive_expect_tx(full + st, kStage);
+      tma_load_2d(sa, mZ, (int)(c0 + (int64_t)ks * 64), (int)row0, full + st);
+      tma_load_2d_hint(sa + kA, &mapVt, (int)(voff + c0 + (int64_t)ks * 64), 0, full + st, keep);
+    }
+  } else if (warp == 1 && lane == 0) {
+    const uint32_t idesc = idesc_bf16(128, 64, 0, 0);
+    bool ok = true;
+    for (int ks = 0; ks < nk; ++ks) {
+      const int st = ks % kP_Stages;
+      if (!mbar_wait(full + st, (ks / kP_Stages) & 1)) {
+        atomicOr(a.dflag, kFlagTimeout);
+        *(volatile int*)abort_flag = 1;
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      uint8_t* sa = base + st * kStage;
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+        mma_bf16(tmem, desc_sw128(sa + kk * 32, 16, 1024), desc_sw128(sa + kA + kk * 32, 16, 1024), idesc,
+                 (ks | kk) ? 1u : 0u);
+      mma_commit(empty + st);
+    }
+    if (ok) mma_commit(done);
+    else mbar_arrive(done);
+  } else if (warp >= 2) {
+    const bool ready = mbar_wait(done, 0);
+    tc_fence_after();
+    if (!ready) {
+      if (lane == 0) atomicOr(a.dflag, kFlagTimeout);
+    } else if (!*(volatile int*)abort_flag) {
+      const int q = warp & 3;
+      const int r = 32 * q + lane;
+      float hi[32], lo[32];
+      tmem_ld32(tmem + ((uint32_t)(32 * q) << 16), hi);
+      tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + 32, lo);
+      float* out = (view ? a.Q : a.P) + (row0 + r) * kTcKP;
+      if (row0 + r < a.b) {
+#pragma unroll
+        for (int i = 0; i < kTcKP; i += 4)
+          atomicAdd(reinterpret_cast<float4*>(out + i),
+                    make_float4(hi[i] + lo[i], hi[i + 1] + lo[i + 1], hi[i + 2] + lo[i + 2], hi[i + 3] + lo[i + 3]));
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) tmem_dealloc(tmem, 64);
+}
+
+struct TcBackArgs {
+  int64_t b, nA, d_x, d_y;
+  int k, split, nslice_x;
+  float inv_nA, inv_nB;
+  float* AV;
+  float* BV;
+  int* dflag;
+};
+
+// grid: d/256 column slices (X slices first, then Y slices)
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_tc_backproject(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapY,
+                     const __grid_constant__ CUtensorMap mapPt, const __grid_constant__ CUtensorMap mapQt,
+                     const TcBackArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = align1024(smem_raw);
+  constexpr int kA = 32768, kB = 8192, kStage = kA + kB;
+  uint64_t* full = (uint64_t*)(base + kB_Stages * kStage);
+  uint64_t* empty = full + kB_Stages;
+  uint64_t* done = empty + kB_Stages;
+  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  int* abort_flag = (int*)(tmem_slot + 1);
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid & 31;
+  const bool isY = (int)blockIdx.x >= a.nslice_x;
+  const int64_t c0 = (int64_t)(isY ? blockIdx.x - a.nslice_x : blockIdx.x) * 256;
+  const int64_t goff = (isY ? a.d_x : 0) + c0;
+  const CUtensorMap* mZ = isY ? &mapY : &mapX;
+  // A rows use the other view's projection, B rows this view's
+  const CUtensorMap* mWA = isY ? &mapPt : &mapQt;
+  const CUtensorMap* mWB = isY ? &mapQt : &mapPt;
+  const int nrb = (int)(a.b / 64);
+
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, 256);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    for (int s = 0; s < kB_Stages; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, 1);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+    prefetch_tensormap(mZ);
+    prefetch_tensormap(mWA);
+    prefetch_tensormap(mWB);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    const uint64_t once = policy_evict_first();
+    for (int s = 0; s < nrb; ++s) {
+      const int st = s % kB_Stages;
+      const int64_t r0 = (int64_t)(nrb - 1 - s) * 64;
+      if (s >= kB_Stages && !mbar_wait(empty + st, ((s / kB_Stages) - 1) & 1)) {
+        atomicOr(a.dflag, kFlagTimeout);
+        *(volatile int*)abort_flag = 1;
+        break;
+      }
+      if (*(volatile int*)abort_flag) break;
+      uint8_t* sa = base + st * kStage;
+      const bool rowA = !a.split || r0 < a.nA;
+      mbar_arrive_expect_tx(full + st, kStage);
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        tma_load_2d_hint(sa + j * 8192, mZ, (int)(c0 + 64 * j), (int)r0, full + st, once);
+      tma_load_2d(sa + kA, rowA ? mWA : mWB, (int)r0, 0, full + st);
+    }
+  } else if (warp == 1 && lane == 0) {
+    const uint32_t idesc = idesc_bf16(128, 64, 1, 0);
+    bool ok = true, usedA = false, usedB = false;
+    for (int s = 0; s < nrb; ++s) {
+      const int st = s % kB_Stages;
+      const int64_t r0 = (int64_t)(nrb - 1 - s) * 64;
+      if (!mbar_wait(full + st, (s / kB_Stages) & 1)) {
+        atomicOr(a.dflag, kFlagTimeout);
+        *(volatile int*)abort_flag = 1;
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      uint8_t* sa = base + st * kStage;
+      const bool rowA = !a.split || r0 < a.nA;
+      const uint32_t dbase = tmem + (rowA ? 0u : 128u);
+      const bool used = rowA ? usedA : usedB;
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+          mma_bf16(dbase + 64 * h, desc_sw128(sa + 2 * h * 8192 + kk * 2048, 8192, 1024),
+                   desc_sw128(sa + kA + kk * 32, 16, 1024), idesc, (used || kk) ? 1u : 0u);
+      if (rowA) usedA = true;
+      else usedB = true;
+      mma_commit(empty + st);
+    }
+    if (ok) mma_commit(done);
+    else mbar_arrive(done);
+  } else if (warp >= 2) {
+    const bool ready = mbar_wait(done, 0);
+    tc_fence_after();
+    if (!ready) {
+      if (lane == 0) atomicOr(a.dflag, kFlagTimeout);
+    } else if (!*(volatile int*)abort_flag) {
+      const int q = warp & 3;
+      const int k = a.k;
+#pragma unroll 1
+      for (int which = 0; which < 2; ++which) {
+        float* out = which == 0 ? a.AV : a.BV;
+        const float sc = which == 0 ? a.inv_nA : a.inv_nB;
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+          float hi[32], lo[32];
+          const uint32_t t = tmem + (uint32_t)(which * 128 + 64 * h) + ((uint32_t)(32 * q) << 16);
+          tmem_ld32(t, hi);
+          tmem_ld32(t + 32, lo);
+          const int64_t col = goff + 128 * h + 32 * q + lane;
+          for (int i = 0; i < k; ++i) out[col * k + i] = (hi[i] + lo[i]) * sc;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) tmem_dealloc(tmem, 256);
+}
+
+}  // namespace
+}  // namespace sgep
+
+
+namespace sgep {
+
+bool tc_supported(const Ctx& c, const char** why) {
+  const char* w = nullptr;
+  if (c.cfg.dtype != SGEP_BF16) w = "needs BF16 minibatches";
+  else if (c.cfg.kind != SGEP_CCA) w = "tensor-core path supports CCA";
+  else if (!c.cfg.split_AB) w = "tensor-core path needs split A/B batches";
+  else if (c.d_x != c.d_y) w = "tensor-core path needs d_x == d_y";
+  else if (c.k > kTcKP) w = "k > 32";
+  else if (c.d_x % 256 || c.d_y % 256) w = "d_x and d_y must be multiples of 256";
+  else if (c.cfg.max_b % 128) w = "max_b must be a multiple of 128";
+  if (why) *why = w;
+  return w == nullptr;
+}
+
+int tc_alloc(Ctx& c) {
+  const size_t mb = (size_t)c.cfg.max_b;
+  SGEP_CUDA_TRY(cudaMalloc((void**)&c.tc_Vt, (size_t)2 * kTcKP * c.d * 2));
+  SGEP_CUDA_TRY(cudaMalloc((void**)&c.tc_PQ, 2 * mb * kTcKP * sizeof(float)));
+  SGEP_CUDA_TRY(cudaMalloc((void**)&c.tc_Pt, 2 * kTcKP * mb * 2));
+  SGEP_CUDA_TRY(cudaMalloc((void**)&c.tc_Qt, 2 * kTcKP * mb * 2));
+  SGEP_CUDA_TRY(cudaMalloc((void**)&c.tc_coef, (size_t)(c.k * c.k + 2 * c.k) * sizeof(float)));
+  // the k x k terms gain a slot for |v_i|^2
+  cudaFree(c.gram);
+  c.gram = nullptr;
+  SGEP_CUDA_TRY(cudaMalloc((void**)&c.gram, (size_t)(2 * c.k * c.k + 3 * c.k) * sizeof(float)));
+  const size_t sp = kP_Stages * 24576 + 1024 + 256, sb = kB_Stages * 40960 + 1024 + 256;
+  SGEP_CUDA_TRY(cudaFuncSetAttribute(k_tc_project, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp));
+  SGEP_CUDA_TRY(cudaFuncSetAttribute(k_tc_backproject, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb));
+  c.tc_smem_p = sp;
+  c.tc_smem_b = sb;
+  return SGEP_OK;
+}
+
+void tc_free(Ctx& c) {
+  cudaFree(c.tc_Vt);
+  cudaFree(c.tc_PQ);
+  cudaFree(c.tc_Pt);
+  cudaFree(c.tc_Qt);
+  cudaFree(c.tc_coef);
+  c.tc_coef = nullptr;
+  c.tc_Vt = nullptr;
+  c.tc_PQ = nullptr;
+  c.tc_Pt = c.tc_Qt = nullptr;
+}
+
+int tc_products(Ctx& c, const void* X, const void* Y, int64_t b, cudaStream_t s) {
+  const int split = c.cfg.split_AB ? 1 : 0;
+  const int64_t nA = split ? b / 2 : b;
+  if (b % 128 || ((uintptr_t)X & 15) || ((uintptr_t)Y & 15) || (split && nA % 64)) {
+    c.tc_generic_step = 1;
+    return generic_products(c, X, Y, b, s);
+  }
+  c.tc_generic_step = 0;
+  float* P = c.tc_PQ;
+  float* Q = c.tc_PQ + (size_t)c.cfg.max_b * kTcKP;
+  const int k = c.k;
+  // 1. V split into BF16 pairs, d-side terms; P, Q and the k x k terms cleared
+  SGEP_CUDA_TRY(cudaMemsetAsync(c.tc_PQ, 0, sizeof(float) * 2 * c.cfg.max_b * kTcKP, s));
+  SGEP_CUDA_TRY(cudaMemsetAsync(c.gram, 0, sizeof(float) * (2 * k * k + 3 * k), s));
+  k_tc_prep_v<<<(unsigned)((c.d + 63) / 64), 256, 0, s>>>(c.V, c.S, c.d, k, c.tc_Vt, c.gram);
+  SGEP_CUDA_TRY(cudaGetLastError());
+  CUtensorMap mX1, mY1, mVt, mX2, mY2, mPt, mQt;
+  int rc = make_map_bf16(&mX1, X, b, c.d_x, c.d_x, 128, 64);
+  if (!rc) rc = make_map_bf16(&mY1, Y, b, c.d_y, c.d_y, 128, 64);
+  if (!rc) rc = make_map_bf16(&mVt, c.tc_Vt, 2 * kTcKP, c.d, c.d, 64, 64);
+  if (!rc) rc = make_map_bf16(&mX2, X, b, c.d_x, c.d_x, 64, 64);
+  if (!rc) rc = make_map_bf16(&mY2, Y, b, c.d_y, c.d_y, 64, 64);
+  if (!rc) rc = make_map_bf16(&mPt, c.tc_Pt, 2 * kTcKP, b, c.cfg.max_b, 64, 64);
+  if (!rc) rc = make_map_bf16(&mQt, c.tc_Qt, 2 * kTcKP, b, c.cfg.max_b, 64, 64);
+  if (rc) return rc;
+  // 2. projections
+  {
+    TcProjArgs pa;
+    pa.b = b;
+    pa.d_x = c.d_x;
+    pa.d_y = c.d_y;
+    // column splits so that the grid covers the SMs; each split a multiple of 64 columns
+    int splits = std::max(1, (int)(c.num_sms / (2 * (b / 128))));
+    const int64_t dmin = std::min(c.d_x, c.d_y);
+    while (splits > 1 && (dmin % (64LL * splits) != 0)) --splits;
+    pa.splits = splits;
+    pa.cols_per_split = c.d_x / splits;
+    pa.P = P;
+    pa.Q = Q;
+    pa.dflag = c.dflag;
+    dim3 grid((unsigned)(b / 128), 2, (unsigned)splits);
+    k_tc_project<<<grid, kTcThreads, c.tc_smem_p, s>>>(mX1, mY1, mVt, pa);
+    SGEP_CUDA_TRY(cudaGetLastError());
+  }
+  // 3. P, Q split into BF16 pairs (transposed), row-side terms a and b
+  k_tc_prep_w<<<(unsigned)((b + 63) / 64), 256, 0, s>>>(P, Q, b, c.cfg.max_b, nA, k, 1.f / (float)nA,
+                                                         1.f / (float)(split ? b - nA : b), c.tc_Pt, c.tc_Qt,
+                                                         c.gram);
+  SGEP_CUDA_TRY(cudaGetLastError());
+  // 4. back-projection into acc = [A_t V ; B_t V]
+  {
+    TcBackArgs ba;
+    ba.b = b;
+    ba.nA = nA;
+    ba.d_x = c.d_x;
+    ba.d_y = c.d_y;
+    ba.k = c.k;
+    ba.split = split;
+    ba.nslice_x = (int)(c.d_x / 256);
+    ba.inv_nA = 1.f / (float)nA;
+    ba.inv_nB = 1.f / (float)(split ? b - nA : b);
+    ba.AV = c.acc;
+    ba.BV = c.acc + c.d * c.k;
+    ba.dflag = c.dflag;
+    k_tc_backproject<<<(unsigned)(c.d / 256), kTcThreads, c.tc_smem_b, s>>>(mX2, mY2, mPt, mQt, ba);
+    SGEP_CUDA_TRY(cudaGetLastError());
+  }
+  c.launches += 4;
+  return SGEP_OK;
+}
+
+int tc_update(Ctx& c, float eta, float gamma, cudaStream_t s) {
+  const int k = c.k;
+  k_tc_update<<<(unsigned)((c.d + 31) / 32), 256, 0, s>>>(c.V, c.S, c.acc, c.acc + c.d * k, c.gram, c.d, k,
+                                                          c.cfg.rho, eta, gamma, c.cfg.eps_B, c.Vtmp,
+                                                          c.cfg.debug ? c.grad : nullptr);
+  SGEP_CUDA_TRY(cudaGetLastError());
+  if (k % 4 == 0) {
+    const int64_t n4 = c.d * k / 4;
+    k_tc_normalize<<<(unsigned)std::min<int64_t>((n4 + 255) / 256, 4 * c.num_sms), 256, 0, s>>>(
+        c.Vtmp, c.gram + 2 * k * k + k, c.V, n4, k, c.dflag);
+    SGEP_CUDA_TRY(cudaGetLastError());
+    c.launches += 2;
+    return SGEP_OK;
+  }
+  // k not a multiple of 4: the generic retraction
+  return generic_normalize(c, s);
+}
+
+}  // namespace sgep
+
+using namespace sgep;
+
+extern "C" int sgep_tc_selftest(int mode, double* max_rel_err) {
+  if (!max_rel_err || mode < 0 || mode > 2) {
+    set_error("sgep_tc_selftest: bad arguments");
+    return SGEP_EINVAL;
+  }
+  __nv_bfloat16 *A = nullptr, *Bt = nullptr;
+  float *out = nullptr, *ref = nullptr;
+  int* flag = nullptr;
+  int rc = SGEP_OK;
+  CUtensorMap mA, mB;
+  const size_t smem = 40960 + 64 + 1024;
+  std::vector<float> h_out(128 * 64), h_ref(128 * 64);
+  int h_flag = 0;
+  cudaError_t e = cudaMalloc((void**)&A, 128 * 64 * 2);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&Bt, 64 * 64 * 2);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&out, 128 * 64 * 4);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&ref, 128 * 64 * 4);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&flag, sizeof(int));
+  if (e != cudaSuccess) {
+    rc = cuda_fail(e, "sgep_tc_selftest alloc");
+    goto done;
+  }
+  cudaMemset(flag, 0, sizeof(int));
+  cudaMemset(out, 0, 128 * 64 * 4);
+  k_fill_bf16<<<16, 256>>>(A, 128 * 64, 12345u);
+  k_fill_bf16<<<16, 256>>>(Bt, 64 * 64, 777u);
+  if (mode == 0) rc = make_map_bf16(&mA, A, 128, 64, 64, 128, 64);
+  else rc = make_map_bf16(&mA, A, 64, 128, 128, 64, 64);
+  if (!rc) rc = make_map_bf16(&mB, Bt, 64, 64, 64, 64, 64);
+  if (rc) goto done;
+  e = cudaFuncSetAttribute(k_tc_selftest, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) {
+    rc = cuda_fail(e, "cudaFuncSetAttribute");
+    goto done;
+  }
+  k_tc_selftest<<<1, 128, smem>>>(mA, mB, mode, out, flag);
+  k_selftest_ref<<<128, 64>>>(A, Bt, mode, ref);
+  e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(h_out.data(), out, h_out.size() * 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(h_ref.data(), ref, h_ref.size() * 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&h_flag, flag, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    rc = cuda_fail(e, "sgep_tc_selftest run");
+    goto done;
+  }
+  if (h_flag) {
+    set_error("sgep_tc_selftest: a bounded wait gave up");
+    rc = SGEP_ETIMEOUT;
+    goto done;
+  }
+  {
+    double mx = 0.0, md = 0.0;
+    for (size_t i = 0; i < h_ref.size(); ++i) {
+      mx = std::max(mx, (double)std::fabs(h_ref[i]));
+      md = std::max(md, (double)std::fabs(h_out[i] - h_ref[i]));
+    }
+    *max_rel_err = md / (mx > 0 ? mx : 1.0);
+  }
+done:
+  cudaFree(A);
+  cudaFree(Bt);
+  cudaFree(out);
+  cudaFree(ref);
+  cudaFree(flag);
+  return rc;
+}

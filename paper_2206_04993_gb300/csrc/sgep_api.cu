@@ -83,6 +83,7 @@ static void gaussian_init(std::vector<float>& V, int64_t d, int k, uint64_t seed
 static void free_ctx(sgep_ctx* c) {
   if (!c) return;
   cluster_free(*c);
+  tc_free(*c);
   cudaFree(c->V);
   cudaFree(c->S);
   cudaFree(c->Vtmp);
@@ -223,7 +224,7 @@ int sgep_init(const sgep_config* cfg, sgep_t* out) {
   const char* why = nullptr;
   const bool cl_ok = cluster_supported(*c, &why);
   if (g.path == SGEP_PATH_AUTO) {
-    c->path = cl_ok ? SGEP_PATH_CLUSTER : SGEP_PATH_GENERIC;
+    c->path = cl_ok ? SGEP_PATH_CLUSTER : (tc_supported(*c, nullptr) ? SGEP_PATH_TC : SGEP_PATH_GENERIC);
   } else if (g.path == SGEP_PATH_CLUSTER) {
     if (!cl_ok) {
       free_ctx(c);
@@ -231,13 +232,17 @@ int sgep_init(const sgep_config* cfg, sgep_t* out) {
     }
     c->path = SGEP_PATH_CLUSTER;
   } else if (g.path == SGEP_PATH_TC) {
-    free_ctx(c);
-    return fail(SGEP_ENOTSUP, "tensor-core path is not built yet");
+    const char* tw = nullptr;
+    if (!tc_supported(*c, &tw)) {
+      free_ctx(c);
+      return fail(SGEP_ENOTSUP, std::string("tensor-core path: ") + tw);
+    }
+    c->path = SGEP_PATH_TC;
   } else {
     c->path = SGEP_PATH_GENERIC;
   }
-  if (c->path == SGEP_PATH_CLUSTER) {
-    int rc = cluster_alloc(*c);
+  if (c->path == SGEP_PATH_CLUSTER || c->path == SGEP_PATH_TC) {
+    int rc = c->path == SGEP_PATH_CLUSTER ? cluster_alloc(*c) : tc_alloc(*c);
     if (rc) {
       free_ctx(c);
       return rc;
@@ -281,8 +286,13 @@ static int do_step(Ctx& c, const void* X, const void* Y, int64_t b, cudaStream_t
   if (c.path == SGEP_PATH_CLUSTER) {
     rc = cluster_step(c, X, Y, b, eta, gamma, s);
   } else {
-    rc = generic_products(c, X, Y, b, s);
-    if (!rc) rc = generic_update(c, eta, gamma, s);
+    if (c.path == SGEP_PATH_TC) {
+      rc = tc_products(c, X, Y, b, s);
+      if (!rc) rc = c.tc_generic_step ? generic_update(c, eta, gamma, s) : tc_update(c, eta, gamma, s);
+    } else {
+      rc = generic_products(c, X, Y, b, s);
+      if (!rc) rc = generic_update(c, eta, gamma, s);
+    }
     if (!rc) c.debug_valid = c.cfg.debug;
   }
   if (!rc) c.t = t;

@@ -68,6 +68,7 @@ _SIGS = {
     "sgep_debug_update": (ctypes.c_int, [_P, _P, _P]),
     "sgep_step_noalloc": (ctypes.c_int, [ctypes.POINTER(sgep_config), _P, _P, ctypes.c_int64,
                                          _P, _P, _P, _P, ctypes.c_int64, _P]),
+    "sgep_tc_selftest": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "sgep_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "sgep_last_error": (ctypes.c_char_p, []),
 }
@@ -222,6 +223,12 @@ def sgep_step_noalloc(cfg: sgep_config, X, Y, b, V, S, V_out, S_out, t, stream=N
     check(lib().sgep_step_noalloc(ctypes.byref(cfg), _ptr(X), _ptr(Y), int(b), _ptr(V), _ptr(S),
                                   _ptr(V_out), _ptr(S_out), int(t), _stream(stream)),
           "sgep_step_noalloc")
+
+
+def sgep_tc_selftest(mode: int) -> float:
+    err = ctypes.c_double(-1.0)
+    check(lib().sgep_tc_selftest(int(mode), ctypes.byref(err)), "sgep_tc_selftest")
+    return err.value
 
 
 def sgep_strerror(status: int) -> str:
