@@ -56,7 +56,27 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--pool-rows", type=int, default=0, help="override the resident row pool")
+    p.add_argument("--no-tte", action="store_true", help="skip the time-to-1e-3 measurements")
+    p.add_argument("--no-forms", action="store_true", help="skip the BF16 tensor-core workload")
+    p.add_argument("--tte-max-steps", type=int, default=80_000)
     return p.parse_args()
+
+
+# DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture of the
+# current kernel (profiles/cluster_step_cca_d1024_k16_b1024_f32.md); set to None whenever
+# the kernel changes until it is captured again.
+TRAFFIC_BYTES = {"cca_d1024_k16_b1024_f32": 4_707_328}
+
+
+def world_max(value: float, world: int, device=None) -> float:
+    """Maximum of a per-rank timing over all ranks (one all-reduce; identity for one rank)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def dist_env():
@@ -166,6 +186,85 @@ def make_pool(cfg, rows, dtype, device, seed=0):
 
 
 # ---------------------------------------------------------------------------
+# time-to-error: ground truth of the resident row pool, as the paper takes it (scipy's dense
+# symmetric generalized solver on the finite-sample covariances, Sec. 5)
+
+def pool_truth(X, Y, k, chunk=65536):
+    import scipy.linalg as sla
+    n, dx = X.shape
+    dy = Y.shape[1]
+    Cxx = np.zeros((dx, dx))
+    Cyy = np.zeros((dy, dy))
+    Cxy = np.zeros((dx, dy))
+    for r0 in range(0, n, chunk):
+        xc = X[r0:r0 + chunk].float().cpu().numpy().astype(np.float64)
+        yc = Y[r0:r0 + chunk].float().cpu().numpy().astype(np.float64)
+        Cxx += xc.T @ xc
+        Cyy += yc.T @ yc
+        Cxy += xc.T @ yc
+    d = dx + dy
+    A = np.zeros((d, d))
+    B = np.zeros((d, d))
+    A[:dx, dx:] = Cxy / n
+    A[dx:, :dx] = Cxy.T / n
+    B[:dx, :dx] = Cxx / n
+    B[dx:, dx:] = Cyy / n
+    w, U = sla.eigh(A, B, subset_by_index=[d - k, d - 1])
+    return U[:, ::-1].copy(), B, w[::-1].copy()
+
+
+def gen_subspace_error(Vt, Vh, B):
+    """1 - tr(U* P)/k of App. A.1 in Gram form."""
+    BVt, BVh = B @ Vt, B @ Vh
+    Gth = Vt.T @ BVh
+    tr = np.trace(np.linalg.solve(Vt.T @ BVt, Gth) @ np.linalg.solve(Vh.T @ BVh, Gth.T))
+    return float(1.0 - tr / Vt.shape[1])
+
+
+def time_to_error(make_solver, X, Y, b, truth, target=1e-3, every=500, max_steps=80_000, seed=123):
+    """Steps and device seconds from the cold start v_i ~ N(0, I) (normalised) until the
+    generalized subspace error against `truth` is at most `target`; the error is evaluated
+    every `every` steps outside the timed region."""
+    import torch
+    Vs, B, _ = truth
+    d, k = Vs.shape
+    solver = make_solver()
+    solver.set_V(synth.random_unit_columns(d, k, seed=seed).astype(np.float32))
+    nb = X.shape[0] // b
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pos, ms, err = 0, 0.0, 1.0
+    curve = []
+    # Epochs over the pool; odd epochs shift the minibatch grid by b/2 rows so that every row
+    # estimates A in one epoch and B in the next (the split of Alg. 2's independent batches).
+    per = [nb, nb - 1]
+    while pos < max_steps:
+        n = min(every, max_steps - pos)
+        e0.record()
+        left, s0 = n, pos
+        while left > 0:
+            ep, j = divmod(s0, nb + nb - 1)
+            odd = j >= nb
+            j = j - nb if odd else j
+            m = min(left, per[odd] - j)
+            r0 = j * b + (b // 2 if odd else 0)
+            solver.step_many(X[r0:r0 + m * b], Y[r0:r0 + m * b], b, m)
+            s0 += m
+            left -= m
+        e1.record()
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+        pos += n
+        err = gen_subspace_error(Vs, solver.V().astype(np.float64), B)
+        curve.append((pos, round(err, 6)))
+        if err <= target:
+            break
+    solver.close()
+    return {"target": target, "reached": err <= target, "steps": pos, "seconds": ms / 1e3,
+            "samples": pos * b, "final_error": err, "curve_every": every,
+            "curve": curve[:: max(1, len(curve) // 12)]}
+
+
+# ---------------------------------------------------------------------------
 # reference arm / CPU baseline: the FP64 oracle on host cores
 
 def oracle_rate(cfg, seconds: float):
@@ -190,6 +289,52 @@ def oracle_rate(cfg, seconds: float):
     return steps * b / el, steps, el
 
 
+def measure_throughput(workload, steps, warmup, dev, rank=0, path=0):
+    """Samples/s and roofline of one workload with its rows resident in HBM."""
+    import torch
+    from paper_2206_04993_gb300 import Solver, sgep
+    name, dtype, pool_rows = WORKLOADS[workload]
+    cfg = getattr(synth, name)(seed=rank)
+    model = cfg["model"]
+    b, k = cfg["b"], cfg["k"]
+    dx, dy = model.d_x, model.d_y
+    d = dx + dy
+    esz = 2 if dtype == "bf16" else 4
+    X, Y = make_pool(cfg, pool_rows, dtype, dev, seed=rank)
+    nb = pool_rows // b
+    solver = Solver(kind=sgep.SGEP_CCA, d_x=dx, d_y=dy, k=k,
+                    dtype=sgep.SGEP_BF16 if dtype == "bf16" else sgep.SGEP_F32,
+                    eta0=cfg["eta0"], gamma0=cfg["gamma0"], rho=cfg["rho"], max_b=b, path=path, seed=rank)
+    for i in range(warmup):
+        j = i % nb
+        solver.step(X[j * b:(j + 1) * b], Y[j * b:(j + 1) * b])
+    solver.sync()
+    torch.cuda.synchronize()
+    l0 = solver.launches
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        e0.record()
+        for i in range(steps):
+            j = (warmup + i) % nb
+            solver.step(X[j * b:(j + 1) * b], Y[j * b:(j + 1) * b])
+        e1.record()
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    peak, peak_kind = measured_peaks()
+    alg = b * d * esz + 16 * d * k
+    out = {"value": b / (ms / 1e3), "unit": "samples/s", "ms_per_step": ms, "dtype": dtype,
+           "path": solver.path, "gpu_launches": solver.launches - l0, "steps": steps, "warmup": warmup,
+           "config": {"d_x": dx, "d_y": dy, "k": k, "b": b, "pool_rows": pool_rows},
+           "roofline": {"bound": "hbm", "achieved": alg / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                        "frac": alg / (ms / 1e3) / 1e9 / peak, "traffic": None,
+                        "kernel": "whole step", "peak_source": peak_kind, "alg_bytes_per_launch": alg},
+           "clocks": clk.summary()}
+    solver.close()
+    del X, Y
+    torch.cuda.empty_cache()
+    return out
+
+
 def cpu_cores():
     for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         if os.environ.get(var):
@@ -202,8 +347,8 @@ def run_reference(args):
     if rank != 0:
         return
     cfg = getattr(synth, WORKLOADS[args.workload][0])()
-    per_step = max(1.0, 120.0 / max(1, args.steps + args.warmup))
-    rate, steps, el = oracle_rate(cfg, min(per_step * args.steps, 120.0))
+    # a bounded sample: about 0.05 s of oracle work per requested step, 3 s to 100 s in total
+    rate, steps, el = oracle_rate(cfg, min(100.0, max(3.0, 0.05 * args.steps)))
     sample = f"{steps} oracle steps of b={cfg['b']} rows ({el:.1f} s), FP64 numpy"
     line = {
         "impl": "reference", "metric": METRIC, "value": rate, "unit": "samples/s",
@@ -275,11 +420,7 @@ def run_native(args):
     if world > 1:
         torch.distributed.barrier()
     launches = solver.launches - launches0
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = world_max(ev0.elapsed_time(ev1), world, dev)
     solver.sync()
     ms_step = ms / args.steps
     value = world * b * args.steps / (ms / 1e3)
@@ -288,10 +429,14 @@ def run_native(args):
     peak, peak_kind = measured_peaks()
     alg_bytes = b * d * esz + 16 * d * k
     achieved = alg_bytes / (ms_step / 1e3) / 1e9
+    one_kernel = solver.path == sgep.SGEP_PATH_CLUSTER
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None,
-                "kernel": f"sgep step, path {solver.path}", "peak_source": peak_kind,
-                "alg_bytes_per_launch": alg_bytes}
+                "frac": achieved / peak,
+                "traffic": TRAFFIC_BYTES.get(args.workload) if one_kernel else None,
+                "kernel": "k_cluster_step (the whole step, one launch)" if one_kernel
+                else f"whole step, path {solver.path}",
+                "peak_source": peak_kind, "alg_bytes_per_launch": alg_bytes,
+                "timing": "CUDA events over the timed launches on their stream"}
 
     # e2e: through the C ABI with host buffers every step
     e2e = None
@@ -324,6 +469,39 @@ def run_native(args):
         cpu = {"value": rate, "unit": "samples/s", "cores": cpu_cores(), "kind": "oracle",
                "sample": f"{steps} FP64 oracle steps of b={b} ({el:.1f} s) on this workload"}
 
+    tte = None
+    if rank == 0 and not args.no_tte and args.workload == DEFAULT_WORKLOAD:
+        truth = pool_truth(X, Y, k)
+
+        def mk(dt):
+            return lambda: Solver(kind=sgep.SGEP_CCA, d_x=dx, d_y=dy, k=k,
+                                  dtype=sgep.SGEP_BF16 if dt == "bf16" else sgep.SGEP_F32,
+                                  eta0=cfg["eta0"], gamma0=cfg["gamma0"], rho=cfg["rho"],
+                                  schedule=cfg["schedule"], t_c=cfg["t_c"], T=cfg["T"],
+                                  eta_T=cfg["eta_T"], max_b=b, path=args.path, seed=rank)
+        def median_runs(fn):
+            runs = [fn(seed) for seed in (1, 2, 3)]
+            secs = sorted(r["seconds"] if r["reached"] else float("inf") for r in runs)
+            steps = sorted(r["steps"] if r["reached"] else 10 ** 12 for r in runs)
+            return {"median_seconds": secs[1], "median_steps": steps[1] if steps[1] < 10 ** 12 else None,
+                    "reached": sum(r["reached"] for r in runs), "runs": [
+                        {kk: r[kk] for kk in ("reached", "steps", "seconds", "final_error")} for r in runs],
+                    "curve_seed1": runs[0]["curve"]}
+        tte = {"truth": "scipy eigh of the pool's FP64 covariances (the paper's ground truth, Sec. 5)",
+               "seeds": "initial V from seeds 1, 2, 3; median reported; device time of the steps only",
+               "plain_f32": median_runs(lambda sd: time_to_error(mk("f32"), X, Y, b, truth, every=1000,
+                                                                 max_steps=args.tte_max_steps, seed=sd))}
+        Xb, Yb = X.to(torch.bfloat16), Y.to(torch.bfloat16)
+        tte["bf16"] = median_runs(lambda sd: time_to_error(mk("bf16"), Xb, Yb, b, truth, every=1000,
+                                                           max_steps=args.tte_max_steps, seed=sd))
+        del Xb, Yb
+
+    forms = None
+    if rank == 0 and not args.no_forms and args.workload == DEFAULT_WORKLOAD:
+        del X, Y
+        torch.cuda.empty_cache()
+        forms = {"cca_d32768_k32_b4096_bf16": measure_throughput("cca_d32768_k32_b4096_bf16", 60, 5, dev, rank)}
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
@@ -334,7 +512,7 @@ def run_native(args):
                        "pool_rows": pool_rows, "l2": "inputs larger than L2 (pool streamed)",
                        "parallelism": f"replicas{world}", "path": solver.path},
             "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "clocks": clk.summary(),
+            "clocks": clk.summary(), "time_to_1e-3": tte, "forms": forms,
         }
         print(json.dumps(line), flush=True)
     solver.close()

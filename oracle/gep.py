@@ -245,6 +245,27 @@ def cca_truth_lowrank(Dx, Dy, Wx, Wy, k: int):
     return lam, V
 
 
+def cca_truth_from_covariances(Cxx, Cyy, Cxy, k: int):
+    """Top-k CCA pairs from the covariance blocks through LAPACK (the paper's ground truth is
+    scipy's symmetric generalized solver, Sec. 5). With Cxx = Lx Lx^T, Cyy = Ly Ly^T, the
+    generalized eigenvalues of the CCA pencil are +-singular values of K = Lx^-1 Cxy Ly^-T and
+    the eigenvectors are [Lx^-T u; Ly^-T w] for the singular pairs (u, w) (Prop. "Similar
+    Matrices" applied blockwise). Returns (lam descending, V with unit Euclidean columns)."""
+    Lx = np.linalg.cholesky(np.asarray(Cxx, dtype=np.float64))
+    Ly = np.linalg.cholesky(np.asarray(Cyy, dtype=np.float64))
+    import scipy.linalg as sla
+    K = sla.solve_triangular(Lx, np.asarray(Cxy, dtype=np.float64), lower=True)
+    K = sla.solve_triangular(Ly, K.T, lower=True).T
+    U, sv, Wt = np.linalg.svd(K)
+    a = sla.solve_triangular(Lx.T, U[:, :k], lower=False)
+    b = sla.solve_triangular(Ly.T, Wt[:k].T, lower=False)
+    V = np.vstack([a, b])
+    V /= np.linalg.norm(V, axis=0, keepdims=True)
+    idx = np.argmax(np.abs(V), axis=0)
+    V *= np.sign(V[idx, np.arange(V.shape[1])])[None, :]
+    return sv[:k], V
+
+
 def cca_truth_planted(model, k: int):
     """Top-k truth of a PlantedCCA model (orthonormal Q, isotropic noise sigma^2).
 

@@ -194,9 +194,10 @@ def config_c2(seed: int = 0):
     """Plain CCA, d_x = d_y = 512, k = 16, b = 1024, latent dim 32, rho 0.95..0.3."""
     rhos = np.linspace(0.95, 0.3, 32)
     model = planted_cca(512, 512, rhos, sigma=0.5, seed=seed)
+    # harmonic step eta_t = 0.2 (1 + 400) / (t + 400) (tuned: the paper gives none for this size)
     return {"name": "cca_d1024_k16_b1024", "model": model, "k": 16, "b": 1024,
-            "n_samples": 1_000_000, "eta0": 0.3, "gamma0": 0.3, "rho": 1e-6,
-            "schedule": 1, "t_c": 100, "T": 20000, "eta_T": 0.3 * 120.0 / 20020.0}
+            "n_samples": 1_000_000, "eta0": 0.2, "gamma0": 0.3, "rho": 1e-6,
+            "schedule": 1, "t_c": 1, "T": 20000, "eta_T": 0.2 * 401.0 / 20400.0}
 
 
 def config_c3(seed: int = 0):

@@ -90,6 +90,18 @@ def test_single_step_shared_batch_and_ridge(path):
 
 
 @pytest.mark.parametrize("path", PATHS, ids=["generic", "cluster"])
+@pytest.mark.parametrize("dx,dy,k,b", [(512, 512, 16, 1024), (160, 96, 6, 200), (64, 64, 4, 256)])
+def test_single_step_bf16_aligned_shapes(path, dx, dy, k, b):
+    """BF16 rows whose slices start on 16-byte boundaries (the asynchronous-copy path)."""
+    X, Y = _data("cca", dx, dy, b, seed=dx + k)
+    V0, S0 = _state(dx + dy, k, seed=4, kind="cca")
+    with _solver("cca", dx, dy, k, path, dtype="bf16", eta0=0.3, gamma0=0.5, rho=1e-4) as s:
+        err = step_errors(s, V0, S0, X, Y, "cca", 0.3, 0.5, 1e-4, dtype="bf16")
+    for name, e in err.items():
+        assert e <= STEP_TOL, (name, e, err)
+
+
+@pytest.mark.parametrize("path", PATHS, ids=["generic", "cluster"])
 def test_single_step_bf16_inputs(path):
     """BF16 minibatch values (the GPU reads bf16, the oracle the same values in FP64);
     accumulation is FP32, so the same bar applies."""

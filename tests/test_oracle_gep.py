@@ -200,3 +200,15 @@ def test_lda_forms(rng):
     Xc = X - X.mean(axis=0)
     np.testing.assert_allclose(A + B, Xc.T @ Xc / X.shape[0], atol=1e-12)
     assert np.linalg.matrix_rank(A, tol=1e-10) <= 2
+
+
+def test_lapack_cca_route_matches_jacobi_oracle(rng):
+    """The LAPACK route used for ground truth at d = 1024 equals Cholesky + Jacobi."""
+    model = synth.planted_cca(20, 16, [0.9, 0.7, 0.5, 0.3], sigma=0.5, seed=8)
+    X, Y = synth.draw_rows(model, 400, batch=2)
+    A, B = gep.form_cca_AB(X, Y)
+    lam, V = gep.gep_topk(A, B, 4)
+    n = X.shape[0]
+    lam2, V2 = gep.cca_truth_from_covariances(X.T @ X / n, Y.T @ Y / n, X.T @ Y / n, 4)
+    np.testing.assert_allclose(lam2, lam, rtol=1e-10)
+    np.testing.assert_allclose(np.abs(np.sum(V * V2, axis=0)), 1.0, atol=1e-9)
