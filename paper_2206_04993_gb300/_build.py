@@ -57,7 +57,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
         list(ex.map(run, jobs))
     if jobs or not os.path.exists(LIB):
         tmp = LIB + ".tmp"
-        run([nvcc, *ARCH, "-shared", "-o", tmp, *objs])
+        run([nvcc, *ARCH, "-shared", "-Xlinker", "--no-undefined", "-o", tmp, *objs])
         os.replace(tmp, LIB)
     return LIB
 

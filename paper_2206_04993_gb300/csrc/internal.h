@@ -1,6 +1,7 @@
 // Internal declarations shared by the host-side ABI and the kernel files.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -62,6 +63,20 @@ struct Ctx {
   __nv_bfloat16* tc_Qt = nullptr;
   float* tc_coef = nullptr;        // k*k + 2k update coefficients
   int tc_generic_step = 0;         // the last step's shape needed the generic products
+  void* tc_fused_buf = nullptr;    // counters of the one-read products kernel
+  size_t tc_fused_bytes = 0;
+  unsigned long long* tc_trace = nullptr;  // SGEP_TRACE=1: per-row-block event times of the one-read kernel
+  int tc_trace_grid = 0, tc_trace_nrb = 0;
+  float* tc_fused_rep = nullptr;   // replicas of the row projections (one-read kernel)
+  float* tc_dbg = nullptr;         // a | G | b used by the last tensor-core update (debug)
+  unsigned long long* tc_bar = nullptr;  // grid-barrier arrivals of the fused update
+  float* tc_part = nullptr;              // its per-block partial sums
+  unsigned long long* tc_upd_trace = nullptr;  // SGEP_TRACE=1: its phase times
+  unsigned long long tc_bar_base = 0;    // arrivals expected before the next launch
+  int tc_upd_fused = 0;            // the fused update fits on the device (all blocks resident)
+  int tc_chain = 0;                // the last update prepared this step's V operand and d-side terms
+  int tc_bar_reset = 0;            // the barrier count must be cleared before the next launch
+  int tc_fused_dirty = 0;          // the replicas must be cleared before the next launch
   size_t tc_smem_p = 0, tc_smem_b = 0;
 
   int64_t t = 0;       // iterations applied (Alg. 2's t)
@@ -99,11 +114,26 @@ int generic_normalize(Ctx& c, cudaStream_t s);
 int generic_rayleigh_sums(Ctx& c, int64_t n, cudaStream_t s);
 
 // ---- tensor-core path (kernels_tc.cu) ----
+// 2-D BF16 row-major tensor map, 128-byte swizzle, box_rows x box_cols (box_cols * 2 == 128).
+int make_map_bf16(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows,
+                  int box_cols);
 bool tc_supported(const Ctx& c, const char** why);
 int tc_alloc(Ctx& c);
 void tc_free(Ctx& c);
 // acc <- [A_t V ; B_t V] of a BF16 minibatch on the tensor cores.
 int tc_products(Ctx& c, const void* X, const void* Y, int64_t b, cudaStream_t s);
+// k x k terms of the tensor-core path, double-buffered by step parity.
+struct TcTerms {
+  float *a, *b, *norms, *G, *vv;
+};
+size_t tc_terms_floats(int k);
+TcTerms tc_terms(const Ctx& c, int slot);
+
+// One-read fused products (kernels_tc_fused.cu).
+bool tc_fused_supported(const Ctx& c, int64_t b);
+int tc_fused_setup(Ctx& c);
+int tc_fused_products(Ctx& c, const CUtensorMap& mX, const CUtensorMap& mY, const CUtensorMap& mX64,
+                      const CUtensorMap& mY64, const CUtensorMap& mVt, int64_t b, cudaStream_t s);
 // Update from acc with the k x k terms the tensor-core products accumulated.
 int tc_update(Ctx& c, float eta, float gamma, cudaStream_t s);
 
@@ -118,6 +148,9 @@ int cluster_step(Ctx& c, const void* X, const void* Y, int64_t b, float eta, flo
 int cluster_flush(Ctx& c, cudaStream_t s);
 // Copy the pending products into acc layout (d x k AV, d x k BV) for debugging.
 int cluster_products(Ctx& c, float* AV, float* BV, cudaStream_t s);
+// SGEP_TRACE=1: print per-row-block event times of the most recent one-read launch to stderr.
+void tc_fused_trace_report(Ctx& c);
+void tc_update_trace_report(Ctx& c);
 // SGEP_TRACE=1: print per-phase times of the most recent cluster launch to stderr.
 void cluster_trace_report(Ctx& c);
 

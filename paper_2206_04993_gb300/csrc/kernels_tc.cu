@@ -6,6 +6,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -203,19 +205,31 @@ struct TcProjArgs {
 
 // V split into BF16 pairs (transposed, players padded to 32) and the d-side terms
 // G_ij = <v_i, [Bv]_j>, vv_i = |v_i|^2 of the update, accumulated per block of 64 rows of V.
-// grid: d/64 blocks of 256 threads. gram layout: a (k*k) | G (k*k) | b (k) | norms (k) | vv (k)
+// grid: d/64 blocks of 256 threads. Gout (k*k) and vvout (k) must be zero on entry.
 __global__ void __launch_bounds__(256) k_tc_prep_v(const float* __restrict__ V, const float* __restrict__ S,
                                                    int64_t d, int k, __nv_bfloat16* __restrict__ Vt,
-                                                   float* __restrict__ gram) {
+                                                   float* __restrict__ Gout, float* __restrict__ vvout) {
   __shared__ float vs[64][kTcKP + 1];
   __shared__ float ss[64][kTcKP + 1];
   const int tid = threadIdx.x;
   const int64_t c0 = (int64_t)blockIdx.x * 64;
-  for (int e = tid; e < 64 * kTcKP; e += 256) {
-    const int r = e / kTcKP, i = e % kTcKP;
-    const bool ok = c0 + r < d && i < k;
-    vs[r][i] = ok ? V[(c0 + r) * k + i] : 0.f;
-    ss[r][i] = ok ? S[(c0 + r) * k + i] : 0.f;
+  {
+    // all loads of the block in flight before the first store (8 rows per thread)
+    float rv[8], rs[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = tid + 256 * u;
+      const int r = e / kTcKP, i = e % kTcKP;
+      const bool ok = c0 + r < d && i < k;
+      rv[u] = ok ? __ldg(V + (c0 + r) * k + i) : 0.f;
+      rs[u] = ok ? __ldg(S + (c0 + r) * k + i) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = tid + 256 * u;
+      vs[e / kTcKP][e % kTcKP] = rv[u];
+      ss[e / kTcKP][e % kTcKP] = rs[u];
+    }
   }
   __syncthreads();
   // transposed BF16 pairs: consecutive threads write consecutive columns
@@ -235,63 +249,78 @@ __global__ void __launch_bounds__(256) k_tc_prep_v(const float* __restrict__ V, 
         s0 = fmaf(vs[r][i], ss[r][j], s0);
         s1 = fmaf(vs[r + 1][i], ss[r + 1][j], s1);
       }
-      atomicAdd(&gram[kk + p], s0 + s1);
+      atomicAdd(&Gout[p], s0 + s1);
     } else {
       const int i = p - kk;
       for (int r = 0; r < 64; r += 2) {
         s0 = fmaf(vs[r][i], vs[r][i], s0);
         s1 = fmaf(vs[r + 1][i], vs[r + 1][i], s1);
       }
-      atomicAdd(&gram[2 * kk + 2 * k + i], s0 + s1);
+      atomicAdd(&vvout[i], s0 + s1);
     }
   }
 }
 
-// P, Q split into BF16 pairs (transposed, row stride ldt) and the row-side terms
-// a_ij = sum_A (P_i Q_j + Q_i P_j) / n_A, b_i = sum_B (P_i^2 + Q_i^2) / n_B.
-// grid: b/64 blocks of 256 threads.
+// P, Q split into BF16 pairs (transposed, row stride ldt; skipped when Pt is null) and the
+// row-side terms a_ij = sum_A (P_i Q_j + Q_i P_j) / n_A, b_i = sum_B (P_i^2 + Q_i^2) / n_B.
+// grid: b/16 blocks of 256 threads (16 rows each; the split point is a multiple of 64).
+// aout (k*k) and bout (k) must be zero on entry.
 __global__ void __launch_bounds__(256) k_tc_prep_w(const float* __restrict__ P, const float* __restrict__ Q,
                                                    int64_t b, int64_t ldt, int64_t nA, int k, float inv_nA,
                                                    float inv_nB, __nv_bfloat16* __restrict__ Pt,
-                                                   __nv_bfloat16* __restrict__ Qt, float* __restrict__ gram) {
-  __shared__ float ps[64][kTcKP + 1];
-  __shared__ float qs[64][kTcKP + 1];
+                                                   __nv_bfloat16* __restrict__ Qt, float* __restrict__ aout,
+                                                   float* __restrict__ bout) {
+  constexpr int R = 16;
+  __shared__ float ps[R][kTcKP + 1];
+  __shared__ float qs[R][kTcKP + 1];
   const int tid = threadIdx.x;
-  const int64_t r0 = (int64_t)blockIdx.x * 64;
-  for (int e = tid; e < 64 * kTcKP; e += 256) {
-    const int r = e / kTcKP, i = e % kTcKP;
-    const bool ok = r0 + r < b;
-    ps[r][i] = ok ? P[(r0 + r) * kTcKP + i] : 0.f;
-    qs[r][i] = ok ? Q[(r0 + r) * kTcKP + i] : 0.f;
+  const int64_t r0 = (int64_t)blockIdx.x * R;
+  {
+    float rp[2], rq[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int e = tid + 256 * u;
+      const int r = e / kTcKP, i = e % kTcKP;
+      const bool ok = r0 + r < b;
+      rp[u] = ok ? __ldcg(P + (r0 + r) * kTcKP + i) : 0.f;
+      rq[u] = ok ? __ldcg(Q + (r0 + r) * kTcKP + i) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int e = tid + 256 * u;
+      ps[e / kTcKP][e % kTcKP] = rp[u];
+      qs[e / kTcKP][e % kTcKP] = rq[u];
+    }
   }
   __syncthreads();
-  for (int e = tid; e < 2 * kTcKP * 64; e += 256) {
-    const int n = e / 64, r = e % 64;
+  for (int e = tid; Pt != nullptr && e < 2 * kTcKP * R; e += 256) {
+    const int n = e / R, r = e % R;
     if (r0 + r >= b) continue;
     const float p = ps[r][n % kTcKP], q = qs[r][n % kTcKP];
     const __nv_bfloat16 ph = __float2bfloat16(p), qh = __float2bfloat16(q);
     Pt[(int64_t)n * ldt + r0 + r] = n < kTcKP ? ph : __float2bfloat16(p - __bfloat162float(ph));
     Qt[(int64_t)n * ldt + r0 + r] = n < kTcKP ? qh : __float2bfloat16(q - __bfloat162float(qh));
   }
-  // rows of this block that estimate A and B (the split point is a multiple of 64)
   const bool rowsA = r0 < nA;
   const int kk = k * k;
   for (int p = tid; p < kk + k; p += 256) {
     float s0 = 0.f, s1 = 0.f;
     if (p < kk && rowsA) {
       const int i = p / k, j = p % k;
-      for (int r = 0; r < 64; ++r) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
         s0 = fmaf(ps[r][i], qs[r][j], s0);
         s1 = fmaf(qs[r][i], ps[r][j], s1);
       }
-      atomicAdd(&gram[p], (s0 + s1) * inv_nA);
+      atomicAdd(&aout[p], (s0 + s1) * inv_nA);
     } else if (p >= kk && !rowsA) {
       const int i = p - kk;
-      for (int r = 0; r < 64; ++r) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
         s0 = fmaf(ps[r][i], ps[r][i], s0);
         s1 = fmaf(qs[r][i], qs[r][i], s1);
       }
-      atomicAdd(&gram[2 * kk + i], (s0 + s1) * inv_nB);
+      atomicAdd(&bout[i], (s0 + s1) * inv_nB);
     }
   }
 }
@@ -303,7 +332,9 @@ __global__ void __launch_bounds__(256) k_tc_prep_w(const float* __restrict__ P, 
 // (v + eta grad)^2 into the norms. gram: a | G | b | norms | vv.
 __global__ void __launch_bounds__(256) k_tc_update(const float* __restrict__ V, float* __restrict__ S,
                                                    const float* __restrict__ AV, const float* __restrict__ BV,
-                                                   float* __restrict__ gram, int64_t d, int k, float rho,
+                                                   const float* __restrict__ a, const float* __restrict__ bterm,
+                                                   const float* __restrict__ G, const float* __restrict__ vv,
+                                                   float* __restrict__ norms, int64_t d, int k, float rho,
                                                    float eta, float gamma, float eps_B,
                                                    float* __restrict__ Vtmp, float* __restrict__ grad_out) {
   __shared__ float T[kTcKP * kTcKP];
@@ -311,11 +342,9 @@ __global__ void __launch_bounds__(256) k_tc_update(const float* __restrict__ V, 
   __shared__ float red[8][kTcKP];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int kk = k * k;
-  const float* a = gram;
-  const float* G = gram + kk;
   if (tid < k) {
     inv_s[tid] = 1.f / fmaxf(G[tid * k + tid], rho);
-    cb[tid] = fmaf(eps_B, gram[2 * kk + 2 * k + tid], gram[2 * kk + tid]);
+    cb[tid] = fmaf(eps_B, vv[tid], bterm[tid]);
   }
   __syncthreads();
   for (int p = tid; p < kk; p += 256) {
@@ -368,7 +397,7 @@ __global__ void __launch_bounds__(256) k_tc_update(const float* __restrict__ V, 
   if (tid < k) {
     float s2 = 0.f;
     for (int w = 0; w < 8; ++w) s2 += red[w][tid];
-    atomicAdd(&gram[2 * kk + k + tid], s2);
+    atomicAdd(&norms[tid], s2);
   }
 }
 
@@ -392,6 +421,292 @@ __global__ void k_tc_normalize(const float* __restrict__ Vtmp, const float* __re
     dst[e] = v;
   }
   if (bad) atomicOr(dflag, kFlagNonFinite);
+}
+
+// Update, retraction and the next step's V-side preparation in one launch, for
+// large-d problems (k <= 32). Blocks of 256 threads own 128 rows of V; all blocks
+// are resident (cooperative launch) and meet at two grid barriers. No atomics: every
+// cross-block sum goes through per-block partials.
+//   phase 1: coefficients of Eq. (update) from a, G, b (and |v_i|^2 when eps_B > 0);
+//            v' = v + eta grad and the [Bv] step S' = S + gamma (BV - S) per row; the
+//            rows stay in shared memory; per-block column sums of v'^2 are stored.
+//   barrier 1; every block adds the column sums (the retraction needs all rows).
+//   phase 2: v = v' / |v'| written out, with its BF16 hi/lo pairs (the next step's
+//            transposed V operand); per-block partials of the next step's d-side
+//            terms G = V^T S' and |v_i|^2.
+//   barrier 2; block j adds entries [j per, (j + 1) per) of those partials.
+// The k x k terms are double-buffered by step parity: this launch reads slot `slot`
+// and writes slot 1 - slot. Block 0 clears a and b (accumulated by the next step's
+// row-side kernel) after barrier 1, when every block has read them.
+struct TcUpdArgs {
+  const float* V;
+  float* Vout;
+  float* S;
+  const float* AV;
+  const float* BV;
+  float* terms;   // a (kk) | b (k) | norms [2][k] | G [2][kk] | vv [2][k]
+  float* part;    // per-block partials: [grid][32] column sums, then [grid][32 * 32 + 32] terms
+  float* dbg;     // a | G | b as used by this update (debug), or null
+  float* grad_out;
+  __nv_bfloat16* Vt;
+  int64_t d;
+  int k, slot;
+  float rho, eta, gamma, eps_B;
+  unsigned long long* bar;  // grid-barrier arrivals (monotone)
+  unsigned long long bar_target;  // arrivals that complete barrier 1 (barrier 2: + grid)
+  int* dflag;
+  unsigned long long* trace;  // [grid][8] globaltimer stamps of the phases, or null
+};
+
+// Bounded grid barrier: returns false (and flags a timeout) when the wait gives up.
+__device__ __forceinline__ bool grid_barrier(unsigned long long* bar, unsigned long long target, int* flag,
+                                             int* ok_s) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(bar, 1ull);
+    *ok_s = tc::spin_until_geq64(bar, target) ? 1 : 0;
+    if (!*ok_s) atomicOr(flag, kFlagTimeout);
+  }
+  __syncthreads();
+  return *ok_s != 0;
+}
+
+__global__ void __launch_bounds__(256) k_tc_update_fused(const TcUpdArgs u) {
+  constexpr int R = 128;
+  constexpr int KT = kTcKP * kTcKP + kTcKP;  // terms per block partial
+  __shared__ float T[kTcKP * kTcKP];
+  __shared__ float cb[kTcKP], cac[kTcKP], inv_s[kTcKP], inv_n[kTcKP];
+  __shared__ float red[8][kTcKP];
+  __shared__ float vs[R][kTcKP + 1];
+  __shared__ float ss[R][kTcKP + 1];
+  __shared__ int ok_s;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int k = u.k, kk = k * k, slot = u.slot;
+  const int nblk = (int)gridDim.x;
+  auto stamp = [&](int ph) {
+    if (u.trace && tid == 0) u.trace[blockIdx.x * 8 + ph] = tc::globaltimer();
+  };
+  stamp(0);
+  float* a = u.terms;
+  float* bt = a + kk;
+  float* nrm = bt + k;             // [2][k]
+  float* Gs = nrm + 2 * k;         // [2][kk]
+  float* vvs = Gs + 2 * kk;        // [2][k]
+  const float* G = Gs + slot * kk;
+  const float* vv = vvs + slot * k;
+  float* part_n = u.part;                      // [nblk][32]
+  float* part_t = u.part + (size_t)nblk * 32;  // [nblk][KT]
+  {
+    // a and G staged in shared memory (vs and ss are free until phase 1): one round trip
+    float* As = &vs[0][0];
+    float* Gm = &ss[0][0];
+    for (int p = tid; p < kk; p += 256) {
+      As[p] = __ldcg(a + p);
+      Gm[p] = __ldcg(G + p);
+    }
+    if (tid < k) cb[tid] = fmaf(u.eps_B, __ldcg(vv + tid), __ldcg(bt + tid));
+    __syncthreads();
+    if (tid < k) inv_s[tid] = 1.f / fmaxf(Gm[tid * k + tid], u.rho);
+    __syncthreads();
+    for (int p = tid; p < kk; p += 256) {
+      const int j = p / k, i = p % k;
+      T[j * kTcKP + i] = j < i ? cb[i] * As[i * k + j] * inv_s[j] : 0.f;
+    }
+    if (tid < k) {
+      float c = 0.f;
+      for (int j = 0; j < tid; ++j) c = fmaf(As[tid * k + j] * Gm[tid * k + j], inv_s[j], c);
+      cac[tid] = As[tid * k + tid] - c;
+    }
+    __syncthreads();
+  }
+  // ---- phase 1: 16 rows per warp, all loads in flight at once -----------------
+  const bool on = lane < k;
+  const int64_t c0 = (int64_t)blockIdx.x * R;
+  float nr = 0.f;
+  {
+    constexpr int U = 16;
+    float v[U], sv[U], av[U], bv[U], pen[U];
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const int r = wid + 8 * q;
+      const int64_t g = (c0 + r) * k + lane;
+      const bool ok = on && c0 + r < u.d;
+      v[q] = ok ? u.V[g] : 0.f;  // plain load: this launch rewrites V
+      sv[q] = ok ? u.S[g] : 0.f;
+      av[q] = ok ? __ldcg(u.AV + g) : 0.f;
+      bv[q] = ok ? __ldcg(u.BV + g) : 0.f;
+      pen[q] = 0.f;
+    }
+    for (int j = 0; j < k; ++j) {
+      const float t = T[j * kTcKP + lane];
+#pragma unroll
+      for (int q = 0; q < U; ++q) pen[q] = fmaf(__shfl_sync(0xffffffffu, sv[q], j), t, pen[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const int r = wid + 8 * q;
+      const int64_t g = (c0 + r) * k + lane;
+      const bool ok = on && c0 + r < u.d;
+      const float bve = fmaf(u.eps_B, v[q], bv[q]);
+      const float gr = cb[lane] * av[q] - cac[lane] * bve - pen[q];
+      const float vn = ok ? fmaf(u.eta, gr, v[q]) : 0.f;
+      const float sn = ok ? fmaf(u.gamma, bve - sv[q], sv[q]) : 0.f;
+      if (ok) {
+        u.S[g] = sn;
+        if (u.grad_out) u.grad_out[g] = gr;
+      }
+      vs[r][lane] = vn;
+      ss[r][lane] = sn;
+      nr = fmaf(vn, vn, nr);
+    }
+  }
+  red[wid][lane] = nr;
+  __syncthreads();
+  if (tid < kTcKP) {
+    float s2 = 0.f;
+    for (int w = 0; w < 8; ++w) s2 += red[w][tid];
+    part_n[(size_t)blockIdx.x * 32 + tid] = s2;
+  }
+  stamp(1);
+  if (!grid_barrier(u.bar, u.bar_target, u.dflag, &ok_s)) return;
+  stamp(2);
+  if (blockIdx.x == 0) {  // every block has read a, G and b: keep them (debug) and clear a and b
+    if (u.dbg) {
+      for (int p = tid; p < kk; p += 256) {
+        u.dbg[p] = __ldcg(a + p);
+        u.dbg[kk + p] = __ldcg(G + p);
+      }
+      if (tid < k) u.dbg[2 * kk + tid] = __ldcg(bt + tid);
+      __syncthreads();
+    }
+    for (int p = tid; p < kk; p += 256) a[p] = 0.f;
+    if (tid < k) bt[tid] = 0.f;
+  }
+  // column sums of v'^2 over all blocks (eight independent loads in flight per thread)
+  {
+    float s2 = 0.f;
+    for (int blk0 = wid; blk0 < nblk; blk0 += 64) {
+      float x[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int blk = blk0 + 8 * q;
+        x[q] = blk < nblk ? __ldcg(part_n + (size_t)blk * 32 + lane) : 0.f;
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) s2 += x[q];
+    }
+    red[wid][lane] = s2;
+  }
+  __syncthreads();
+  if (tid < kTcKP) {
+    float s2 = 0.f;
+    for (int w = 0; w < 8; ++w) s2 += red[w][tid];
+    inv_n[tid] = tid < k ? 1.f / sqrtf(s2) : 0.f;
+    if (blockIdx.x == 0 && tid < k) nrm[slot * k + tid] = s2;
+  }
+  __syncthreads();
+  // ---- phase 2 -----------------------------------------------------------------
+  bool bad = false;
+  for (int e = tid; e < R * kTcKP; e += 256) {
+    const int r = e / kTcKP, i = e % kTcKP;
+    const float v = vs[r][i] * inv_n[i];
+    vs[r][i] = v;
+    if (i < k && c0 + r < u.d) {
+      u.Vout[(c0 + r) * k + i] = v;
+      bad |= !isfinite(v);
+    }
+  }
+  if (bad) atomicOr(u.dflag, kFlagNonFinite);
+  __syncthreads();
+  // transposed BF16 pairs: thread -> (operand row n, two consecutive rows of V)
+  for (int e = tid; e < 2 * kTcKP * (R / 2); e += 256) {
+    const int n = e / (R / 2), rp = 2 * (e % (R / 2));
+    if (c0 + rp >= u.d) continue;  // d is even: rp + 1 < d as well
+    const float v0 = vs[rp][n % kTcKP], v1 = vs[rp + 1][n % kTcKP];
+    __nv_bfloat162 w;
+    if (n < kTcKP) {
+      w = __floats2bfloat162_rn(v0, v1);
+    } else {
+      const float h0 = __bfloat162float(__float2bfloat16(v0)), h1 = __bfloat162float(__float2bfloat16(v1));
+      w = __floats2bfloat162_rn(v0 - h0, v1 - h1);
+    }
+    *reinterpret_cast<__nv_bfloat162*>(u.Vt + (int64_t)n * u.d + c0 + rp) = w;
+  }
+  // block partial of G = V^T S' (4 x 4 register tiles over four groups of 32 rows) and |v_i|^2
+  {
+    const int tl = tid & 63, rg = tid >> 6;
+    const int i0 = 4 * (tl & 7), j0 = 4 * (tl >> 3);
+    float acc[4][4] = {};
+    for (int r = 32 * rg; r < 32 * rg + 32; ++r) {
+      float x[4], y[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        x[q] = vs[r][i0 + q];
+        y[q] = ss[r][j0 + q];
+      }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(x[p], y[q], acc[p][q]);
+    }
+    float nv = 0.f;
+    if (tid < 128) {  // |v_i|^2: column i = tid % 32 over rows 32 (tid / 32) ..
+      const int i = tid & 31, g4 = tid >> 5;
+      for (int r = 32 * g4; r < 32 * g4 + 32; ++r) nv = fmaf(vs[r][i], vs[r][i], nv);
+    }
+    __syncthreads();  // vs is reused as the reduction buffer below
+    float* rbuf = &vs[0][0];  // [4][KT]
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) rbuf[rg * KT + (i0 + p) * kTcKP + j0 + q] = acc[p][q];
+    if (tid < 128) rbuf[(tid >> 5) * KT + kTcKP * kTcKP + (tid & 31)] = nv;
+    __syncthreads();
+    for (int e = tid; e < KT; e += 256)
+      part_t[(size_t)blockIdx.x * KT + e] = rbuf[e] + rbuf[KT + e] + rbuf[2 * KT + e] + rbuf[3 * KT + e];
+  }
+  stamp(3);
+  if (!grid_barrier(u.bar, u.bar_target + (unsigned long long)nblk, u.dflag, &ok_s)) return;
+  stamp(4);
+  // ---- entries [j per, (j + 1) per) of the next step's terms -------------------
+  {
+    __shared__ float sums[KT];
+    const int per = (KT + nblk - 1) / nblk;
+    const int e0 = (int)blockIdx.x * per;
+    const int ne = max(0, min(per, KT - e0));
+    // warp per entry, lanes over the blocks (eight loads in flight per lane), shuffle sum
+    for (int el = wid; el < ne; el += 8) {
+      float s2 = 0.f;
+      for (int blk0 = lane; blk0 < nblk; blk0 += 256) {
+        float x[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int blk = blk0 + 32 * q;
+          x[q] = blk < nblk ? __ldcg(part_t + (size_t)blk * KT + e0 + el) : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) s2 += x[q];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+      if (lane == 0) sums[el] = s2;
+    }
+    __syncthreads();
+    float* Gn = Gs + (1 - slot) * kk;
+    float* vvn = vvs + (1 - slot) * k;
+    for (int e = tid; e < ne; e += 256) {
+      const int te = e0 + e;
+      if (te < kTcKP * kTcKP) {
+        const int i = te / kTcKP, j = te % kTcKP;
+        if (i < k && j < k) Gn[i * k + j] = sums[e];
+      } else {
+        const int i = te - kTcKP * kTcKP;
+        if (i < k) vvn[i] = sums[e];
+      }
+    }
+  }
+  stamp(5);
 }
 
 // grid: (b/128 row tiles, 2 views, splits)
@@ -631,6 +946,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
 namespace sgep {
 
+size_t tc_terms_floats(int k) { return (size_t)3 * k * k + 5 * k; }
+
+// Pointers into the k x k terms for step parity `slot`: a | b | norms[2] | G[2] | vv[2].
+TcTerms tc_terms(const Ctx& c, int slot) {
+  const int k = c.k, kk = k * k;
+  TcTerms t;
+  t.a = c.gram;
+  t.b = c.gram + kk;
+  t.norms = c.gram + kk + k + slot * k;
+  t.G = c.gram + kk + 3 * k + slot * kk;
+  t.vv = c.gram + 3 * kk + 3 * k + slot * k;
+  return t;
+}
+
 bool tc_supported(const Ctx& c, const char** why) {
   const char* w = nullptr;
   if (c.cfg.dtype != SGEP_BF16) w = "needs BF16 minibatches";
@@ -651,15 +980,47 @@ int tc_alloc(Ctx& c) {
   SGEP_CUDA_TRY(cudaMalloc((void**)&c.tc_Pt, 2 * kTcKP * mb * 2));
   SGEP_CUDA_TRY(cudaMalloc((void**)&c.tc_Qt, 2 * kTcKP * mb * 2));
   SGEP_CUDA_TRY(cudaMalloc((void**)&c.tc_coef, (size_t)(c.k * c.k + 2 * c.k) * sizeof(float)));
-  // the k x k terms gain a slot for |v_i|^2
+  // k x k terms: a | b | norms [2] | G [2] | |v_i|^2 [2] (double-buffered by step parity)
   cudaFree(c.gram);
   c.gram = nullptr;
-  SGEP_CUDA_TRY(cudaMalloc((void**)&c.gram, (size_t)(2 * c.k * c.k + 3 * c.k) * sizeof(float)));
+  SGEP_CUDA_TRY(cudaMalloc((void**)&c.gram, tc_terms_floats(c.k) * sizeof(float)));
+  SGEP_CUDA_TRY(cudaMemset(c.gram, 0, tc_terms_floats(c.k) * sizeof(float)));
+  if (c.cfg.debug) SGEP_CUDA_TRY(cudaMalloc((void**)&c.tc_dbg, (size_t)(2 * c.k * c.k + c.k) * sizeof(float)));
+  SGEP_CUDA_TRY(cudaMalloc((void**)&c.tc_bar, sizeof(unsigned long long)));
+  SGEP_CUDA_TRY(cudaMalloc((void**)&c.tc_part,
+                           (size_t)((c.d + 127) / 128) * (32 + kTcKP * kTcKP + kTcKP) * sizeof(float)));
+  SGEP_CUDA_TRY(cudaMemset(c.tc_bar, 0, sizeof(unsigned long long)));
+  c.tc_bar_base = 0;
+  c.tc_chain = 0;
+  {
+    const char* tr = getenv("SGEP_TRACE");
+    if (tr && tr[0] == '1') {
+      const size_t n = (size_t)((c.d + 127) / 128) * 8;
+      SGEP_CUDA_TRY(cudaMalloc((void**)&c.tc_upd_trace, n * sizeof(unsigned long long)));
+      SGEP_CUDA_TRY(cudaMemset(c.tc_upd_trace, 0, n * sizeof(unsigned long long)));
+    }
+  }
+  {
+    // the fused update needs every block resident at once
+    int per_sm = 0;
+    const int grid = (int)((c.d + 127) / 128);
+    c.tc_upd_fused = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_update_fused, 256, 0) ==
+                             cudaSuccess &&
+                         grid <= per_sm * c.num_sms
+                     ? 1
+                     : 0;
+    cudaGetLastError();
+  }
   const size_t sp = kP_Stages * 24576 + 1024 + 256, sb = kB_Stages * 40960 + 1024 + 256;
   SGEP_CUDA_TRY(cudaFuncSetAttribute(k_tc_project, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp));
   SGEP_CUDA_TRY(cudaFuncSetAttribute(k_tc_backproject, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb));
   c.tc_smem_p = sp;
   c.tc_smem_b = sb;
+  // The one-read products kernel is opt-in (SGEP_TC_FUSED=1): on GB300 its cross-CTA
+  // reductions share the memory system with the minibatch stream and it is slower than the
+  // two-pass products.
+  const char* fused = getenv("SGEP_TC_FUSED");
+  if (fused && fused[0] == '1') return tc_fused_setup(c);
   return SGEP_OK;
 }
 
@@ -670,6 +1031,20 @@ void tc_free(Ctx& c) {
   cudaFree(c.tc_Qt);
   cudaFree(c.tc_coef);
   c.tc_coef = nullptr;
+  cudaFree(c.tc_dbg);
+  c.tc_dbg = nullptr;
+  cudaFree(c.tc_bar);
+  c.tc_bar = nullptr;
+  cudaFree(c.tc_part);
+  c.tc_part = nullptr;
+  cudaFree(c.tc_upd_trace);
+  c.tc_upd_trace = nullptr;
+  cudaFree(c.tc_fused_buf);
+  cudaFree(c.tc_fused_rep);
+  c.tc_fused_rep = nullptr;
+  cudaFree(c.tc_trace);
+  c.tc_trace = nullptr;
+  c.tc_fused_buf = nullptr;
   c.tc_Vt = nullptr;
   c.tc_PQ = nullptr;
   c.tc_Pt = c.tc_Qt = nullptr;
@@ -686,21 +1061,39 @@ int tc_products(Ctx& c, const void* X, const void* Y, int64_t b, cudaStream_t s)
   float* P = c.tc_PQ;
   float* Q = c.tc_PQ + (size_t)c.cfg.max_b * kTcKP;
   const int k = c.k;
-  // 1. V split into BF16 pairs, d-side terms; P, Q and the k x k terms cleared
-  SGEP_CUDA_TRY(cudaMemsetAsync(c.tc_PQ, 0, sizeof(float) * 2 * c.cfg.max_b * kTcKP, s));
-  SGEP_CUDA_TRY(cudaMemsetAsync(c.gram, 0, sizeof(float) * (2 * k * k + 3 * k), s));
-  k_tc_prep_v<<<(unsigned)((c.d + 63) / 64), 256, 0, s>>>(c.V, c.S, c.d, k, c.tc_Vt, c.gram);
-  SGEP_CUDA_TRY(cudaGetLastError());
+  const int slot = (int)(c.t & 1);
+  const TcTerms tt = tc_terms(c, slot);
+  // 1. V split into BF16 pairs and the d-side terms -- unless the previous step's fused
+  //    update produced them (and cleared the terms this step accumulates)
+  if (!c.tc_chain) {
+    SGEP_CUDA_TRY(cudaMemsetAsync(c.gram, 0, tc_terms_floats(k) * sizeof(float), s));
+    k_tc_prep_v<<<(unsigned)((c.d + 63) / 64), 256, 0, s>>>(c.V, c.S, c.d, k, c.tc_Vt, tt.G, tt.vv);
+    SGEP_CUDA_TRY(cudaGetLastError());
+    ++c.launches;
+  }
   CUtensorMap mX1, mY1, mVt, mX2, mY2, mPt, mQt;
   int rc = make_map_bf16(&mX1, X, b, c.d_x, c.d_x, 128, 64);
   if (!rc) rc = make_map_bf16(&mY1, Y, b, c.d_y, c.d_y, 128, 64);
   if (!rc) rc = make_map_bf16(&mVt, c.tc_Vt, 2 * kTcKP, c.d, c.d, 64, 64);
   if (!rc) rc = make_map_bf16(&mX2, X, b, c.d_x, c.d_x, 64, 64);
   if (!rc) rc = make_map_bf16(&mY2, Y, b, c.d_y, c.d_y, 64, 64);
-  if (!rc) rc = make_map_bf16(&mPt, c.tc_Pt, 2 * kTcKP, b, c.cfg.max_b, 64, 64);
+  if (rc) return rc;
+  if (c.tc_fused_buf && tc_fused_supported(c, b)) {
+    // one read of the minibatch: products in one persistent launch, then the row-side terms
+    rc = tc_fused_products(c, mX1, mY1, mX2, mY2, mVt, b, s);
+    if (rc) return rc;
+    k_tc_prep_w<<<(unsigned)((b + 15) / 16), 256, 0, s>>>(P, Q, b, c.cfg.max_b, nA, k, 1.f / (float)nA,
+                                                           1.f / (float)(split ? b - nA : b), nullptr, nullptr,
+                                                           tt.a, tt.b);
+    SGEP_CUDA_TRY(cudaGetLastError());
+    c.launches += 1;
+    return SGEP_OK;
+  }
+  rc = make_map_bf16(&mPt, c.tc_Pt, 2 * kTcKP, b, c.cfg.max_b, 64, 64);
   if (!rc) rc = make_map_bf16(&mQt, c.tc_Qt, 2 * kTcKP, b, c.cfg.max_b, 64, 64);
   if (rc) return rc;
-  // 2. projections
+  // 2. projections (accumulated into P and Q)
+  SGEP_CUDA_TRY(cudaMemsetAsync(c.tc_PQ, 0, sizeof(float) * 2 * c.cfg.max_b * kTcKP, s));
   {
     TcProjArgs pa;
     pa.b = b;
@@ -720,9 +1113,9 @@ int tc_products(Ctx& c, const void* X, const void* Y, int64_t b, cudaStream_t s)
     SGEP_CUDA_TRY(cudaGetLastError());
   }
   // 3. P, Q split into BF16 pairs (transposed), row-side terms a and b
-  k_tc_prep_w<<<(unsigned)((b + 63) / 64), 256, 0, s>>>(P, Q, b, c.cfg.max_b, nA, k, 1.f / (float)nA,
+  k_tc_prep_w<<<(unsigned)((b + 15) / 16), 256, 0, s>>>(P, Q, b, c.cfg.max_b, nA, k, 1.f / (float)nA,
                                                          1.f / (float)(split ? b - nA : b), c.tc_Pt, c.tc_Qt,
-                                                         c.gram);
+                                                         tt.a, tt.b);
   SGEP_CUDA_TRY(cudaGetLastError());
   // 4. back-projection into acc = [A_t V ; B_t V]
   {
@@ -742,20 +1135,74 @@ int tc_products(Ctx& c, const void* X, const void* Y, int64_t b, cudaStream_t s)
     k_tc_backproject<<<(unsigned)(c.d / 256), kTcThreads, c.tc_smem_b, s>>>(mX2, mY2, mPt, mQt, ba);
     SGEP_CUDA_TRY(cudaGetLastError());
   }
-  c.launches += 4;
+  c.launches += 3;
   return SGEP_OK;
 }
 
 int tc_update(Ctx& c, float eta, float gamma, cudaStream_t s) {
   const int k = c.k;
-  k_tc_update<<<(unsigned)((c.d + 31) / 32), 256, 0, s>>>(c.V, c.S, c.acc, c.acc + c.d * k, c.gram, c.d, k,
-                                                          c.cfg.rho, eta, gamma, c.cfg.eps_B, c.Vtmp,
-                                                          c.cfg.debug ? c.grad : nullptr);
+  const int slot = (int)(c.t & 1);
+  const TcTerms tt = tc_terms(c, slot);
+  if (c.tc_upd_fused) {
+    if (c.tc_bar_reset) {  // an aborted launch may have left the barrier count short
+      SGEP_CUDA_TRY(cudaMemsetAsync(c.tc_bar, 0, sizeof(unsigned long long), s));
+      c.tc_bar_base = 0;
+      c.tc_bar_reset = 0;
+    }
+    const unsigned grid = (unsigned)((c.d + 127) / 128);
+    TcUpdArgs u;
+    u.V = c.V;
+    u.Vout = c.V;  // each block reads its rows in phase 1 and writes them in phase 2
+    u.S = c.S;
+    u.AV = c.acc;
+    u.BV = c.acc + c.d * k;
+    u.terms = c.gram;
+    u.part = c.tc_part;
+    u.dbg = c.cfg.debug ? c.tc_dbg : nullptr;
+    u.grad_out = c.cfg.debug ? c.grad : nullptr;
+    u.Vt = c.tc_Vt;
+    u.d = c.d;
+    u.k = k;
+    u.slot = slot;
+    u.rho = c.cfg.rho;
+    u.eta = eta;
+    u.gamma = gamma;
+    u.eps_B = c.cfg.eps_B;
+    u.bar = c.tc_bar;
+    u.bar_target = c.tc_bar_base + grid;
+    u.trace = c.tc_upd_trace;
+    u.dflag = c.dflag;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(256);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    SGEP_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_tc_update_fused, u));
+    c.tc_bar_base += 2 * (unsigned long long)grid;  // two barriers
+    c.tc_chain = 1;
+    ++c.launches;
+    return SGEP_OK;
+  }
+  c.tc_chain = 0;
+  if (c.cfg.debug) {
+    SGEP_CUDA_TRY(cudaMemcpyAsync(c.tc_dbg, tt.a, (size_t)k * k * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    SGEP_CUDA_TRY(
+        cudaMemcpyAsync(c.tc_dbg + k * k, tt.G, (size_t)k * k * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    SGEP_CUDA_TRY(
+        cudaMemcpyAsync(c.tc_dbg + 2 * k * k, tt.b, (size_t)k * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  }
+  k_tc_update<<<(unsigned)((c.d + 31) / 32), 256, 0, s>>>(c.V, c.S, c.acc, c.acc + c.d * k, tt.a, tt.b, tt.G,
+                                                          tt.vv, tt.norms, c.d, k, c.cfg.rho, eta, gamma,
+                                                          c.cfg.eps_B, c.Vtmp, c.cfg.debug ? c.grad : nullptr);
   SGEP_CUDA_TRY(cudaGetLastError());
   if (k % 4 == 0) {
     const int64_t n4 = c.d * k / 4;
     k_tc_normalize<<<(unsigned)std::min<int64_t>((n4 + 255) / 256, 4 * c.num_sms), 256, 0, s>>>(
-        c.Vtmp, c.gram + 2 * k * k + k, c.V, n4, k, c.dflag);
+        c.Vtmp, tt.norms, c.V, n4, k, c.dflag);
     SGEP_CUDA_TRY(cudaGetLastError());
     c.launches += 2;
     return SGEP_OK;
@@ -834,3 +1281,24 @@ done:
   cudaFree(flag);
   return rc;
 }
+
+namespace sgep {
+// SGEP_TRACE=1: phase times of the most recent fused update (stderr).
+void tc_update_trace_report(Ctx& c) {
+  if (!c.tc_upd_trace) return;
+  const int n = (int)((c.d + 127) / 128);
+  std::vector<unsigned long long> t((size_t)n * 8);
+  if (cudaMemcpy(t.data(), c.tc_upd_trace, t.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess) return;
+  unsigned long long g0 = ~0ull;
+  for (int b = 0; b < n; ++b) g0 = std::min(g0, t[(size_t)b * 8]);
+  std::fprintf(stderr, "[sgep trace] fused update, %d blocks (us from first start, median/max):", n);
+  const char* names[6] = {"start", "phase1", "bar1", "phase2", "bar2", "end"};
+  for (int ph = 0; ph < 6; ++ph) {
+    std::vector<double> v;
+    for (int b = 0; b < n; ++b) v.push_back((t[(size_t)b * 8 + ph] - g0) / 1e3);
+    std::sort(v.begin(), v.end());
+    std::fprintf(stderr, " %s %.2f/%.2f", names[ph], v[v.size() / 2], v.back());
+  }
+  std::fprintf(stderr, "\n");
+}
+}  // namespace sgep

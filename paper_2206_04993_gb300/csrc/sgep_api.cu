@@ -101,7 +101,12 @@ static int check_flag(Ctx& c) {
   SGEP_CUDA_TRY(cudaMemcpy(&flag, c.dflag, sizeof(int), cudaMemcpyDeviceToHost));
   if (flag) {
     SGEP_CUDA_TRY(cudaMemset(c.dflag, 0, sizeof(int)));
-    if (flag & kFlagTimeout) return fail(SGEP_ETIMEOUT, "a bounded device-side wait gave up");
+    if (flag & kFlagTimeout) {
+      c.tc_fused_dirty = 1;  // an aborted one-read launch may leave partial sums behind
+      c.tc_bar_reset = 1;    // ... and an aborted update a short barrier count
+      c.tc_chain = 0;
+      return fail(SGEP_ETIMEOUT, "a bounded device-side wait gave up");
+    }
     if (flag & kFlagNonFinite) return fail(SGEP_ENONFINITE, "non-finite values in V");
   }
   return SGEP_OK;
@@ -288,6 +293,7 @@ static int do_step(Ctx& c, const void* X, const void* Y, int64_t b, cudaStream_t
   } else {
     if (c.path == SGEP_PATH_TC) {
       rc = tc_products(c, X, Y, b, s);
+      if (!rc && c.tc_generic_step) c.tc_chain = 0;
       if (!rc) rc = c.tc_generic_step ? generic_update(c, eta, gamma, s) : tc_update(c, eta, gamma, s);
     } else {
       rc = generic_products(c, X, Y, b, s);
@@ -328,6 +334,8 @@ int sgep_sync(sgep_t h, void* stream) {
   if (!h) return fail(SGEP_EINVAL, "handle is NULL");
   int rc = complete(*h, (cudaStream_t)stream);
   if (h->trace) cluster_trace_report(*h);
+  if (h->tc_trace) tc_fused_trace_report(*h);
+  if (h->tc_upd_trace) tc_update_trace_report(*h);
   return rc;
 }
 
@@ -367,6 +375,7 @@ int sgep_set_VS(sgep_t h, const float* V, const float* S, int on_device, void* s
   SGEP_CUDA_TRY(cudaMemcpyAsync(c.S, S, sizeof(float) * c.d * c.k, kd, s));
   SGEP_CUDA_TRY(cudaStreamSynchronize(s));
   c.debug_valid = 0;
+  c.tc_chain = 0;
   return SGEP_OK;
 }
 
@@ -472,6 +481,7 @@ int sgep_set_state(sgep_t h, const void* buf, size_t nbytes) {
   SGEP_CUDA_TRY(cudaMemcpy(c.S, p + dk * sizeof(float), dk * sizeof(float), cudaMemcpyHostToDevice));
   c.t = hd.t;
   c.debug_valid = 0;
+  c.tc_chain = 0;
   return SGEP_OK;
 }
 
@@ -513,7 +523,9 @@ int sgep_debug_update(sgep_t h, float* grad, double* terms) {
   const int k = c.k;
   SGEP_CUDA_TRY(cudaMemcpy(grad, c.grad, dk * sizeof(float), cudaMemcpyDeviceToHost));
   std::vector<float> g(2 * k * k + 2 * k);
-  SGEP_CUDA_TRY(cudaMemcpy(g.data(), c.gram, g.size() * sizeof(float), cudaMemcpyDeviceToHost));
+  const bool from_tc = c.path == SGEP_PATH_TC && !c.tc_generic_step;  // a | G | b kept by the update
+  SGEP_CUDA_TRY(cudaMemcpy(g.data(), from_tc ? c.tc_dbg : c.gram,
+                           (from_tc ? 2 * k * k + k : g.size()) * sizeof(float), cudaMemcpyDeviceToHost));
   for (int i = 0; i < 2 * k * k + k; ++i) terms[i] = g[i];
   return SGEP_OK;
 }
