@@ -55,7 +55,14 @@ extern "C" {
 #define SGEP_PCA 0  /* A = E[x x^T], B = I                                       */
 #define SGEP_CCA 1  /* A = [[0, E xy^T], [E yx^T, 0]], B = blockdiag(E xx^T, E yy^T) */
 #define SGEP_PLS 2  /* A as CCA, B = I (reading of Sec. 1, which gives no formula) */
-#define SGEP_LDA 3  /* reserved: between-class A, within-class B (not built yet)  */
+#define SGEP_LDA 3  /* between-class A from running class means, within-class B  */
+/* LDA (Sec. 1 names it without estimators; reading): the handle keeps the exact
+ * running class sums and counts of every row seen (FP64); a step first adds all
+ * of its rows, then uses A = sum_c pi_c (mu_c - mu)(mu_c - mu)^T (pi_c = n_c / n,
+ * mu = sum_c pi_c mu_c) and B_t = the covariance of the B rows, each centred by
+ * the mean of its class. d_y = 0; labels are int32 in [0, n_classes), 2 <= n_classes
+ * <= 32. LDA runs on the generic path. rank(A) <= n_classes - 1, so only the top
+ * n_classes - 1 generalized eigenvalues are nonzero. */
 
 /* ---- element type of X and Y ------------------------------------------- */
 #define SGEP_F32  0
@@ -82,7 +89,7 @@ typedef struct {
   int64_t  d_x;        /* columns of X (>= 1)                                      */
   int64_t  d_y;        /* columns of Y (>= 1 for CCA/PLS, must be 0 for PCA)       */
   int32_t  k;          /* number of players, 1 <= k <= 64 and k <= d              */
-  int32_t  n_classes;  /* LDA only (reserved)                                      */
+  int32_t  n_classes;  /* LDA only: number of classes, 2..32                         */
   float    eta0;       /* player step size eta (Alg. 2 "step size sequence")      */
   float    gamma0;     /* auxiliary step size gamma_t (constant; beta_t in App. H) */
   float    rho;        /* clipping floor of <v_j, [Bv]_j> (Alg. 2), > 0           */
@@ -110,7 +117,7 @@ int sgep_config_default(sgep_config* cfg);
  * (Alg. 2, line "v_i ~ S^{d-1}"), and set [Bv]_i = v_i (Alg. 2, auxiliary
  * initialisation). Synchronous. On error *out is left NULL and nothing leaks.
  * Errors: SGEP_EINVAL (bad shape/kind/dtype/rho/k), SGEP_ENOMEM, SGEP_ECUDA,
- * SGEP_ENOTSUP (e.g. LDA, or a forced path that cannot run the shape). */
+ * SGEP_ENOTSUP (a forced path that cannot run the shape or kind). */
 int sgep_init(const sgep_config* cfg, sgep_t* out);
 
 /* Free every resource of the handle (synchronises the device first).
@@ -122,7 +129,10 @@ int sgep_destroy(sgep_t h);
  * the update direction is Eq. (update) with the clipped auxiliary terms,
  * v_i <- (v_i + eta_t grad_i) / ||.||, [Bv]_i <- [Bv]_i + gamma_t (B_t v_i - [Bv]_i),
  * all players reading the state of step t. Asynchronous on `stream`.
- * X: device, b x d_x; Y: device, b x d_y (NULL for PCA); labels: reserved, NULL.
+ * X: device, b x d_x; Y: device, b x d_y (NULL for PCA and LDA); labels: LDA
+ * only, device, b int32 class labels in [0, n_classes) (NULL otherwise). A label
+ * outside the range is reported as SGEP_EINVAL by the next synchronising call
+ * (its row is then left uncentred; no out-of-bounds access happens).
  * Requires 2 <= b <= max_b when split_AB = 1 (1 <= b otherwise).
  * The work of a step may be completed lazily by the next step or by the
  * next synchronising call. Errors: SGEP_EINVAL, SGEP_ECUDA, SGEP_ELAUNCH. */
@@ -130,7 +140,7 @@ int sgep_step(sgep_t h, const void* X, const void* Y, const int32_t* labels,
               int64_t b, void* stream);
 
 /* `nsteps` consecutive iterations on minibatches stored back to back:
- * step s reads rows [s*b, (s+1)*b) of X and Y. Same contract as sgep_step. */
+ * step s reads rows [s*b, (s+1)*b) of X and Y (and labels). Same contract as sgep_step. */
 int sgep_step_many(sgep_t h, const void* X, const void* Y, const int32_t* labels,
                    int64_t b, int64_t nsteps, void* stream);
 
@@ -157,11 +167,15 @@ int sgep_set_VS(sgep_t h, const float* V, const float* S, int on_device, void* s
  * (Sec. 2, below Eq. util_new) with A and B estimated on the n evaluation
  * rows (X, Y) (all rows for both; App. H.2.2 evaluates on a larger batch than
  * it trains on). Sums are accumulated in double. out_k: host, k doubles.
+ * LDA: <v_i, A v_i> comes from the handle's class statistics (the readout does
+ * not update them) and <v_i, B v_i> from the n rows centred by their class
+ * means; labels (device, n int32) are required.
  * Synchronous. Any n >= 1 (processed in chunks of max_b rows). */
 int sgep_get_eigenvalues(sgep_t h, const void* X, const void* Y, const int32_t* labels,
                          int64_t n, double* out_k, void* stream);
 
-/* Serialise the state (versioned header, V, [Bv], step counter) into `buf`.
+/* Serialise the state (versioned header, V, [Bv], step counter; LDA also its
+ * class sums, C x d doubles, and counts, C doubles) into `buf`.
  * If buf is NULL, only writes the required size to *nbytes. Synchronous. */
 int sgep_get_state(sgep_t h, void* buf, size_t* nbytes);
 

@@ -28,6 +28,11 @@ direction (Prop. "Equivalence to EigenGame Unloaded"); the streamed operators
 equal the explicit block matrices of Sec. 1; averaged over many independent
 minibatches the update equals the update with population A and B (unbiased
 estimates, Sec. 3); Alg. 1 and Alg. 2 with full-batch estimates converge to O1.
+LDA (tests/test_oracle_lda.py): streaming every row of a finite set through
+`lda_stats_update` gives the between-class scatter of the whole set; with the
+batch's own class means `lda_ops` A + B is the batch covariance (law of total
+variance); the population problem of Gaussian classes with isotropic shared
+covariance reduces to the eigenproblem of the between-class scatter.
 """
 from __future__ import annotations
 
@@ -81,6 +86,32 @@ def pca_ops(X: np.ndarray, eps_B: float = 0.0):
 def matrix_ops(A: np.ndarray, B: np.ndarray):
     """Exact operators from explicit matrices (full-batch setting)."""
     return (lambda U: A @ U), (lambda U: B @ U)
+
+
+def lda_stats_update(sums: np.ndarray, counts: np.ndarray, X: np.ndarray, labels: np.ndarray):
+    """Running class statistics of LDA: per-class sums of every row seen and counts.
+
+    Reading (the paper names LDA in Sec. 1 without its estimators): the class means
+    are the exact cumulative means over all rows seen so far. A step first adds
+    every row of its minibatch (both halves), then uses the updated means.
+    Returns new (sums, counts); `sums` is C x d, `counts` has C entries.
+    """
+    sums = np.array(sums, dtype=np.float64, copy=True)
+    counts = np.array(counts, dtype=np.float64, copy=True)
+    X = np.asarray(X, dtype=np.float64)
+    for r in range(X.shape[0]):
+        sums[labels[r]] += X[r]
+        counts[labels[r]] += 1.0
+    return sums, counts
+
+
+def lda_state(sums: np.ndarray, counts: np.ndarray):
+    """Class means mu_c = sums_c / n_c (0 for a class not seen yet) and priors pi_c = n_c / n."""
+    counts = np.asarray(counts, dtype=np.float64)
+    mean = np.zeros_like(np.asarray(sums, dtype=np.float64))
+    seen = counts > 0
+    mean[seen] = sums[seen] / counts[seen][:, None]
+    return mean, counts / counts.sum()
 
 
 def lda_ops(X: np.ndarray, labels: np.ndarray, class_mean: np.ndarray,

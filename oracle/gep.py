@@ -185,6 +185,17 @@ def form_lda_AB(X: np.ndarray, labels: np.ndarray, n_classes: int):
 # ---------------------------------------------------------------------------
 # Closed forms for the planted models
 
+def lda_population_AB(model):
+    """Population A (between-class, equal priors) and B (shared within-class L L^T) of planted LDA."""
+    means = np.asarray(model["means"], dtype=np.float64)
+    C = means.shape[0]
+    mu = means.mean(axis=0)
+    Mc = means - mu[None, :]
+    A = Mc.T @ Mc / C
+    L = np.asarray(model["L"], dtype=np.float64)
+    return A, L @ L.T
+
+
 def cca_population_AB(model):
     """Population A and B of a planted CCA model (x = W_x z + noise, y = W_y z + noise)."""
     if hasattr(model, "sigma"):

@@ -79,6 +79,14 @@ struct Ctx {
   int tc_fused_dirty = 0;          // the replicas must be cleared before the next launch
   size_t tc_smem_p = 0, tc_smem_b = 0;
 
+  // LDA: running class statistics (exact cumulative sums over every row seen)
+  double* lda_sum = nullptr;  // C x d class sums
+  double* lda_cnt = nullptr;  // C class counts
+  float* lda_mean = nullptr;  // C x d class means
+  float* lda_M = nullptr;     // C x d mu_c - mu
+  float* lda_pi = nullptr;    // C priors n_c / n
+  float* lda_W = nullptr;     // C x k: (mu_c - mu)^T V
+
   int64_t t = 0;       // iterations applied (Alg. 2's t)
   int64_t launches = 0; // kernels launched
   int debug_valid = 0; // sgep_debug_update has data
@@ -87,6 +95,8 @@ struct Ctx {
 // Flag bits of Ctx::dflag.
 constexpr int kFlagNonFinite = 1;
 constexpr int kFlagTimeout = 2;
+constexpr int kFlagBadLabel = 4;
+constexpr int kMaxClasses = 32;  // LDA classes
 
 // Error reporting (thread-local message).
 void set_error(const std::string& msg);
@@ -107,7 +117,20 @@ int generic_products(Ctx& c, const void* X, const void* Y, int64_t b, cudaStream
 // Update from acc: grams, update, retraction. eta/gamma of this step.
 int generic_update(Ctx& c, float eta, float gamma, cudaStream_t s);
 // Row projections of n rows into PQ (n <= max_b), zeroing PQ first.
-int generic_project(Ctx& c, const void* X, const void* Y, int64_t n, cudaStream_t s);
+int generic_project(Ctx& c, const void* X, const void* Y, int64_t n, cudaStream_t s,
+                    const float* center = nullptr, const int32_t* labels = nullptr);
+// LDA: BV = X~^T (X~ V) / n over n rows centred by the class means (kernels_generic.cu).
+int generic_lda_within(Ctx& c, const void* X, const int32_t* labels, int64_t n, cudaStream_t s);
+
+// LDA (kernels_lda.cu): class statistics and the between-class products.
+int lda_alloc(Ctx& c);
+void lda_free(Ctx& c);
+// Adds the minibatch rows to the class statistics, then acc = [A_t V ; B_t V].
+int lda_products(Ctx& c, const void* X, const int32_t* labels, int64_t b, cudaStream_t s);
+// Recomputes means, mu_c - mu and priors from the sums and counts (after a state load).
+int lda_refresh(Ctx& c, cudaStream_t s);
+// W = (mu_c - mu)^T V into lda_W (C x k) for the current V.
+int lda_project_means(Ctx& c, cudaStream_t s);
 // Retraction V <- Vtmp / ||Vtmp|| with the norms in gram (counts the update launch too).
 int generic_normalize(Ctx& c, cudaStream_t s);
 // Rayleigh sums of the n rows in PQ accumulated into rq (double).

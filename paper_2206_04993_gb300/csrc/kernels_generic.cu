@@ -26,6 +26,25 @@ __device__ __forceinline__ float load_elem(const __nv_bfloat16* p, int64_t i) {
   return __bfloat162float(p[i]);
 }
 
+// Class-mean centring of LDA rows: x - mu_{label}. A label outside [0, C) is
+// flagged and the row is left uncentred (the step then reports the bad label).
+struct Centring {
+  const float* mean;      // C x ld class means, or null (no centring)
+  const int32_t* labels;  // labels of the rows passed to the kernel
+  int C;
+  int* dflag;
+};
+
+__device__ __forceinline__ float centred(const Centring& cz, float x, int64_t row, int64_t ld, int64_t col) {
+  if (!cz.mean) return x;
+  const int lab = cz.labels[row];
+  if ((unsigned)lab >= (unsigned)cz.C) {
+    atomicOr(cz.dflag, kFlagBadLabel);
+    return x;
+  }
+  return x - cz.mean[(int64_t)lab * ld + col];
+}
+
 // ---------------------------------------------------------------------------
 // k_project: PQ[r, 0:k] += X[r, cols] V[cols, :], PQ[r, k:2k] += Y[r, cols] V[d_x + cols, :]
 // grid.x: row tiles of 32, grid.y: column chunks (X chunks first, then Y chunks),
@@ -35,7 +54,7 @@ __global__ void __launch_bounds__(kThreads) k_project(const T* __restrict__ X, c
                                                       int64_t n, int64_t dx, int64_t dy,
                                                       const float* __restrict__ V, int k,
                                                       int64_t chunk, int nchunk_x,
-                                                      float* __restrict__ PQ) {
+                                                      float* __restrict__ PQ, const Centring cz) {
   constexpr int BR = 32, TC = 32;
   __shared__ float Xs[BR][TC + 1];
   __shared__ float Vs[TC][kMaxK];
@@ -58,7 +77,7 @@ __global__ void __launch_bounds__(kThreads) k_project(const T* __restrict__ X, c
     for (int e = tid; e < BR * TC; e += kThreads) {
       const int rr = e / TC, cc = e % TC;
       const int64_t row = row0 + rr, col = c0 + cc;
-      Xs[rr][cc] = (row < n && col < c_end) ? load_elem(Z, row * ld + col) : 0.f;
+      Xs[rr][cc] = (row < n && col < c_end) ? centred(cz, load_elem(Z, row * ld + col), row, ld, col) : 0.f;
     }
     for (int e = tid; e < TC * k; e += kThreads) {
       const int cc = e / k, i = e % k;
@@ -92,14 +111,15 @@ __global__ void __launch_bounds__(kThreads) k_project(const T* __restrict__ X, c
 //   AV[c,i] += inv_nA * sum_{r in A rows} Z[r,c] W_A[r,i]
 //   BV[c,i] += inv_nB * sum_{r in B rows} Z[r,c] W_B[r,i]
 // where (CCA) W_A = Q for X columns / P for Y columns and W_B = P for X / Q for Y;
-// (PCA) W_A = P over every row, no BV; (PLS) W_A as CCA over every row, no BV.
+// (PCA) W_A = P over every row, no BV; (PLS) W_A as CCA over every row, no BV;
+// (LDA) every row passed is a B row, centred by its class mean: W_B = P, no AV.
 // grid.x: column blocks of 64 (X blocks then Y blocks), grid.y: row splits.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_backproject(
     const T* __restrict__ X, const T* __restrict__ Y, int64_t b, int64_t dx, int64_t dy,
     int64_t nA, int kind, int split, const float* __restrict__ PQ, int k, int nblk_x,
     int64_t rows_per_split, float inv_nA, float inv_nB, float* __restrict__ AV,
-    float* __restrict__ BV) {
+    float* __restrict__ BV, const Centring cz) {
   constexpr int TR = 32, CB = 64;
   __shared__ float Zs[TR][CB];
   __shared__ float Ws[TR][2 * kMaxK];
@@ -117,6 +137,7 @@ __global__ void __launch_bounds__(kThreads) k_backproject(
   const int own = isY ? k : 0;
   const int cross = isY ? 0 : k;
   const bool cca = kind == SGEP_CCA;
+  const bool lda = kind == SGEP_LDA;
   float accA[kMaxK / 4], accB[kMaxK / 4];
 #pragma unroll
   for (int m = 0; m < kMaxK / 4; ++m) accA[m] = accB[m] = 0.f;
@@ -125,7 +146,7 @@ __global__ void __launch_bounds__(kThreads) k_backproject(
     for (int e = tid; e < TR * CB; e += kThreads) {
       const int rr = e / CB, cc = e % CB;
       const int64_t row = r0 + rr, cg = (int64_t)bidx * CB + cc;
-      Zs[rr][cc] = (row < r_end && cg < ld) ? load_elem(Z, row * ld + cg) : 0.f;
+      Zs[rr][cc] = (row < r_end && cg < ld) ? centred(cz, load_elem(Z, row * ld + cg), row, ld, cg) : 0.f;
     }
     for (int e = tid; e < TR * 2 * k; e += kThreads) {
       const int rr = e / (2 * k), j = e % (2 * k);
@@ -139,7 +160,10 @@ __global__ void __launch_bounds__(kThreads) k_backproject(
       const float z = Zs[rr][cl];
       // which estimate(s) this row feeds
       bool toA, toB;
-      if (!cca) {
+      if (lda) {
+        toA = false;
+        toB = true;
+      } else if (!cca) {
         toA = true;
         toB = false;
       } else if (split) {
@@ -172,8 +196,8 @@ __global__ void __launch_bounds__(kThreads) k_backproject(
     for (int m = 0; m < kMaxK / 4; ++m) {
       const int i = g + 4 * m;
       if (i < k) {
-        atomicAdd(&AV[gc * k + i], accA[m] * inv_nA);
-        if (cca) atomicAdd(&BV[gc * k + i], accB[m] * inv_nB);
+        if (!lda) atomicAdd(&AV[gc * k + i], accA[m] * inv_nA);
+        if (cca || lda) atomicAdd(&BV[gc * k + i], accB[m] * inv_nB);
       }
     }
   }
@@ -311,7 +335,8 @@ __global__ void k_normalize(const float* __restrict__ Vtmp, const float* __restr
   }
 }
 
-// k_rayleigh: num_i += sum_r 2 P_ri Q_ri (CCA, PLS) or P_ri^2 (PCA); den_i += P_ri^2 + Q_ri^2 (CCA).
+// k_rayleigh: num_i += sum_r 2 P_ri Q_ri (CCA, PLS) or P_ri^2 (PCA, and LDA's B rows);
+// den_i += P_ri^2 + Q_ri^2 (CCA).
 __global__ void k_rayleigh(const float* __restrict__ PQ, int64_t n, int k, int kind,
                            double* __restrict__ rq) {
   const int i = threadIdx.x % k;
@@ -322,7 +347,7 @@ __global__ void k_rayleigh(const float* __restrict__ PQ, int64_t n, int k, int k
   for (int64_t r = (int64_t)blockIdx.x * lanes + lr; r < n; r += (int64_t)gridDim.x * lanes) {
     const double p = PQ[r * 2 * k + i];
     const double q = PQ[r * 2 * k + k + i];
-    if (kind == SGEP_PCA) {
+    if (kind == SGEP_PCA || kind == SGEP_LDA) {
       num += p * p;
     } else {
       num += 2.0 * p * q;
@@ -336,7 +361,7 @@ __global__ void k_rayleigh(const float* __restrict__ PQ, int64_t n, int k, int k
 inline int grid_cap(const Ctx& c, int per_sm) { return c.num_sms * per_sm; }
 
 template <typename T>
-int launch_project(Ctx& c, const T* X, const T* Y, int64_t n, cudaStream_t s) {
+int launch_project(Ctx& c, const T* X, const T* Y, int64_t n, cudaStream_t s, const Centring& cz) {
   const int64_t row_tiles = (n + 31) / 32;
   // Column chunk: enough blocks to fill the GPU, at least 32 columns each.
   int64_t chunk = 1024;
@@ -344,19 +369,19 @@ int launch_project(Ctx& c, const T* X, const T* Y, int64_t n, cudaStream_t s) {
   const int nchunk_x = (int)((c.d_x + chunk - 1) / chunk);
   const int nchunk_y = c.has_y ? (int)((c.d_y + chunk - 1) / chunk) : 0;
   dim3 grid((unsigned)row_tiles, (unsigned)(nchunk_x + nchunk_y));
-  k_project<T><<<grid, kThreads, 0, s>>>(X, Y, n, c.d_x, c.d_y, c.V, c.k, chunk, nchunk_x, c.PQ);
+  k_project<T><<<grid, kThreads, 0, s>>>(X, Y, n, c.d_x, c.d_y, c.V, c.k, chunk, nchunk_x, c.PQ, cz);
   SGEP_CUDA_TRY(cudaGetLastError());
   ++c.launches;
   return SGEP_OK;
 }
 
 template <typename T>
-int launch_backproject(Ctx& c, const T* X, const T* Y, int64_t b, cudaStream_t s) {
+int launch_backproject(Ctx& c, const T* X, const T* Y, int64_t b, cudaStream_t s, const Centring& cz) {
   const int kind = c.cfg.kind;
   const bool cca = kind == SGEP_CCA;
   const int split = (cca && c.cfg.split_AB) ? 1 : 0;
   const int64_t nA = split ? b / 2 : b;
-  const int64_t nB = split ? b - nA : b;
+  const int64_t nB = split ? b - nA : b;  // LDA: every row passed is a B row (nB = b)
   const int nblk_x = (int)((c.d_x + 63) / 64);
   const int nblk_y = c.has_y ? (int)((c.d_y + 63) / 64) : 0;
   const int nblk = nblk_x + nblk_y;
@@ -370,7 +395,7 @@ int launch_backproject(Ctx& c, const T* X, const T* Y, int64_t b, cudaStream_t s
   float* BV = c.acc + c.d * c.k;
   k_backproject<T><<<grid, kThreads, 0, s>>>(X, Y, b, c.d_x, c.d_y, nA, kind, split, c.PQ, c.k,
                                              nblk_x, rows_per_split, 1.f / (float)nA,
-                                             1.f / (float)nB, AV, BV);
+                                             1.f / (float)nB, AV, BV, cz);
   SGEP_CUDA_TRY(cudaGetLastError());
   ++c.launches;
   return SGEP_OK;
@@ -378,20 +403,33 @@ int launch_backproject(Ctx& c, const T* X, const T* Y, int64_t b, cudaStream_t s
 
 }  // namespace
 
-int generic_project(Ctx& c, const void* X, const void* Y, int64_t n, cudaStream_t s) {
+int generic_project(Ctx& c, const void* X, const void* Y, int64_t n, cudaStream_t s, const float* center,
+                    const int32_t* labels) {
   SGEP_CUDA_TRY(cudaMemsetAsync(c.PQ, 0, sizeof(float) * n * 2 * c.k, s));
+  const Centring cz{center, labels, c.cfg.n_classes, c.dflag};
   if (c.cfg.dtype == SGEP_BF16)
-    return launch_project<__nv_bfloat16>(c, (const __nv_bfloat16*)X, (const __nv_bfloat16*)Y, n, s);
-  return launch_project<float>(c, (const float*)X, (const float*)Y, n, s);
+    return launch_project<__nv_bfloat16>(c, (const __nv_bfloat16*)X, (const __nv_bfloat16*)Y, n, s, cz);
+  return launch_project<float>(c, (const float*)X, (const float*)Y, n, s, cz);
+}
+
+// LDA: BV = X~^T (X~ V) / n over the n rows passed (already the B rows), centred by class means.
+int generic_lda_within(Ctx& c, const void* X, const int32_t* labels, int64_t n, cudaStream_t s) {
+  int rc = generic_project(c, X, nullptr, n, s, c.lda_mean, labels);
+  if (rc) return rc;
+  const Centring cz{c.lda_mean, labels, c.cfg.n_classes, c.dflag};
+  if (c.cfg.dtype == SGEP_BF16)
+    return launch_backproject<__nv_bfloat16>(c, (const __nv_bfloat16*)X, nullptr, n, s, cz);
+  return launch_backproject<float>(c, (const float*)X, nullptr, n, s, cz);
 }
 
 int generic_products(Ctx& c, const void* X, const void* Y, int64_t b, cudaStream_t s) {
   int rc = generic_project(c, X, Y, b, s);
   if (rc) return rc;
   SGEP_CUDA_TRY(cudaMemsetAsync(c.acc, 0, sizeof(float) * 2 * c.d * c.k, s));
+  const Centring none{nullptr, nullptr, 0, c.dflag};
   if (c.cfg.dtype == SGEP_BF16)
-    return launch_backproject<__nv_bfloat16>(c, (const __nv_bfloat16*)X, (const __nv_bfloat16*)Y, b, s);
-  return launch_backproject<float>(c, (const float*)X, (const float*)Y, b, s);
+    return launch_backproject<__nv_bfloat16>(c, (const __nv_bfloat16*)X, (const __nv_bfloat16*)Y, b, s, none);
+  return launch_backproject<float>(c, (const float*)X, (const float*)Y, b, s, none);
 }
 
 int generic_update(Ctx& c, float eta, float gamma, cudaStream_t s) {

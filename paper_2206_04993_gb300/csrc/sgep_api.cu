@@ -84,6 +84,7 @@ static void free_ctx(sgep_ctx* c) {
   if (!c) return;
   cluster_free(*c);
   tc_free(*c);
+  lda_free(*c);
   cudaFree(c->V);
   cudaFree(c->S);
   cudaFree(c->Vtmp);
@@ -107,6 +108,7 @@ static int check_flag(Ctx& c) {
       c.tc_chain = 0;
       return fail(SGEP_ETIMEOUT, "a bounded device-side wait gave up");
     }
+    if (flag & kFlagBadLabel) return fail(SGEP_EINVAL, "a label is outside [0, n_classes)");
     if (flag & kFlagNonFinite) return fail(SGEP_ENONFINITE, "non-finite values in V");
   }
   return SGEP_OK;
@@ -159,13 +161,15 @@ int sgep_init(const sgep_config* cfg, sgep_t* out) {
   *out = nullptr;
   if (!cfg) return fail(SGEP_EINVAL, "cfg is NULL");
   const sgep_config& g = *cfg;
-  if (g.kind == SGEP_LDA) return fail(SGEP_ENOTSUP, "LDA is not built yet");
-  if (g.kind != SGEP_PCA && g.kind != SGEP_CCA && g.kind != SGEP_PLS)
+  if (g.kind != SGEP_PCA && g.kind != SGEP_CCA && g.kind != SGEP_PLS && g.kind != SGEP_LDA)
     return fail(SGEP_EINVAL, "unknown kind");
+  if (g.kind == SGEP_LDA && (g.n_classes < 2 || g.n_classes > kMaxClasses))
+    return fail(SGEP_EINVAL, "LDA needs 2 <= n_classes <= 32");
   if (g.dtype != SGEP_F32 && g.dtype != SGEP_BF16) return fail(SGEP_EINVAL, "unknown dtype");
   if (g.d_x < 1) return fail(SGEP_EINVAL, "d_x must be >= 1");
-  if (g.kind == SGEP_PCA && g.d_y != 0) return fail(SGEP_EINVAL, "PCA requires d_y = 0");
-  if (g.kind != SGEP_PCA && g.d_y < 1) return fail(SGEP_EINVAL, "CCA/PLS require d_y >= 1");
+  const bool one_view = g.kind == SGEP_PCA || g.kind == SGEP_LDA;
+  if (one_view && g.d_y != 0) return fail(SGEP_EINVAL, "PCA and LDA require d_y = 0");
+  if (!one_view && g.d_y < 1) return fail(SGEP_EINVAL, "CCA/PLS require d_y >= 1");
   const int64_t d = g.d_x + g.d_y;
   if (g.k < 1 || g.k > 64 || g.k > d) return fail(SGEP_EINVAL, "k must satisfy 1 <= k <= min(64, d)");
   if (!(g.rho > 0.f) || !std::isfinite(g.rho)) return fail(SGEP_EINVAL, "rho must be > 0");
@@ -186,7 +190,7 @@ int sgep_init(const sgep_config* cfg, sgep_t* out) {
   c->d = d;
   c->k = g.k;
   c->b_is_identity = (g.kind == SGEP_PCA || g.kind == SGEP_PLS);
-  c->has_y = (g.kind != SGEP_PCA);
+  c->has_y = (g.kind != SGEP_PCA && g.kind != SGEP_LDA);
   cudaError_t e = cudaGetDevice(&c->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
   if (e != cudaSuccess) {
@@ -228,7 +232,18 @@ int sgep_init(const sgep_config* cfg, sgep_t* out) {
   // Path selection.
   const char* why = nullptr;
   const bool cl_ok = cluster_supported(*c, &why);
-  if (g.path == SGEP_PATH_AUTO) {
+  if (g.kind == SGEP_LDA && g.path != SGEP_PATH_AUTO && g.path != SGEP_PATH_GENERIC) {
+    free_ctx(c);
+    return fail(SGEP_ENOTSUP, "LDA runs on the generic path only");
+  }
+  if (g.kind == SGEP_LDA) {
+    c->path = SGEP_PATH_GENERIC;
+    int rc = lda_alloc(*c);
+    if (rc) {
+      free_ctx(c);
+      return rc;
+    }
+  } else if (g.path == SGEP_PATH_AUTO) {
     c->path = cl_ok ? SGEP_PATH_CLUSTER : (tc_supported(*c, nullptr) ? SGEP_PATH_TC : SGEP_PATH_GENERIC);
   } else if (g.path == SGEP_PATH_CLUSTER) {
     if (!cl_ok) {
@@ -274,16 +289,17 @@ int sgep_destroy(sgep_t h) {
   return SGEP_OK;
 }
 
-static int step_checks(Ctx& c, const void* X, const void* Y, int64_t b) {
+static int step_checks(Ctx& c, const void* X, const void* Y, const int32_t* labels, int64_t b) {
   if (!X) return fail(SGEP_EINVAL, "X is NULL");
   if (c.has_y && !Y) return fail(SGEP_EINVAL, "Y is NULL");
-  const bool split = c.cfg.kind == SGEP_CCA && c.cfg.split_AB;
+  if (c.cfg.kind == SGEP_LDA && !labels) return fail(SGEP_EINVAL, "LDA needs labels");
+  const bool split = (c.cfg.kind == SGEP_CCA || c.cfg.kind == SGEP_LDA) && c.cfg.split_AB;
   if (b < (split ? 2 : 1)) return fail(SGEP_EINVAL, "b too small (split batches need b >= 2)");
   if (b > c.cfg.max_b) return fail(SGEP_EINVAL, "b exceeds max_b");
   return SGEP_OK;
 }
 
-static int do_step(Ctx& c, const void* X, const void* Y, int64_t b, cudaStream_t s) {
+static int do_step(Ctx& c, const void* X, const void* Y, const int32_t* labels, int64_t b, cudaStream_t s) {
   const int64_t t = c.t + 1;
   const float eta = (float)schedule_eta(c.cfg, t);
   const float gamma = c.cfg.gamma0;
@@ -296,7 +312,7 @@ static int do_step(Ctx& c, const void* X, const void* Y, int64_t b, cudaStream_t
       if (!rc && c.tc_generic_step) c.tc_chain = 0;
       if (!rc) rc = c.tc_generic_step ? generic_update(c, eta, gamma, s) : tc_update(c, eta, gamma, s);
     } else {
-      rc = generic_products(c, X, Y, b, s);
+      rc = c.cfg.kind == SGEP_LDA ? lda_products(c, X, labels, b, s) : generic_products(c, X, Y, b, s);
       if (!rc) rc = generic_update(c, eta, gamma, s);
     }
     if (!rc) c.debug_valid = c.cfg.debug;
@@ -306,25 +322,24 @@ static int do_step(Ctx& c, const void* X, const void* Y, int64_t b, cudaStream_t
 }
 
 int sgep_step(sgep_t h, const void* X, const void* Y, const int32_t* labels, int64_t b, void* stream) {
-  (void)labels;
   if (!h) return fail(SGEP_EINVAL, "handle is NULL");
-  int rc = step_checks(*h, X, Y, b);
+  int rc = step_checks(*h, X, Y, labels, b);
   if (rc) return rc;
-  return do_step(*h, X, Y, b, (cudaStream_t)stream);
+  return do_step(*h, X, Y, labels, b, (cudaStream_t)stream);
 }
 
 int sgep_step_many(sgep_t h, const void* X, const void* Y, const int32_t* labels, int64_t b,
                    int64_t nsteps, void* stream) {
-  (void)labels;
   if (!h) return fail(SGEP_EINVAL, "handle is NULL");
   if (nsteps < 0) return fail(SGEP_EINVAL, "nsteps < 0");
-  int rc = step_checks(*h, X, Y, b);
+  int rc = step_checks(*h, X, Y, labels, b);
   if (rc) return rc;
   const size_t esz = h->cfg.dtype == SGEP_BF16 ? 2 : 4;
   for (int64_t s = 0; s < nsteps; ++s) {
     const char* xs = (const char*)X + (size_t)s * b * h->d_x * esz;
     const char* ys = Y ? (const char*)Y + (size_t)s * b * h->d_y * esz : nullptr;
-    rc = do_step(*h, xs, ys, b, (cudaStream_t)stream);
+    const int32_t* ls = labels ? labels + s * b : nullptr;
+    rc = do_step(*h, xs, ys, ls, b, (cudaStream_t)stream);
     if (rc) return rc;
   }
   return SGEP_OK;
@@ -385,10 +400,11 @@ int sgep_set_V(sgep_t h, const float* V, int on_device, void* stream) {
 
 int sgep_get_eigenvalues(sgep_t h, const void* X, const void* Y, const int32_t* labels, int64_t n,
                          double* out_k, void* stream) {
-  (void)labels;
   if (!h) return fail(SGEP_EINVAL, "handle is NULL");
   Ctx& c = *h;
   if (!X || (c.has_y && !Y) || !out_k) return fail(SGEP_EINVAL, "NULL argument");
+  const bool lda = c.cfg.kind == SGEP_LDA;
+  if (lda && !labels) return fail(SGEP_EINVAL, "LDA needs labels");
   if (n < 1) return fail(SGEP_EINVAL, "n must be >= 1");
   cudaStream_t s = (cudaStream_t)stream;
   int rc = complete(c, s);
@@ -400,7 +416,8 @@ int sgep_get_eigenvalues(sgep_t h, const void* X, const void* Y, const int32_t* 
     const int64_t m = std::min<int64_t>(c.cfg.max_b, n - r0);
     const char* xs = (const char*)X + (size_t)r0 * c.d_x * esz;
     const char* ys = c.has_y ? (const char*)Y + (size_t)r0 * c.d_y * esz : nullptr;
-    rc = generic_project(c, xs, ys, m, s);
+    // LDA: rows centred by the running class means (the readout does not update them)
+    rc = lda ? generic_project(c, xs, ys, m, s, c.lda_mean, labels + r0) : generic_project(c, xs, ys, m, s);
     if (!rc) rc = generic_rayleigh_sums(c, m, s);
     if (rc) return rc;
   }
@@ -408,12 +425,28 @@ int sgep_get_eigenvalues(sgep_t h, const void* X, const void* Y, const int32_t* 
   std::vector<float> V((size_t)c.d * k);
   SGEP_CUDA_TRY(cudaMemcpyAsync(sums.data(), c.rq, sizeof(double) * 2 * k, cudaMemcpyDeviceToHost, s));
   SGEP_CUDA_TRY(cudaMemcpyAsync(V.data(), c.V, sizeof(float) * V.size(), cudaMemcpyDeviceToHost, s));
+  // LDA: v_i^T A v_i = sum_c pi_c ((mu_c - mu)^T v_i)^2 from the class statistics
+  const int C = lda ? c.cfg.n_classes : 0;
+  std::vector<float> W((size_t)C * k), pi(C);
+  if (lda) {
+    rc = lda_project_means(c, s);
+    if (rc) return rc;
+    SGEP_CUDA_TRY(cudaMemcpyAsync(W.data(), c.lda_W, sizeof(float) * W.size(), cudaMemcpyDeviceToHost, s));
+    SGEP_CUDA_TRY(cudaMemcpyAsync(pi.data(), c.lda_pi, sizeof(float) * C, cudaMemcpyDeviceToHost, s));
+  }
   SGEP_CUDA_TRY(cudaStreamSynchronize(s));
+  rc = check_flag(c);
+  if (rc) return rc;
   for (int i = 0; i < k; ++i) {
     double vv = 0.0;
     for (int64_t r = 0; r < c.d; ++r) vv += (double)V[r * k + i] * V[r * k + i];
     double num = sums[i] / (double)n;
     double den = c.b_is_identity ? vv : sums[k + i] / (double)n;
+    if (lda) {
+      num = 0.0;
+      for (int cl = 0; cl < C; ++cl) num += (double)pi[cl] * W[cl * k + i] * W[cl * k + i];
+      den = sums[i] / (double)n;  // sum of squared projections of the centred rows
+    }
     den += (double)c.cfg.eps_B * vv;
     out_k[i] = num / den;
   }
@@ -421,6 +454,11 @@ int sgep_get_eigenvalues(sgep_t h, const void* X, const void* Y, const int32_t* 
 }
 
 // State blob: header then V and S (float, d x k each).
+// LDA appends its class sums (C x d doubles) and counts (C doubles) to the state.
+static size_t lda_state_bytes(const Ctx& c) {
+  return c.cfg.kind == SGEP_LDA ? ((size_t)c.cfg.n_classes * c.d + c.cfg.n_classes) * sizeof(double) : 0;
+}
+
 struct StateHeader {
   char magic[8];
   int32_t version;
@@ -435,7 +473,7 @@ int sgep_get_state(sgep_t h, void* buf, size_t* nbytes) {
   if (!h || !nbytes) return fail(SGEP_EINVAL, "NULL argument");
   Ctx& c = *h;
   const size_t dk = (size_t)c.d * c.k;
-  const size_t need = sizeof(StateHeader) + 2 * dk * sizeof(float);
+  const size_t need = sizeof(StateHeader) + 2 * dk * sizeof(float) + lda_state_bytes(c);
   if (!buf) {
     *nbytes = need;
     return SGEP_OK;
@@ -457,6 +495,13 @@ int sgep_get_state(sgep_t h, void* buf, size_t* nbytes) {
   SGEP_CUDA_TRY(cudaMemcpy(p + sizeof(hd), c.V, dk * sizeof(float), cudaMemcpyDeviceToHost));
   SGEP_CUDA_TRY(cudaMemcpy(p + sizeof(hd) + dk * sizeof(float), c.S, dk * sizeof(float),
                            cudaMemcpyDeviceToHost));
+  if (c.cfg.kind == SGEP_LDA) {  // class sums, then counts
+    char* q = p + sizeof(hd) + 2 * dk * sizeof(float);
+    const size_t cd = (size_t)c.cfg.n_classes * c.d;
+    SGEP_CUDA_TRY(cudaMemcpy(q, c.lda_sum, cd * sizeof(double), cudaMemcpyDeviceToHost));
+    SGEP_CUDA_TRY(cudaMemcpy(q + cd * sizeof(double), c.lda_cnt, c.cfg.n_classes * sizeof(double),
+                             cudaMemcpyDeviceToHost));
+  }
   *nbytes = need;
   return SGEP_OK;
 }
@@ -472,13 +517,23 @@ int sgep_set_state(sgep_t h, const void* buf, size_t nbytes) {
     return fail(SGEP_ESTATE, "not a state blob of this version");
   if (hd.kind != c.cfg.kind || hd.d_x != c.d_x || hd.d_y != c.d_y || hd.k != c.k)
     return fail(SGEP_ESTATE, "state blob has a different kind or shape");
-  if (nbytes != sizeof(StateHeader) + 2 * dk * sizeof(float))
+  if (nbytes != sizeof(StateHeader) + 2 * dk * sizeof(float) + lda_state_bytes(c))
     return fail(SGEP_ESTATE, "state blob has the wrong size");
   int rc = complete(c, (cudaStream_t)0);
   if (rc) return rc;
   const char* p = (const char*)buf + sizeof(hd);
   SGEP_CUDA_TRY(cudaMemcpy(c.V, p, dk * sizeof(float), cudaMemcpyHostToDevice));
   SGEP_CUDA_TRY(cudaMemcpy(c.S, p + dk * sizeof(float), dk * sizeof(float), cudaMemcpyHostToDevice));
+  if (c.cfg.kind == SGEP_LDA) {
+    const char* q = p + 2 * dk * sizeof(float);
+    const size_t cd = (size_t)c.cfg.n_classes * c.d;
+    SGEP_CUDA_TRY(cudaMemcpy(c.lda_sum, q, cd * sizeof(double), cudaMemcpyHostToDevice));
+    SGEP_CUDA_TRY(cudaMemcpy(c.lda_cnt, q + cd * sizeof(double), c.cfg.n_classes * sizeof(double),
+                             cudaMemcpyHostToDevice));
+    rc = lda_refresh(c, (cudaStream_t)0);
+    if (rc) return rc;
+    SGEP_CUDA_TRY(cudaDeviceSynchronize());
+  }
   c.t = hd.t;
   c.debug_valid = 0;
   c.tc_chain = 0;

@@ -70,8 +70,12 @@ def test_init_rejects_shape_and_schedule_mismatch():
     assert L.sgep_init(ctypes.byref(cfg), ctypes.byref(h)) == S.SGEP_EINVAL
     cfg = S.sgep_config_default(d_x=8, d_y=8, k=2, schedule=2, t_c=10, T=5, eta_T=0.01)
     assert L.sgep_init(ctypes.byref(cfg), ctypes.byref(h)) == S.SGEP_EINVAL
-    cfg = S.sgep_config_default(kind=S.SGEP_LDA, d_x=8, d_y=0, k=2)
-    assert L.sgep_init(ctypes.byref(cfg), ctypes.byref(h)) == S.SGEP_ENOTSUP
+    cfg = S.sgep_config_default(kind=S.SGEP_LDA, d_x=8, d_y=0, k=2)  # n_classes missing
+    assert L.sgep_init(ctypes.byref(cfg), ctypes.byref(h)) == S.SGEP_EINVAL
+    cfg = S.sgep_config_default(kind=S.SGEP_LDA, d_x=8, d_y=2, k=2, n_classes=3)  # LDA has one view
+    assert L.sgep_init(ctypes.byref(cfg), ctypes.byref(h)) == S.SGEP_EINVAL
+    cfg = S.sgep_config_default(kind=S.SGEP_LDA, d_x=8, d_y=0, k=2, n_classes=33)
+    assert L.sgep_init(ctypes.byref(cfg), ctypes.byref(h)) == S.SGEP_EINVAL
 
 
 def test_init_without_gpu_fails_cleanly():
