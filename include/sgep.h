@@ -174,6 +174,20 @@ int sgep_set_VS(sgep_t h, const float* V, const float* S, int on_device, void* s
 int sgep_get_eigenvalues(sgep_t h, const void* X, const void* Y, const int32_t* labels,
                          int64_t n, double* out_k, void* stream);
 
+/* Rayleigh-Ritz correction (precision form): on the n evaluation rows (X, Y,
+ * labels as for sgep_get_eigenvalues; A and B estimated on all rows, in FP64
+ * sums of the FP32 row projections), solve the k x k pencil
+ * (V^T A V) c = lambda (V^T B V) c in FP64 on the device (Cholesky reduction and
+ * Jacobi, App. A), set V <- V C and [Bv] <- [Bv] C, and divide every column of
+ * both by ||v'_i|| (unit sphere). The players become the Ritz vectors of their
+ * span, ordered by descending Ritz value; lambda_out (host, k doubles, may be
+ * NULL) receives those values. The paper has no such step: it is a correction
+ * applied between iterations to win back accuracy lost to low-precision data.
+ * Synchronous. Errors: SGEP_EINVAL, SGEP_ENONFINITE (V^T B V not positive
+ * definite: V and [Bv] are then left unchanged), SGEP_ECUDA. */
+int sgep_rayleigh_ritz(sgep_t h, const void* X, const void* Y, const int32_t* labels,
+                       int64_t n, double* lambda_out, void* stream);
+
 /* Serialise the state (versioned header, V, [Bv], step counter; LDA also its
  * class sums, C x d doubles, and counts, C doubles) into `buf`.
  * If buf is NULL, only writes the required size to *nbytes. Synchronous. */

@@ -142,6 +142,34 @@ def lda_ops(X: np.ndarray, labels: np.ndarray, class_mean: np.ndarray,
 
 
 # ---------------------------------------------------------------------------
+# Rayleigh-Ritz correction of the current players (precision form)
+
+def rayleigh_ritz(V: np.ndarray, S: np.ndarray, Amv, Bmv):
+    """Rayleigh-Ritz step in the span of the players, in FP64.
+
+    Solves the k x k pencil (V^T A V) c = lambda (V^T B V) c (A and B estimated on an
+    evaluation batch, through the operators), with the Cholesky reduction and Jacobi
+    eigensolver of O1 (Prop. "Similar matrices", App. A), and rotates the players into
+    the Ritz vectors: V' = V C, [Bv]' = S C (the auxiliary variables follow the same
+    linear map), then every column of both is divided by ||v'_i|| (unit sphere).
+    Returns (V', S', lam) with lam descending; the columns of V' are ordered by lam
+    (signs are those of the k x k eigenvectors, unit Euclidean length in R^k).
+    """
+    from . import gep
+    V = np.asarray(V, dtype=np.float64)
+    S = np.asarray(S, dtype=np.float64)
+    k = V.shape[1]
+    Ak = V.T @ Amv(V)
+    Bk = V.T @ Bmv(V)
+    Ak = 0.5 * (Ak + Ak.T)
+    Bk = 0.5 * (Bk + Bk.T)
+    lam, C = gep.gep_topk(Ak, Bk, k)
+    Vn = V @ C
+    nrm = np.linalg.norm(Vn, axis=0)
+    return Vn / nrm[None, :], (S @ C) / nrm[None, :], lam
+
+
+# ---------------------------------------------------------------------------
 # Alg. 2 and Alg. 1
 
 def eg_step(V: np.ndarray, S: np.ndarray, Amv, Bmv, eta: float, gamma: float,

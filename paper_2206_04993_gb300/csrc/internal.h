@@ -86,6 +86,7 @@ struct Ctx {
   float* lda_M = nullptr;     // C x d mu_c - mu
   float* lda_pi = nullptr;    // C priors n_c / n
   float* lda_W = nullptr;     // C x k: (mu_c - mu)^T V
+  double* rr_buf = nullptr;   // Rayleigh-Ritz: k x k sums, C, eigenvalues, norms (FP64)
 
   int64_t t = 0;       // iterations applied (Alg. 2's t)
   int64_t launches = 0; // kernels launched
@@ -96,6 +97,7 @@ struct Ctx {
 constexpr int kFlagNonFinite = 1;
 constexpr int kFlagTimeout = 2;
 constexpr int kFlagBadLabel = 4;
+constexpr int kFlagNotPD = 8;    // Rayleigh-Ritz: V^T B V not positive definite
 constexpr int kMaxClasses = 32;  // LDA classes
 
 // Error reporting (thread-local message).
@@ -121,6 +123,10 @@ int generic_project(Ctx& c, const void* X, const void* Y, int64_t n, cudaStream_
                     const float* center = nullptr, const int32_t* labels = nullptr);
 // LDA: BV = X~^T (X~ V) / n over n rows centred by the class means (kernels_generic.cu).
 int generic_lda_within(Ctx& c, const void* X, const int32_t* labels, int64_t n, cudaStream_t s);
+
+// Rayleigh-Ritz correction of V and [Bv] on n evaluation rows (kernels_rr.cu).
+int rr_correct(Ctx& c, const void* X, const void* Y, const int32_t* labels, int64_t n, double* lam_host,
+               cudaStream_t s);
 
 // LDA (kernels_lda.cu): class statistics and the between-class products.
 int lda_alloc(Ctx& c);

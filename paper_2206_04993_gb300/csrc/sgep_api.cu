@@ -85,6 +85,7 @@ static void free_ctx(sgep_ctx* c) {
   cluster_free(*c);
   tc_free(*c);
   lda_free(*c);
+  cudaFree(c->rr_buf);
   cudaFree(c->V);
   cudaFree(c->S);
   cudaFree(c->Vtmp);
@@ -109,6 +110,8 @@ static int check_flag(Ctx& c) {
       return fail(SGEP_ETIMEOUT, "a bounded device-side wait gave up");
     }
     if (flag & kFlagBadLabel) return fail(SGEP_EINVAL, "a label is outside [0, n_classes)");
+    if (flag & kFlagNotPD)
+      return fail(SGEP_ENONFINITE, "V^T B V is not positive definite (players not independent)");
     if (flag & kFlagNonFinite) return fail(SGEP_ENONFINITE, "non-finite values in V");
   }
   return SGEP_OK;
@@ -468,6 +471,23 @@ struct StateHeader {
   int32_t pad;
   int64_t t;
 };
+
+int sgep_rayleigh_ritz(sgep_t h, const void* X, const void* Y, const int32_t* labels, int64_t n,
+                       double* lambda_out, void* stream) {
+  if (!h) return fail(SGEP_EINVAL, "handle is NULL");
+  Ctx& c = *h;
+  if (!X || (c.has_y && !Y)) return fail(SGEP_EINVAL, "NULL argument");
+  if (c.cfg.kind == SGEP_LDA && !labels) return fail(SGEP_EINVAL, "LDA needs labels");
+  if (n < 1) return fail(SGEP_EINVAL, "n must be >= 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = complete(c, s);
+  if (rc) return rc;
+  rc = rr_correct(c, X, Y, labels, n, lambda_out, s);
+  c.tc_chain = 0;  // V and [Bv] changed outside the step
+  c.debug_valid = 0;
+  if (rc) return rc;
+  return check_flag(c);
+}
 
 int sgep_get_state(sgep_t h, void* buf, size_t* nbytes) {
   if (!h || !nbytes) return fail(SGEP_EINVAL, "NULL argument");

@@ -58,6 +58,7 @@ _SIGS = {
     "sgep_set_V": (ctypes.c_int, [_P, _P, ctypes.c_int, _P]),
     "sgep_set_VS": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
     "sgep_get_eigenvalues": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, _P, _P]),
+    "sgep_rayleigh_ritz": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, _P, _P]),
     "sgep_get_state": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_size_t)]),
     "sgep_set_state": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
     "sgep_step_count": (ctypes.c_int64, [_P]),
@@ -176,6 +177,11 @@ def sgep_set_V(h, V, on_device: bool, stream=None) -> None:
 
 def sgep_set_VS(h, V, S, on_device: bool, stream=None) -> None:
     check(lib().sgep_set_VS(h, _ptr(V), _ptr(S), int(on_device), _stream(stream)), "sgep_set_VS")
+
+
+def sgep_rayleigh_ritz(h, X, Y, n, out=None, labels=None, stream=None) -> None:
+    check(lib().sgep_rayleigh_ritz(h, _ptr(X), _ptr(Y), _ptr(labels), int(n), _ptr(out),
+                                   _stream(stream)), "sgep_rayleigh_ritz")
 
 
 def sgep_get_eigenvalues(h, X, Y, n, out, labels=None, stream=None) -> None:

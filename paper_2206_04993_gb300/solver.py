@@ -70,6 +70,12 @@ class Solver:
         _s.sgep_get_eigenvalues(self.h, X, Y, X.shape[0], out, labels, self._cur_stream())
         return out
 
+    def rayleigh_ritz(self, X, Y=None, labels=None) -> np.ndarray:
+        """Rotate the players into the Ritz vectors of their span on rows (X, Y); Ritz values."""
+        out = np.empty(self.k, dtype=np.float64)
+        _s.sgep_rayleigh_ritz(self.h, X, Y, X.shape[0], out, labels, self._cur_stream())
+        return out
+
     def products(self):
         AV = np.empty((self.d, self.k), dtype=np.float32)
         BV = np.empty((self.d, self.k), dtype=np.float32)
