@@ -24,7 +24,9 @@
  *  - Data matrices are row-major, one sample per row: X is b x d_x, Y is
  *    b x d_y, element (r, c) at X[r * d_x + c]. Their element type is the
  *    handle's dtype (float for SGEP_F32, bfloat16 bit patterns for
- *    SGEP_BF16). They are caller-owned DEVICE pointers and must stay valid
+ *    SGEP_BF16, FP8 e4m3 bytes for SGEP_FP8E4M3 together with one float
+ *    scale per row: the row's values are scale_r * e4m3(code)). They are
+ *    caller-owned DEVICE pointers and must stay valid
  *    until the work on `stream` has completed.
  *  - The player matrix V (and [Bv], called S here) is d x k row-major float:
  *    element (c, i) at V[c * k + i], so column i is the player vector v_i
@@ -65,8 +67,9 @@ extern "C" {
  * n_classes - 1 generalized eigenvalues are nonzero. */
 
 /* ---- element type of X and Y ------------------------------------------- */
-#define SGEP_F32  0
-#define SGEP_BF16 1
+#define SGEP_F32      0
+#define SGEP_BF16     1
+#define SGEP_FP8E4M3  2  /* e4m3 codes with per-row float scales (generic path) */
 
 /* ---- step-size schedules (App. H.2.2) ----------------------------------- */
 #define SGEP_SCHED_CONST          0  /* eta_t = eta0                                   */
@@ -85,7 +88,7 @@ typedef struct sgep_ctx* sgep_t;
  * and override fields; unknown future fields keep their defaults. */
 typedef struct {
   int32_t  kind;       /* SGEP_PCA / SGEP_CCA / SGEP_PLS                          */
-  int32_t  dtype;      /* SGEP_F32 or SGEP_BF16 (element type of X, Y)            */
+  int32_t  dtype;      /* SGEP_F32, SGEP_BF16 or SGEP_FP8E4M3 (element type of X, Y) */
   int64_t  d_x;        /* columns of X (>= 1)                                      */
   int64_t  d_y;        /* columns of Y (>= 1 for CCA/PLS, must be 0 for PCA)       */
   int32_t  k;          /* number of players, 1 <= k <= 64 and k <= d              */
@@ -129,20 +132,24 @@ int sgep_destroy(sgep_t h);
  * the update direction is Eq. (update) with the clipped auxiliary terms,
  * v_i <- (v_i + eta_t grad_i) / ||.||, [Bv]_i <- [Bv]_i + gamma_t (B_t v_i - [Bv]_i),
  * all players reading the state of step t. Asynchronous on `stream`.
- * X: device, b x d_x; Y: device, b x d_y (NULL for PCA and LDA); labels: LDA
+ * X: device, b x d_x; Y: device, b x d_y (NULL for PCA and LDA);
+ * row_scale_x, row_scale_y: FP8E4M3 only, device, b floats each (NULL for the
+ * other dtypes and for a missing view); labels: LDA
  * only, device, b int32 class labels in [0, n_classes) (NULL otherwise). A label
  * outside the range is reported as SGEP_EINVAL by the next synchronising call
  * (its row is then left uncentred; no out-of-bounds access happens).
  * Requires 2 <= b <= max_b when split_AB = 1 (1 <= b otherwise).
  * The work of a step may be completed lazily by the next step or by the
  * next synchronising call. Errors: SGEP_EINVAL, SGEP_ECUDA, SGEP_ELAUNCH. */
-int sgep_step(sgep_t h, const void* X, const void* Y, const int32_t* labels,
-              int64_t b, void* stream);
+int sgep_step(sgep_t h, const void* X, const void* Y, const float* row_scale_x,
+              const float* row_scale_y, const int32_t* labels, int64_t b, void* stream);
 
 /* `nsteps` consecutive iterations on minibatches stored back to back:
- * step s reads rows [s*b, (s+1)*b) of X and Y (and labels). Same contract as sgep_step. */
-int sgep_step_many(sgep_t h, const void* X, const void* Y, const int32_t* labels,
-                   int64_t b, int64_t nsteps, void* stream);
+ * step s reads rows [s*b, (s+1)*b) of X and Y (and of the row scales and labels).
+ * Same contract as sgep_step. */
+int sgep_step_many(sgep_t h, const void* X, const void* Y, const float* row_scale_x,
+                   const float* row_scale_y, const int32_t* labels, int64_t b, int64_t nsteps,
+                   void* stream);
 
 /* Wait for the handle's work on `stream` and report device-side errors
  * (SGEP_ENONFINITE, SGEP_ETIMEOUT). Clears the recorded error. */
@@ -171,8 +178,9 @@ int sgep_set_VS(sgep_t h, const float* V, const float* S, int on_device, void* s
  * not update them) and <v_i, B v_i> from the n rows centred by their class
  * means; labels (device, n int32) are required.
  * Synchronous. Any n >= 1 (processed in chunks of max_b rows). */
-int sgep_get_eigenvalues(sgep_t h, const void* X, const void* Y, const int32_t* labels,
-                         int64_t n, double* out_k, void* stream);
+int sgep_get_eigenvalues(sgep_t h, const void* X, const void* Y, const float* row_scale_x,
+                         const float* row_scale_y, const int32_t* labels, int64_t n,
+                         double* out_k, void* stream);
 
 /* Rayleigh-Ritz correction (precision form): on the n evaluation rows (X, Y,
  * labels as for sgep_get_eigenvalues; A and B estimated on all rows, in FP64
@@ -185,8 +193,9 @@ int sgep_get_eigenvalues(sgep_t h, const void* X, const void* Y, const int32_t* 
  * applied between iterations to win back accuracy lost to low-precision data.
  * Synchronous. Errors: SGEP_EINVAL, SGEP_ENONFINITE (V^T B V not positive
  * definite: V and [Bv] are then left unchanged), SGEP_ECUDA. */
-int sgep_rayleigh_ritz(sgep_t h, const void* X, const void* Y, const int32_t* labels,
-                       int64_t n, double* lambda_out, void* stream);
+int sgep_rayleigh_ritz(sgep_t h, const void* X, const void* Y, const float* row_scale_x,
+                       const float* row_scale_y, const int32_t* labels, int64_t n,
+                       double* lambda_out, void* stream);
 
 /* Serialise the state (versioned header, V, [Bv], step counter; LDA also its
  * class sums, C x d doubles, and counts, C doubles) into `buf`.

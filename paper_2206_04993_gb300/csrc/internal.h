@@ -115,24 +115,31 @@ double schedule_eta(const sgep_config& c, int64_t t);
 
 // ---- generic SIMT path (kernels_generic.cu) ----
 // Products of one minibatch: acc <- [A_t V ; B_t V], PQ scratch.
-int generic_products(Ctx& c, const void* X, const void* Y, int64_t b, cudaStream_t s);
+// Bytes per element of X and Y for the handle's dtype.
+inline size_t elem_size(const Ctx& c) { return c.cfg.dtype == SGEP_F32 ? 4 : (c.cfg.dtype == SGEP_BF16 ? 2 : 1); }
+
+int generic_products(Ctx& c, const void* X, const void* Y, int64_t b, cudaStream_t s,
+                     const float* sx = nullptr, const float* sy = nullptr);
 // Update from acc: grams, update, retraction. eta/gamma of this step.
 int generic_update(Ctx& c, float eta, float gamma, cudaStream_t s);
 // Row projections of n rows into PQ (n <= max_b), zeroing PQ first.
+// sx, sy: per-row scales of FP8 rows (null otherwise); center/labels: LDA centring.
 int generic_project(Ctx& c, const void* X, const void* Y, int64_t n, cudaStream_t s,
-                    const float* center = nullptr, const int32_t* labels = nullptr);
+                    const float* center = nullptr, const int32_t* labels = nullptr, const float* sx = nullptr,
+                    const float* sy = nullptr);
 // LDA: BV = X~^T (X~ V) / n over n rows centred by the class means (kernels_generic.cu).
-int generic_lda_within(Ctx& c, const void* X, const int32_t* labels, int64_t n, cudaStream_t s);
+int generic_lda_within(Ctx& c, const void* X, const int32_t* labels, int64_t n, cudaStream_t s,
+                       const float* sx = nullptr);
 
 // Rayleigh-Ritz correction of V and [Bv] on n evaluation rows (kernels_rr.cu).
-int rr_correct(Ctx& c, const void* X, const void* Y, const int32_t* labels, int64_t n, double* lam_host,
-               cudaStream_t s);
+int rr_correct(Ctx& c, const void* X, const void* Y, const float* sx, const float* sy, const int32_t* labels,
+               int64_t n, double* lam_host, cudaStream_t s);
 
 // LDA (kernels_lda.cu): class statistics and the between-class products.
 int lda_alloc(Ctx& c);
 void lda_free(Ctx& c);
 // Adds the minibatch rows to the class statistics, then acc = [A_t V ; B_t V].
-int lda_products(Ctx& c, const void* X, const int32_t* labels, int64_t b, cudaStream_t s);
+int lda_products(Ctx& c, const void* X, const int32_t* labels, int64_t b, cudaStream_t s, const float* sx);
 // Recomputes means, mu_c - mu and priors from the sums and counts (after a state load).
 int lda_refresh(Ctx& c, cudaStream_t s);
 // W = (mu_c - mu)^T V into lda_W (C x k) for the current V.

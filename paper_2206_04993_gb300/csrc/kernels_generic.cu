@@ -9,8 +9,10 @@
 // It handles every shape (any d_x, d_y, b, 1 <= k <= 64) and both element
 // types; the fused cluster and tensor-core paths are checked against it.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "eg_math.cuh"
 #include "internal.h"
@@ -24,6 +26,14 @@ constexpr int kMaxK = 64;
 __device__ __forceinline__ float load_elem(const float* p, int64_t i) { return __ldg(p + i); }
 __device__ __forceinline__ float load_elem(const __nv_bfloat16* p, int64_t i) {
   return __bfloat162float(p[i]);
+}
+__device__ __forceinline__ float load_elem(const __nv_fp8_e4m3* p, int64_t i) { return static_cast<float>(p[i]); }
+
+// Element (row, i) of a row-major matrix, times the row's scale when there is one (FP8 rows).
+template <typename T>
+__device__ __forceinline__ float load_row_elem(const T* p, const float* scale, int64_t row, int64_t i) {
+  const float x = load_elem(p, i);
+  return scale ? x * scale[row] : x;
 }
 
 // Class-mean centring of LDA rows: x - mu_{label}. A label outside [0, C) is
@@ -54,7 +64,9 @@ __global__ void __launch_bounds__(kThreads) k_project(const T* __restrict__ X, c
                                                       int64_t n, int64_t dx, int64_t dy,
                                                       const float* __restrict__ V, int k,
                                                       int64_t chunk, int nchunk_x,
-                                                      float* __restrict__ PQ, const Centring cz) {
+                                                      float* __restrict__ PQ, const Centring cz,
+                                                      const float* __restrict__ rsx,
+                                                      const float* __restrict__ rsy) {
   constexpr int BR = 32, TC = 32;
   __shared__ float Xs[BR][TC + 1];
   __shared__ float Vs[TC][kMaxK];
@@ -65,6 +77,7 @@ __global__ void __launch_bounds__(kThreads) k_project(const T* __restrict__ X, c
   const bool isY = (int)blockIdx.y >= nchunk_x;
   const int cidx = isY ? (int)blockIdx.y - nchunk_x : (int)blockIdx.y;
   const T* Z = isY ? Y : X;
+  const float* rs = isY ? rsy : rsx;
   const int64_t ld = isY ? dy : dx;
   const int64_t voff = isY ? dx : 0;
   const int64_t c_begin = (int64_t)cidx * chunk;
@@ -77,7 +90,8 @@ __global__ void __launch_bounds__(kThreads) k_project(const T* __restrict__ X, c
     for (int e = tid; e < BR * TC; e += kThreads) {
       const int rr = e / TC, cc = e % TC;
       const int64_t row = row0 + rr, col = c0 + cc;
-      Xs[rr][cc] = (row < n && col < c_end) ? centred(cz, load_elem(Z, row * ld + col), row, ld, col) : 0.f;
+      Xs[rr][cc] =
+          (row < n && col < c_end) ? centred(cz, load_row_elem(Z, rs, row, row * ld + col), row, ld, col) : 0.f;
     }
     for (int e = tid; e < TC * k; e += kThreads) {
       const int cc = e / k, i = e % k;
@@ -119,7 +133,7 @@ __global__ void __launch_bounds__(kThreads) k_backproject(
     const T* __restrict__ X, const T* __restrict__ Y, int64_t b, int64_t dx, int64_t dy,
     int64_t nA, int kind, int split, const float* __restrict__ PQ, int k, int nblk_x,
     int64_t rows_per_split, float inv_nA, float inv_nB, float* __restrict__ AV,
-    float* __restrict__ BV, const Centring cz) {
+    float* __restrict__ BV, const Centring cz, const float* __restrict__ rsx, const float* __restrict__ rsy) {
   constexpr int TR = 32, CB = 64;
   __shared__ float Zs[TR][CB];
   __shared__ float Ws[TR][2 * kMaxK];
@@ -129,6 +143,7 @@ __global__ void __launch_bounds__(kThreads) k_backproject(
   const bool isY = (int)blockIdx.x >= nblk_x;
   const int bidx = isY ? (int)blockIdx.x - nblk_x : (int)blockIdx.x;
   const T* Z = isY ? Y : X;
+  const float* rs = isY ? rsy : rsx;
   const int64_t ld = isY ? dy : dx;
   const int64_t col = (int64_t)bidx * CB + cl;
   const int64_t r_begin = (int64_t)blockIdx.y * rows_per_split;
@@ -146,7 +161,8 @@ __global__ void __launch_bounds__(kThreads) k_backproject(
     for (int e = tid; e < TR * CB; e += kThreads) {
       const int rr = e / CB, cc = e % CB;
       const int64_t row = r0 + rr, cg = (int64_t)bidx * CB + cc;
-      Zs[rr][cc] = (row < r_end && cg < ld) ? centred(cz, load_elem(Z, row * ld + cg), row, ld, cg) : 0.f;
+      Zs[rr][cc] =
+          (row < r_end && cg < ld) ? centred(cz, load_row_elem(Z, rs, row, row * ld + cg), row, ld, cg) : 0.f;
     }
     for (int e = tid; e < TR * 2 * k; e += kThreads) {
       const int rr = e / (2 * k), j = e % (2 * k);
@@ -361,7 +377,8 @@ __global__ void k_rayleigh(const float* __restrict__ PQ, int64_t n, int k, int k
 inline int grid_cap(const Ctx& c, int per_sm) { return c.num_sms * per_sm; }
 
 template <typename T>
-int launch_project(Ctx& c, const T* X, const T* Y, int64_t n, cudaStream_t s, const Centring& cz) {
+int launch_project(Ctx& c, const T* X, const T* Y, int64_t n, cudaStream_t s, const Centring& cz,
+                   const float* sx, const float* sy) {
   const int64_t row_tiles = (n + 31) / 32;
   // Column chunk: enough blocks to fill the GPU, at least 32 columns each.
   int64_t chunk = 1024;
@@ -369,14 +386,15 @@ int launch_project(Ctx& c, const T* X, const T* Y, int64_t n, cudaStream_t s, co
   const int nchunk_x = (int)((c.d_x + chunk - 1) / chunk);
   const int nchunk_y = c.has_y ? (int)((c.d_y + chunk - 1) / chunk) : 0;
   dim3 grid((unsigned)row_tiles, (unsigned)(nchunk_x + nchunk_y));
-  k_project<T><<<grid, kThreads, 0, s>>>(X, Y, n, c.d_x, c.d_y, c.V, c.k, chunk, nchunk_x, c.PQ, cz);
+  k_project<T><<<grid, kThreads, 0, s>>>(X, Y, n, c.d_x, c.d_y, c.V, c.k, chunk, nchunk_x, c.PQ, cz, sx, sy);
   SGEP_CUDA_TRY(cudaGetLastError());
   ++c.launches;
   return SGEP_OK;
 }
 
 template <typename T>
-int launch_backproject(Ctx& c, const T* X, const T* Y, int64_t b, cudaStream_t s, const Centring& cz) {
+int launch_backproject(Ctx& c, const T* X, const T* Y, int64_t b, cudaStream_t s, const Centring& cz,
+                       const float* sx, const float* sy) {
   const int kind = c.cfg.kind;
   const bool cca = kind == SGEP_CCA;
   const int split = (cca && c.cfg.split_AB) ? 1 : 0;
@@ -395,7 +413,7 @@ int launch_backproject(Ctx& c, const T* X, const T* Y, int64_t b, cudaStream_t s
   float* BV = c.acc + c.d * c.k;
   k_backproject<T><<<grid, kThreads, 0, s>>>(X, Y, b, c.d_x, c.d_y, nA, kind, split, c.PQ, c.k,
                                              nblk_x, rows_per_split, 1.f / (float)nA,
-                                             1.f / (float)nB, AV, BV, cz);
+                                             1.f / (float)nB, AV, BV, cz, sx, sy);
   SGEP_CUDA_TRY(cudaGetLastError());
   ++c.launches;
   return SGEP_OK;
@@ -403,33 +421,45 @@ int launch_backproject(Ctx& c, const T* X, const T* Y, int64_t b, cudaStream_t s
 
 }  // namespace
 
+// Dispatch on the handle's element type.
+template <typename F>
+int by_dtype(const Ctx& c, F&& f) {
+  if (c.cfg.dtype == SGEP_BF16) return f(static_cast<const __nv_bfloat16*>(nullptr));
+  if (c.cfg.dtype == SGEP_FP8E4M3) return f(static_cast<const __nv_fp8_e4m3*>(nullptr));
+  return f(static_cast<const float*>(nullptr));
+}
+
 int generic_project(Ctx& c, const void* X, const void* Y, int64_t n, cudaStream_t s, const float* center,
-                    const int32_t* labels) {
+                    const int32_t* labels, const float* sx, const float* sy) {
   SGEP_CUDA_TRY(cudaMemsetAsync(c.PQ, 0, sizeof(float) * n * 2 * c.k, s));
   const Centring cz{center, labels, c.cfg.n_classes, c.dflag};
-  if (c.cfg.dtype == SGEP_BF16)
-    return launch_project<__nv_bfloat16>(c, (const __nv_bfloat16*)X, (const __nv_bfloat16*)Y, n, s, cz);
-  return launch_project<float>(c, (const float*)X, (const float*)Y, n, s, cz);
+  return by_dtype(c, [&](auto tag) {
+    using T = std::remove_const_t<std::remove_pointer_t<decltype(tag)>>;
+    return launch_project<T>(c, (const T*)X, (const T*)Y, n, s, cz, sx, sy);
+  });
 }
 
 // LDA: BV = X~^T (X~ V) / n over the n rows passed (already the B rows), centred by class means.
-int generic_lda_within(Ctx& c, const void* X, const int32_t* labels, int64_t n, cudaStream_t s) {
-  int rc = generic_project(c, X, nullptr, n, s, c.lda_mean, labels);
+int generic_lda_within(Ctx& c, const void* X, const int32_t* labels, int64_t n, cudaStream_t s, const float* sx) {
+  int rc = generic_project(c, X, nullptr, n, s, c.lda_mean, labels, sx, nullptr);
   if (rc) return rc;
   const Centring cz{c.lda_mean, labels, c.cfg.n_classes, c.dflag};
-  if (c.cfg.dtype == SGEP_BF16)
-    return launch_backproject<__nv_bfloat16>(c, (const __nv_bfloat16*)X, nullptr, n, s, cz);
-  return launch_backproject<float>(c, (const float*)X, nullptr, n, s, cz);
+  return by_dtype(c, [&](auto tag) {
+    using T = std::remove_const_t<std::remove_pointer_t<decltype(tag)>>;
+    return launch_backproject<T>(c, (const T*)X, nullptr, n, s, cz, sx, nullptr);
+  });
 }
 
-int generic_products(Ctx& c, const void* X, const void* Y, int64_t b, cudaStream_t s) {
-  int rc = generic_project(c, X, Y, b, s);
+int generic_products(Ctx& c, const void* X, const void* Y, int64_t b, cudaStream_t s, const float* sx,
+                     const float* sy) {
+  int rc = generic_project(c, X, Y, b, s, nullptr, nullptr, sx, sy);
   if (rc) return rc;
   SGEP_CUDA_TRY(cudaMemsetAsync(c.acc, 0, sizeof(float) * 2 * c.d * c.k, s));
   const Centring none{nullptr, nullptr, 0, c.dflag};
-  if (c.cfg.dtype == SGEP_BF16)
-    return launch_backproject<__nv_bfloat16>(c, (const __nv_bfloat16*)X, (const __nv_bfloat16*)Y, b, s, none);
-  return launch_backproject<float>(c, (const float*)X, (const float*)Y, b, s, none);
+  return by_dtype(c, [&](auto tag) {
+    using T = std::remove_const_t<std::remove_pointer_t<decltype(tag)>>;
+    return launch_backproject<T>(c, (const T*)X, (const T*)Y, b, s, none, sx, sy);
+  });
 }
 
 int generic_update(Ctx& c, float eta, float gamma, cudaStream_t s) {

@@ -10,6 +10,8 @@
 // A V therefore costs O(C d k) from the class means (no pass over the rows):
 //   W = (mu_c - mu)^T V  (C x k),   A V = sum_c (mu_c - mu) pi_c W_c.
 // The k x k terms and the update are the generic ones.
+#include <cuda_fp8.h>
+
 #include <algorithm>
 
 #include "internal.h"
@@ -21,6 +23,7 @@ constexpr int kThreads = 256;
 
 __device__ __forceinline__ float load_x(const float* p, int64_t i) { return __ldg(p + i); }
 __device__ __forceinline__ float load_x(const __nv_bfloat16* p, int64_t i) { return __bfloat162float(p[i]); }
+__device__ __forceinline__ float load_x(const __nv_fp8_e4m3* p, int64_t i) { return static_cast<float>(p[i]); }
 
 // Counts of this minibatch's labels added to the running counts; priors. One block.
 __global__ void k_lda_counts(const int32_t* __restrict__ labels, int64_t b, int C, double* __restrict__ cnt,
@@ -53,7 +56,8 @@ __global__ void k_lda_counts(const int32_t* __restrict__ labels, int64_t b, int 
 // mu_c - mu and the class means used for centring. grid: ceil(d / 256) blocks, one
 // column per thread; dynamic shared memory C x 256 floats.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_lda_stats(const T* __restrict__ X, const int32_t* __restrict__ labels,
+__global__ void __launch_bounds__(kThreads) k_lda_stats(const T* __restrict__ X, const float* __restrict__ rs,
+                                                        const int32_t* __restrict__ labels,
                                                         int64_t b, int64_t d, int C, double* __restrict__ sum,
                                                         const double* __restrict__ cnt, float* __restrict__ mean,
                                                         float* __restrict__ M) {
@@ -75,7 +79,7 @@ __global__ void __launch_bounds__(kThreads) k_lda_stats(const T* __restrict__ X,
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const int64_t row = r0 + q0 + q;
-          x[q] = (q0 + q < nr) ? load_x(X, row * d + col) : 0.f;
+          x[q] = (q0 + q < nr) ? load_x(X, row * d + col) * (rs ? rs[row] : 1.f) : 0.f;
         }
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
@@ -188,24 +192,27 @@ void lda_free(Ctx& c) {
   c.lda_mean = c.lda_M = c.lda_pi = c.lda_W = nullptr;
 }
 
-static int stats(Ctx& c, const void* X, const int32_t* labels, int64_t b, cudaStream_t s) {
+static int stats(Ctx& c, const void* X, const int32_t* labels, int64_t b, cudaStream_t s, const float* sx) {
   const int C = c.cfg.n_classes;
   k_lda_counts<<<1, kThreads, 0, s>>>(labels, b, C, c.lda_cnt, c.lda_pi, c.dflag);
   SGEP_CUDA_TRY(cudaGetLastError());
   const unsigned grid = (unsigned)((c.d + kThreads - 1) / kThreads);
   const size_t smem = (size_t)C * kThreads * sizeof(float);
   if (c.cfg.dtype == SGEP_BF16)
-    k_lda_stats<__nv_bfloat16><<<grid, kThreads, smem, s>>>((const __nv_bfloat16*)X, labels, b, c.d, C, c.lda_sum,
-                                                            c.lda_cnt, c.lda_mean, c.lda_M);
+    k_lda_stats<__nv_bfloat16><<<grid, kThreads, smem, s>>>((const __nv_bfloat16*)X, sx, labels, b, c.d, C,
+                                                            c.lda_sum, c.lda_cnt, c.lda_mean, c.lda_M);
+  else if (c.cfg.dtype == SGEP_FP8E4M3)
+    k_lda_stats<__nv_fp8_e4m3><<<grid, kThreads, smem, s>>>((const __nv_fp8_e4m3*)X, sx, labels, b, c.d, C,
+                                                            c.lda_sum, c.lda_cnt, c.lda_mean, c.lda_M);
   else
-    k_lda_stats<float><<<grid, kThreads, smem, s>>>((const float*)X, labels, b, c.d, C, c.lda_sum, c.lda_cnt,
+    k_lda_stats<float><<<grid, kThreads, smem, s>>>((const float*)X, sx, labels, b, c.d, C, c.lda_sum, c.lda_cnt,
                                                     c.lda_mean, c.lda_M);
   SGEP_CUDA_TRY(cudaGetLastError());
   c.launches += 2;
   return SGEP_OK;
 }
 
-int lda_refresh(Ctx& c, cudaStream_t s) { return stats(c, nullptr, nullptr, 0, s); }
+int lda_refresh(Ctx& c, cudaStream_t s) { return stats(c, nullptr, nullptr, 0, s, nullptr); }
 
 int lda_project_means(Ctx& c, cudaStream_t s) {
   SGEP_CUDA_TRY(cudaMemsetAsync(c.lda_W, 0, (size_t)c.cfg.n_classes * c.k * sizeof(float), s));
@@ -216,14 +223,14 @@ int lda_project_means(Ctx& c, cudaStream_t s) {
   return SGEP_OK;
 }
 
-int lda_products(Ctx& c, const void* X, const int32_t* labels, int64_t b, cudaStream_t s) {
-  int rc = stats(c, X, labels, b, s);
+int lda_products(Ctx& c, const void* X, const int32_t* labels, int64_t b, cudaStream_t s, const float* sx) {
+  int rc = stats(c, X, labels, b, s, sx);
   if (rc) return rc;
   SGEP_CUDA_TRY(cudaMemsetAsync(c.acc, 0, sizeof(float) * 2 * c.d * c.k, s));
   // B_t V from the B rows (second half when the batch is split), centred by class means
   const int64_t nA = c.cfg.split_AB ? b / 2 : 0;
-  const size_t esz = c.cfg.dtype == SGEP_BF16 ? 2 : 4;
-  rc = generic_lda_within(c, (const char*)X + (size_t)nA * c.d * esz, labels + nA, b - nA, s);
+  rc = generic_lda_within(c, (const char*)X + (size_t)nA * c.d * elem_size(c), labels + nA, b - nA, s,
+                          sx ? sx + nA : nullptr);
   if (rc) return rc;
   // A V from the class means
   rc = lda_project_means(c, s);

@@ -357,8 +357,8 @@ __global__ void k_rr_scale(const float* __restrict__ Vtmp, float* __restrict__ V
 
 }  // namespace
 
-int rr_correct(Ctx& c, const void* X, const void* Y, const int32_t* labels, int64_t n, double* lam_host,
-               cudaStream_t s) {
+int rr_correct(Ctx& c, const void* X, const void* Y, const float* sx, const float* sy, const int32_t* labels,
+               int64_t n, double* lam_host, cudaStream_t s) {
   const int k = c.k, kk = k * k;
   if (!c.rr_buf) SGEP_CUDA_TRY(cudaMalloc((void**)&c.rr_buf, (size_t)(4 * kk + 2 * k) * sizeof(double)));
   double* Asum = c.rr_buf;
@@ -370,12 +370,14 @@ int rr_correct(Ctx& c, const void* X, const void* Y, const int32_t* labels, int6
   SGEP_CUDA_TRY(cudaMemsetAsync(c.rr_buf, 0, (size_t)(4 * kk + 2 * k) * sizeof(double), s));
   const int kind = c.cfg.kind;
   const bool lda = kind == SGEP_LDA;
-  const size_t esz = c.cfg.dtype == SGEP_BF16 ? 2 : 4;
+  const size_t esz = elem_size(c);
   for (int64_t r0 = 0; r0 < n; r0 += c.cfg.max_b) {
     const int64_t m = std::min<int64_t>(c.cfg.max_b, n - r0);
     const char* xs = (const char*)X + (size_t)r0 * c.d_x * esz;
     const char* ys = c.has_y ? (const char*)Y + (size_t)r0 * c.d_y * esz : nullptr;
-    int rc = lda ? generic_project(c, xs, ys, m, s, c.lda_mean, labels + r0) : generic_project(c, xs, ys, m, s);
+    const float* sxs = sx ? sx + r0 : nullptr;
+    const float* sys = sy ? sy + r0 : nullptr;
+    int rc = generic_project(c, xs, ys, m, s, lda ? c.lda_mean : nullptr, lda ? labels + r0 : nullptr, sxs, sys);
     if (rc) return rc;
     const int grid = (int)std::min<int64_t>((m + 31) / 32, 2LL * c.num_sms);
     k_rr_gram_pq<<<grid, kThreads, (size_t)32 * 2 * k * sizeof(float), s>>>(c.PQ, m, k, kind, Asum, Bsum);

@@ -168,7 +168,8 @@ int sgep_init(const sgep_config* cfg, sgep_t* out) {
     return fail(SGEP_EINVAL, "unknown kind");
   if (g.kind == SGEP_LDA && (g.n_classes < 2 || g.n_classes > kMaxClasses))
     return fail(SGEP_EINVAL, "LDA needs 2 <= n_classes <= 32");
-  if (g.dtype != SGEP_F32 && g.dtype != SGEP_BF16) return fail(SGEP_EINVAL, "unknown dtype");
+  if (g.dtype != SGEP_F32 && g.dtype != SGEP_BF16 && g.dtype != SGEP_FP8E4M3)
+    return fail(SGEP_EINVAL, "unknown dtype");
   if (g.d_x < 1) return fail(SGEP_EINVAL, "d_x must be >= 1");
   const bool one_view = g.kind == SGEP_PCA || g.kind == SGEP_LDA;
   if (one_view && g.d_y != 0) return fail(SGEP_EINVAL, "PCA and LDA require d_y = 0");
@@ -235,17 +236,20 @@ int sgep_init(const sgep_config* cfg, sgep_t* out) {
   // Path selection.
   const char* why = nullptr;
   const bool cl_ok = cluster_supported(*c, &why);
-  if (g.kind == SGEP_LDA && g.path != SGEP_PATH_AUTO && g.path != SGEP_PATH_GENERIC) {
+  const bool generic_only = g.kind == SGEP_LDA || g.dtype == SGEP_FP8E4M3;
+  if (generic_only && g.path != SGEP_PATH_AUTO && g.path != SGEP_PATH_GENERIC) {
     free_ctx(c);
-    return fail(SGEP_ENOTSUP, "LDA runs on the generic path only");
+    return fail(SGEP_ENOTSUP, "LDA and FP8 rows run on the generic path only");
   }
+  if (generic_only) c->path = SGEP_PATH_GENERIC;
   if (g.kind == SGEP_LDA) {
-    c->path = SGEP_PATH_GENERIC;
     int rc = lda_alloc(*c);
     if (rc) {
       free_ctx(c);
       return rc;
     }
+  } else if (generic_only) {
+    // FP8 rows: the generic kernels dequantise with the per-row scales
   } else if (g.path == SGEP_PATH_AUTO) {
     c->path = cl_ok ? SGEP_PATH_CLUSTER : (tc_supported(*c, nullptr) ? SGEP_PATH_TC : SGEP_PATH_GENERIC);
   } else if (g.path == SGEP_PATH_CLUSTER) {
@@ -292,9 +296,22 @@ int sgep_destroy(sgep_t h) {
   return SGEP_OK;
 }
 
-static int step_checks(Ctx& c, const void* X, const void* Y, const int32_t* labels, int64_t b) {
+// Row scales: required for FP8 rows (one per row and view), absent otherwise.
+static int scale_checks(const Ctx& c, const float* sx, const float* sy) {
+  if (c.cfg.dtype == SGEP_FP8E4M3) {
+    if (!sx || (c.has_y && !sy)) return fail(SGEP_EINVAL, "FP8 rows need their row scales");
+    if (!c.has_y && sy) return fail(SGEP_EINVAL, "row_scale_y given for a one-view problem");
+  } else if (sx || sy) {
+    return fail(SGEP_EINVAL, "row scales are for FP8 rows only");
+  }
+  return SGEP_OK;
+}
+
+static int step_checks(Ctx& c, const void* X, const void* Y, const float* sx, const float* sy,
+                       const int32_t* labels, int64_t b) {
   if (!X) return fail(SGEP_EINVAL, "X is NULL");
   if (c.has_y && !Y) return fail(SGEP_EINVAL, "Y is NULL");
+  if (int rc = scale_checks(c, sx, sy)) return rc;
   if (c.cfg.kind == SGEP_LDA && !labels) return fail(SGEP_EINVAL, "LDA needs labels");
   const bool split = (c.cfg.kind == SGEP_CCA || c.cfg.kind == SGEP_LDA) && c.cfg.split_AB;
   if (b < (split ? 2 : 1)) return fail(SGEP_EINVAL, "b too small (split batches need b >= 2)");
@@ -302,7 +319,8 @@ static int step_checks(Ctx& c, const void* X, const void* Y, const int32_t* labe
   return SGEP_OK;
 }
 
-static int do_step(Ctx& c, const void* X, const void* Y, const int32_t* labels, int64_t b, cudaStream_t s) {
+static int do_step(Ctx& c, const void* X, const void* Y, const float* sx, const float* sy, const int32_t* labels,
+                   int64_t b, cudaStream_t s) {
   const int64_t t = c.t + 1;
   const float eta = (float)schedule_eta(c.cfg, t);
   const float gamma = c.cfg.gamma0;
@@ -315,7 +333,7 @@ static int do_step(Ctx& c, const void* X, const void* Y, const int32_t* labels, 
       if (!rc && c.tc_generic_step) c.tc_chain = 0;
       if (!rc) rc = c.tc_generic_step ? generic_update(c, eta, gamma, s) : tc_update(c, eta, gamma, s);
     } else {
-      rc = c.cfg.kind == SGEP_LDA ? lda_products(c, X, labels, b, s) : generic_products(c, X, Y, b, s);
+      rc = c.cfg.kind == SGEP_LDA ? lda_products(c, X, labels, b, s, sx) : generic_products(c, X, Y, b, s, sx, sy);
       if (!rc) rc = generic_update(c, eta, gamma, s);
     }
     if (!rc) c.debug_valid = c.cfg.debug;
@@ -324,25 +342,28 @@ static int do_step(Ctx& c, const void* X, const void* Y, const int32_t* labels, 
   return rc;
 }
 
-int sgep_step(sgep_t h, const void* X, const void* Y, const int32_t* labels, int64_t b, void* stream) {
+int sgep_step(sgep_t h, const void* X, const void* Y, const float* row_scale_x, const float* row_scale_y,
+              const int32_t* labels, int64_t b, void* stream) {
   if (!h) return fail(SGEP_EINVAL, "handle is NULL");
-  int rc = step_checks(*h, X, Y, labels, b);
+  int rc = step_checks(*h, X, Y, row_scale_x, row_scale_y, labels, b);
   if (rc) return rc;
-  return do_step(*h, X, Y, labels, b, (cudaStream_t)stream);
+  return do_step(*h, X, Y, row_scale_x, row_scale_y, labels, b, (cudaStream_t)stream);
 }
 
-int sgep_step_many(sgep_t h, const void* X, const void* Y, const int32_t* labels, int64_t b,
-                   int64_t nsteps, void* stream) {
+int sgep_step_many(sgep_t h, const void* X, const void* Y, const float* row_scale_x, const float* row_scale_y,
+                   const int32_t* labels, int64_t b, int64_t nsteps, void* stream) {
   if (!h) return fail(SGEP_EINVAL, "handle is NULL");
   if (nsteps < 0) return fail(SGEP_EINVAL, "nsteps < 0");
-  int rc = step_checks(*h, X, Y, labels, b);
+  int rc = step_checks(*h, X, Y, row_scale_x, row_scale_y, labels, b);
   if (rc) return rc;
-  const size_t esz = h->cfg.dtype == SGEP_BF16 ? 2 : 4;
+  const size_t esz = elem_size(*h);
   for (int64_t s = 0; s < nsteps; ++s) {
     const char* xs = (const char*)X + (size_t)s * b * h->d_x * esz;
     const char* ys = Y ? (const char*)Y + (size_t)s * b * h->d_y * esz : nullptr;
     const int32_t* ls = labels ? labels + s * b : nullptr;
-    rc = do_step(*h, xs, ys, ls, b, (cudaStream_t)stream);
+    const float* sxs = row_scale_x ? row_scale_x + s * b : nullptr;
+    const float* sys = row_scale_y ? row_scale_y + s * b : nullptr;
+    rc = do_step(*h, xs, ys, sxs, sys, ls, b, (cudaStream_t)stream);
     if (rc) return rc;
   }
   return SGEP_OK;
@@ -401,26 +422,29 @@ int sgep_set_V(sgep_t h, const float* V, int on_device, void* stream) {
   return sgep_set_VS(h, V, V, on_device, stream);
 }
 
-int sgep_get_eigenvalues(sgep_t h, const void* X, const void* Y, const int32_t* labels, int64_t n,
-                         double* out_k, void* stream) {
+int sgep_get_eigenvalues(sgep_t h, const void* X, const void* Y, const float* row_scale_x,
+                         const float* row_scale_y, const int32_t* labels, int64_t n, double* out_k,
+                         void* stream) {
   if (!h) return fail(SGEP_EINVAL, "handle is NULL");
   Ctx& c = *h;
   if (!X || (c.has_y && !Y) || !out_k) return fail(SGEP_EINVAL, "NULL argument");
   const bool lda = c.cfg.kind == SGEP_LDA;
   if (lda && !labels) return fail(SGEP_EINVAL, "LDA needs labels");
   if (n < 1) return fail(SGEP_EINVAL, "n must be >= 1");
+  if (int e = scale_checks(c, row_scale_x, row_scale_y)) return e;
   cudaStream_t s = (cudaStream_t)stream;
   int rc = complete(c, s);
   if (rc) return rc;
   const int k = c.k;
   SGEP_CUDA_TRY(cudaMemsetAsync(c.rq, 0, sizeof(double) * 2 * k, s));
-  const size_t esz = c.cfg.dtype == SGEP_BF16 ? 2 : 4;
+  const size_t esz = elem_size(c);
   for (int64_t r0 = 0; r0 < n; r0 += c.cfg.max_b) {
     const int64_t m = std::min<int64_t>(c.cfg.max_b, n - r0);
     const char* xs = (const char*)X + (size_t)r0 * c.d_x * esz;
     const char* ys = c.has_y ? (const char*)Y + (size_t)r0 * c.d_y * esz : nullptr;
     // LDA: rows centred by the running class means (the readout does not update them)
-    rc = lda ? generic_project(c, xs, ys, m, s, c.lda_mean, labels + r0) : generic_project(c, xs, ys, m, s);
+    rc = generic_project(c, xs, ys, m, s, lda ? c.lda_mean : nullptr, lda ? labels + r0 : nullptr,
+                         row_scale_x ? row_scale_x + r0 : nullptr, row_scale_y ? row_scale_y + r0 : nullptr);
     if (!rc) rc = generic_rayleigh_sums(c, m, s);
     if (rc) return rc;
   }
@@ -472,17 +496,19 @@ struct StateHeader {
   int64_t t;
 };
 
-int sgep_rayleigh_ritz(sgep_t h, const void* X, const void* Y, const int32_t* labels, int64_t n,
-                       double* lambda_out, void* stream) {
+int sgep_rayleigh_ritz(sgep_t h, const void* X, const void* Y, const float* row_scale_x,
+                       const float* row_scale_y, const int32_t* labels, int64_t n, double* lambda_out,
+                       void* stream) {
   if (!h) return fail(SGEP_EINVAL, "handle is NULL");
   Ctx& c = *h;
   if (!X || (c.has_y && !Y)) return fail(SGEP_EINVAL, "NULL argument");
   if (c.cfg.kind == SGEP_LDA && !labels) return fail(SGEP_EINVAL, "LDA needs labels");
   if (n < 1) return fail(SGEP_EINVAL, "n must be >= 1");
+  if (int e = scale_checks(c, row_scale_x, row_scale_y)) return e;
   cudaStream_t s = (cudaStream_t)stream;
   int rc = complete(c, s);
   if (rc) return rc;
-  rc = rr_correct(c, X, Y, labels, n, lambda_out, s);
+  rc = rr_correct(c, X, Y, row_scale_x, row_scale_y, labels, n, lambda_out, s);
   c.tc_chain = 0;  // V and [Bv] changed outside the step
   c.debug_valid = 0;
   if (rc) return rc;

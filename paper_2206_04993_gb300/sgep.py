@@ -20,7 +20,7 @@ HEADER = os.path.join(os.path.dirname(_PKG), "include", "sgep.h")
 SGEP_OK, SGEP_EINVAL, SGEP_ENOMEM, SGEP_ECUDA = 0, -1, -2, -3
 SGEP_ETIMEOUT, SGEP_ENONFINITE, SGEP_ELAUNCH, SGEP_ESTATE, SGEP_ENOTSUP = -4, -5, -6, -7, -8
 SGEP_PCA, SGEP_CCA, SGEP_PLS, SGEP_LDA = 0, 1, 2, 3
-SGEP_F32, SGEP_BF16 = 0, 1
+SGEP_F32, SGEP_BF16, SGEP_FP8E4M3 = 0, 1, 2
 SGEP_SCHED_CONST, SGEP_SCHED_HOLD_HARMONIC, SGEP_SCHED_WARMUP_HARMONIC = 0, 1, 2
 SGEP_PATH_AUTO, SGEP_PATH_GENERIC, SGEP_PATH_CLUSTER, SGEP_PATH_TC = 0, 1, 2, 3
 
@@ -50,15 +50,15 @@ _SIGS = {
     "sgep_config_default": (ctypes.c_int, [ctypes.POINTER(sgep_config)]),
     "sgep_init": (ctypes.c_int, [ctypes.POINTER(sgep_config), ctypes.POINTER(_P)]),
     "sgep_destroy": (ctypes.c_int, [_P]),
-    "sgep_step": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, _P]),
-    "sgep_step_many": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int64, _P]),
+    "sgep_step": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.c_int64, _P]),
+    "sgep_step_many": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.c_int64, ctypes.c_int64, _P]),
     "sgep_sync": (ctypes.c_int, [_P, _P]),
     "sgep_get_V": (ctypes.c_int, [_P, _P, ctypes.c_int, _P]),
     "sgep_get_S": (ctypes.c_int, [_P, _P, ctypes.c_int, _P]),
     "sgep_set_V": (ctypes.c_int, [_P, _P, ctypes.c_int, _P]),
     "sgep_set_VS": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
-    "sgep_get_eigenvalues": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, _P, _P]),
-    "sgep_rayleigh_ritz": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, _P, _P]),
+    "sgep_get_eigenvalues": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.c_int64, _P, _P]),
+    "sgep_rayleigh_ritz": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.c_int64, _P, _P]),
     "sgep_get_state": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_size_t)]),
     "sgep_set_state": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
     "sgep_step_count": (ctypes.c_int64, [_P]),
@@ -148,14 +148,16 @@ def sgep_destroy(h) -> None:
     check(lib().sgep_destroy(h), "sgep_destroy")
 
 
-def sgep_step(h, X, Y=None, labels=None, b=None, stream=None) -> None:
+def sgep_step(h, X, Y=None, labels=None, b=None, stream=None, sx=None, sy=None) -> None:
+    """sx, sy: per-row scales of FP8 rows (device float arrays), else None."""
     if b is None:
         b = X.shape[0]
-    check(lib().sgep_step(h, _ptr(X), _ptr(Y), _ptr(labels), int(b), _stream(stream)), "sgep_step")
+    check(lib().sgep_step(h, _ptr(X), _ptr(Y), _ptr(sx), _ptr(sy), _ptr(labels), int(b), _stream(stream)),
+          "sgep_step")
 
 
-def sgep_step_many(h, X, Y, b, nsteps, labels=None, stream=None) -> None:
-    check(lib().sgep_step_many(h, _ptr(X), _ptr(Y), _ptr(labels), int(b), int(nsteps),
+def sgep_step_many(h, X, Y, b, nsteps, labels=None, stream=None, sx=None, sy=None) -> None:
+    check(lib().sgep_step_many(h, _ptr(X), _ptr(Y), _ptr(sx), _ptr(sy), _ptr(labels), int(b), int(nsteps),
                                _stream(stream)), "sgep_step_many")
 
 
@@ -179,13 +181,13 @@ def sgep_set_VS(h, V, S, on_device: bool, stream=None) -> None:
     check(lib().sgep_set_VS(h, _ptr(V), _ptr(S), int(on_device), _stream(stream)), "sgep_set_VS")
 
 
-def sgep_rayleigh_ritz(h, X, Y, n, out=None, labels=None, stream=None) -> None:
-    check(lib().sgep_rayleigh_ritz(h, _ptr(X), _ptr(Y), _ptr(labels), int(n), _ptr(out),
+def sgep_rayleigh_ritz(h, X, Y, n, out=None, labels=None, stream=None, sx=None, sy=None) -> None:
+    check(lib().sgep_rayleigh_ritz(h, _ptr(X), _ptr(Y), _ptr(sx), _ptr(sy), _ptr(labels), int(n), _ptr(out),
                                    _stream(stream)), "sgep_rayleigh_ritz")
 
 
-def sgep_get_eigenvalues(h, X, Y, n, out, labels=None, stream=None) -> None:
-    check(lib().sgep_get_eigenvalues(h, _ptr(X), _ptr(Y), _ptr(labels), int(n), _ptr(out),
+def sgep_get_eigenvalues(h, X, Y, n, out, labels=None, stream=None, sx=None, sy=None) -> None:
+    check(lib().sgep_get_eigenvalues(h, _ptr(X), _ptr(Y), _ptr(sx), _ptr(sy), _ptr(labels), int(n), _ptr(out),
                                      _stream(stream)), "sgep_get_eigenvalues")
 
 

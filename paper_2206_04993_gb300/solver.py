@@ -37,12 +37,13 @@ class Solver:
         import torch
         return torch.cuda.current_stream().cuda_stream
 
-    def step(self, X, Y=None, b=None, labels=None):
-        """One step on device rows X (and Y); LDA also takes int32 device labels."""
-        _s.sgep_step(self.h, X, Y, labels, X.shape[0] if b is None else b, self._cur_stream())
+    def step(self, X, Y=None, b=None, labels=None, sx=None, sy=None):
+        """One step on device rows X (and Y); LDA also takes int32 device labels, FP8 rows
+        their per-row scales sx (and sy)."""
+        _s.sgep_step(self.h, X, Y, labels, X.shape[0] if b is None else b, self._cur_stream(), sx, sy)
 
-    def step_many(self, X, Y, b, nsteps, labels=None):
-        _s.sgep_step_many(self.h, X, Y, b, nsteps, labels, self._cur_stream())
+    def step_many(self, X, Y, b, nsteps, labels=None, sx=None, sy=None):
+        _s.sgep_step_many(self.h, X, Y, b, nsteps, labels, self._cur_stream(), sx, sy)
 
     def sync(self):
         _s.sgep_sync(self.h, self._cur_stream())
@@ -65,15 +66,15 @@ class Solver:
             S = np.ascontiguousarray(S, dtype=np.float32)
             _s.sgep_set_VS(self.h, V, S, False, self._cur_stream())
 
-    def eigenvalues(self, X, Y=None, labels=None) -> np.ndarray:
+    def eigenvalues(self, X, Y=None, labels=None, sx=None, sy=None) -> np.ndarray:
         out = np.empty(self.k, dtype=np.float64)
-        _s.sgep_get_eigenvalues(self.h, X, Y, X.shape[0], out, labels, self._cur_stream())
+        _s.sgep_get_eigenvalues(self.h, X, Y, X.shape[0], out, labels, self._cur_stream(), sx, sy)
         return out
 
-    def rayleigh_ritz(self, X, Y=None, labels=None) -> np.ndarray:
+    def rayleigh_ritz(self, X, Y=None, labels=None, sx=None, sy=None) -> np.ndarray:
         """Rotate the players into the Ritz vectors of their span on rows (X, Y); Ritz values."""
         out = np.empty(self.k, dtype=np.float64)
-        _s.sgep_rayleigh_ritz(self.h, X, Y, X.shape[0], out, labels, self._cur_stream())
+        _s.sgep_rayleigh_ritz(self.h, X, Y, X.shape[0], out, labels, self._cur_stream(), sx, sy)
         return out
 
     def products(self):

@@ -206,3 +206,35 @@ def config_c3(seed: int = 0):
     return {"name": "cca_d32768_k32_b4096", "model": model, "k": 32, "b": 4096,
             "n_samples": 10_000_000, "eta0": 0.3, "gamma0": 0.3, "rho": 1e-6,
             "schedule": 1, "t_c": 100, "T": 2442, "eta_T": 0.3 * 120.0 / 2462.0}
+
+
+# ---------------------------------------------------------------------------
+# FP8 e4m3 rows with one scale per row (input encoding of the precision form)
+
+def _e4m3_table():
+    """All finite non-negative e4m3 values, indexed by code 0..0x7E (sign bit clear)."""
+    vals = []
+    for code in range(0x7F):
+        e, m = code >> 3, code & 7
+        vals.append((m / 8.0) * 2.0 ** -6 if e == 0 else (1.0 + m / 8.0) * 2.0 ** (e - 7))
+    return np.array(vals)
+
+
+def quantize_e4m3_rows(X):
+    """Per-row scale s_r = max|x_r| / 448 (1 for an all-zero row) and the e4m3 codes of
+    x_r / s_r rounded to the nearest value (ties to the even code). Returns (codes uint8,
+    scales float32); the represented rows are s_r * e4m3(codes)."""
+    X = np.asarray(X, dtype=np.float64)
+    scales = np.max(np.abs(X), axis=1) / 448.0
+    scales[scales == 0] = 1.0
+    scales = scales.astype(np.float32)
+    Z = X / scales.astype(np.float64)[:, None]
+    table = _e4m3_table()
+    a = np.minimum(np.abs(Z), 448.0)
+    hi = np.clip(np.searchsorted(table, a, side="left"), 0, len(table) - 1)
+    lo = np.clip(hi - 1, 0, len(table) - 1)
+    dlo, dhi = a - table[lo], table[hi] - a
+    pick_hi = (dhi < dlo) | ((dhi == dlo) & (hi % 2 == 0))
+    code = np.where(pick_hi, hi, lo).astype(np.uint8)
+    code = np.where(Z < 0, code | 0x80, code).astype(np.uint8)
+    return code, scales

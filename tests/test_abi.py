@@ -44,7 +44,7 @@ def test_strerror_and_null_arguments():
     assert L.sgep_config_default(None) == S.SGEP_EINVAL
     assert L.sgep_init(None, None) == S.SGEP_EINVAL
     assert L.sgep_destroy(None) == S.SGEP_OK
-    assert L.sgep_step(None, None, None, None, 4, None) == S.SGEP_EINVAL
+    assert L.sgep_step(None, None, None, None, None, None, 4, None) == S.SGEP_EINVAL
     assert L.sgep_step_count(None) == -1
 
 
