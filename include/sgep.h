@@ -197,6 +197,64 @@ int sgep_rayleigh_ritz(sgep_t h, const void* X, const void* Y, const float* row_
                        const float* row_scale_y, const int32_t* labels, int64_t n,
                        double* lambda_out, void* stream);
 
+/* ---- batching form ------------------------------------------------------
+ * Many independent problems (uneven kind, d_x, d_y, k, element type) advanced
+ * together: one call runs one step of every instance. The paper has no batched
+ * form; this groups independent Alg. 2 iterations. Every handle must have been
+ * created with path = SGEP_PATH_GENERIC (the batch runs the generic tiles); it
+ * stays owned by the caller, must outlive the batch, and must not be stepped on
+ * its own while the batch may have work in flight (sgep_batch_sync first).
+ * Per-instance results and errors are read through the handles as usual. */
+typedef struct sgep_batch_ctx* sgep_batch_t;
+
+/* Group n handles (host array) into a batch. Synchronises every handle first.
+ * Errors: SGEP_EINVAL (NULL, duplicate, non-generic handle), SGEP_ENOMEM. */
+int sgep_batch_create(const sgep_t* handles, int n, sgep_batch_t* out);
+
+/* Free the batch (not the handles). NULL is accepted. */
+int sgep_batch_destroy(sgep_batch_t b);
+
+/* One step of every instance. X, Y, row_scale_x, row_scale_y, labels: host
+ * arrays of n device pointers with the meaning of sgep_step's arguments for
+ * instance i (Y, the scale arrays and labels may be NULL when no instance needs
+ * them); rows: host array of n row counts. Asynchronous on `stream`: a table of
+ * per-instance descriptors is copied from pinned host memory, then either one
+ * persistent cooperative launch runs the eight phases of the step (zeroing, LDA
+ * class statistics, projection, back-projection, LDA between-class products, k x k
+ * terms, update, retraction) separated by bounded grid barriers (mode 0), or one
+ * launch per phase (mode 1); with use_graph the copy and the launch(es) are
+ * captured in a CUDA graph once per launch shape and replayed. */
+int sgep_batch_step(sgep_batch_t b, const void* const* X, const void* const* Y,
+                    const float* const* row_scale_x, const float* const* row_scale_y,
+                    const int32_t* const* labels, const int64_t* rows, void* stream);
+
+/* Wait for the batch's work on `stream`; report a barrier timeout of the batched
+ * launch (SGEP_ETIMEOUT) or the first instance error (as sgep_sync). */
+int sgep_batch_sync(sgep_batch_t b, void* stream);
+
+/* Set the launch configuration; a negative or zero value keeps the current one.
+ * mode: 0 persistent, 1 one launch per phase; blocks_per_sm: persistent grid
+ * (capped by occupancy); chunk_cap: projection tile width in columns (64..4096);
+ * rows_cap: back-projection tile height in rows (>= 32); use_graph: 0 or 1. */
+int sgep_batch_configure(sgep_batch_t b, int mode, int blocks_per_sm, int chunk_cap,
+                         int rows_cap, int use_graph);
+
+/* The current configuration: out5 = {mode, blocks_per_sm, chunk_cap, rows_cap, use_graph}. */
+int sgep_batch_get_config(sgep_batch_t b, int* out5);
+
+/* Autotuner: time every candidate configuration (mode x chunk_cap in {256, 512,
+ * 1024} x rows_cap in {64, 128, 256} x blocks_per_sm in {1, 2, 4} for mode 0) for
+ * `reps` steps on these rows, keep the fastest, and cache it for this batch
+ * signature (kind, dtype, d_x, d_y, k, rows of every instance) for the life of the
+ * process. The instances' state (V, [Bv], step count, LDA statistics) is saved
+ * before and restored after. out5 receives the chosen configuration. Synchronous. */
+int sgep_batch_autotune(sgep_batch_t b, const void* const* X, const void* const* Y,
+                        const float* const* row_scale_x, const float* const* row_scale_y,
+                        const int32_t* const* labels, const int64_t* rows, int reps, int* out5);
+
+/* Kernel launches issued by the batch so far (a graph replay counts its kernels). */
+int64_t sgep_batch_launch_count(sgep_batch_t b);
+
 /* Serialise the state (versioned header, V, [Bv], step counter; LDA also its
  * class sums, C x d doubles, and counts, C doubles) into `buf`.
  * If buf is NULL, only writes the required size to *nbytes. Synchronous. */

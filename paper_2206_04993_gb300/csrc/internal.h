@@ -131,6 +131,20 @@ int generic_project(Ctx& c, const void* X, const void* Y, int64_t n, cudaStream_
 int generic_lda_within(Ctx& c, const void* X, const int32_t* labels, int64_t n, cudaStream_t s,
                        const float* sx = nullptr);
 
+// Batching form (kernels_batch.cu).
+struct BatchCtx;
+int batch_create(Ctx** hs, int n, BatchCtx** out);
+void batch_free(BatchCtx* B);
+int batch_step(BatchCtx& B, const void* const* X, const void* const* Y, const float* const* sx,
+               const float* const* sy, const int32_t* const* labels, const int64_t* b, cudaStream_t s);
+int batch_sync(BatchCtx& B, cudaStream_t s);
+void batch_set(BatchCtx& B, int mode, int blocks_per_sm, int chunk_cap, int rows_cap, int use_graph);
+void batch_get(const BatchCtx& B, int* out5);
+int64_t batch_launches(const BatchCtx& B);
+int batch_autotune(BatchCtx& B, const void* const* X, const void* const* Y, const float* const* sx,
+                   const float* const* sy, const int32_t* const* labels, const int64_t* b, int reps, int* best5);
+double schedule_eta(const sgep_config& cfg, int64_t t);
+
 // Rayleigh-Ritz correction of V and [Bv] on n evaluation rows (kernels_rr.cu).
 int rr_correct(Ctx& c, const void* X, const void* Y, const float* sx, const float* sy, const int32_t* labels,
                int64_t n, double* lam_host, cudaStream_t s);

@@ -59,6 +59,15 @@ _SIGS = {
     "sgep_set_VS": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
     "sgep_get_eigenvalues": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.c_int64, _P, _P]),
     "sgep_rayleigh_ritz": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.c_int64, _P, _P]),
+    "sgep_batch_create": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P)]),
+    "sgep_batch_destroy": (ctypes.c_int, [_P]),
+    "sgep_batch_step": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
+    "sgep_batch_sync": (ctypes.c_int, [_P, _P]),
+    "sgep_batch_configure": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_int]),
+    "sgep_batch_get_config": (ctypes.c_int, [_P, _P]),
+    "sgep_batch_autotune": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, ctypes.c_int, _P]),
+    "sgep_batch_launch_count": (ctypes.c_int64, [_P]),
     "sgep_get_state": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_size_t)]),
     "sgep_set_state": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
     "sgep_step_count": (ctypes.c_int64, [_P]),
@@ -245,3 +254,61 @@ def sgep_strerror(status: int) -> str:
 
 def sgep_last_error() -> str:
     return lib().sgep_last_error().decode()
+
+
+# ---- batching form -----------------------------------------------------------
+
+def _ptr_array(items):
+    """Host array of device pointers (None entries become NULL); None if all are None."""
+    if items is None:
+        return None
+    ptrs = [_ptr(x) for x in items]
+    if all(p is None for p in ptrs):
+        return None
+    return (ctypes.c_void_p * len(ptrs))(*ptrs)
+
+
+def sgep_batch_create(handles):
+    arr = (ctypes.c_void_p * len(handles))(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    out = ctypes.c_void_p()
+    check(lib().sgep_batch_create(arr, len(handles), ctypes.byref(out)), "sgep_batch_create")
+    return out
+
+
+def sgep_batch_destroy(b) -> None:
+    check(lib().sgep_batch_destroy(b), "sgep_batch_destroy")
+
+
+def _rows(rows):
+    return (ctypes.c_int64 * len(rows))(*[int(r) for r in rows])
+
+
+def sgep_batch_step(b, X, Y=None, rows=None, labels=None, sx=None, sy=None, stream=None) -> None:
+    check(lib().sgep_batch_step(b, _ptr_array(X), _ptr_array(Y), _ptr_array(sx), _ptr_array(sy),
+                                _ptr_array(labels), _rows(rows), _stream(stream)), "sgep_batch_step")
+
+
+def sgep_batch_sync(b, stream=None) -> None:
+    check(lib().sgep_batch_sync(b, _stream(stream)), "sgep_batch_sync")
+
+
+def sgep_batch_configure(b, mode=-1, blocks_per_sm=0, chunk_cap=0, rows_cap=0, use_graph=-1) -> None:
+    check(lib().sgep_batch_configure(b, int(mode), int(blocks_per_sm), int(chunk_cap), int(rows_cap),
+                                     int(use_graph)), "sgep_batch_configure")
+
+
+def sgep_batch_get_config(b):
+    out = (ctypes.c_int * 5)()
+    check(lib().sgep_batch_get_config(b, out), "sgep_batch_get_config")
+    return list(out)
+
+
+def sgep_batch_autotune(b, X, Y=None, rows=None, labels=None, sx=None, sy=None, reps=3):
+    out = (ctypes.c_int * 5)()
+    check(lib().sgep_batch_autotune(b, _ptr_array(X), _ptr_array(Y), _ptr_array(sx), _ptr_array(sy),
+                                    _ptr_array(labels), _rows(rows), int(reps), out), "sgep_batch_autotune")
+    return list(out)
+
+
+def sgep_batch_launch_count(b) -> int:
+    return int(lib().sgep_batch_launch_count(b))

@@ -107,3 +107,53 @@ class Solver:
 
     def load_state(self, blob: bytes):
         _s.sgep_set_state(self.h, blob)
+
+
+class Batch:
+    """Many Solvers (generic path) advanced by one batched launch per step."""
+
+    def __init__(self, solvers):
+        self.solvers = list(solvers)
+        self.b = _s.sgep_batch_create([x.h for x in self.solvers])
+
+    def close(self):
+        if getattr(self, "b", None) is not None:
+            _s.sgep_batch_destroy(self.b)
+            self.b = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _stream():
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+
+    def step(self, Xs, Ys=None, rows=None, labels=None, sx=None, sy=None):
+        rows = [x.shape[0] for x in Xs] if rows is None else rows
+        _s.sgep_batch_step(self.b, Xs, Ys, rows, labels, sx, sy, self._stream())
+
+    def sync(self):
+        _s.sgep_batch_sync(self.b, self._stream())
+
+    def configure(self, mode=-1, blocks_per_sm=0, chunk_cap=0, rows_cap=0, use_graph=-1):
+        _s.sgep_batch_configure(self.b, mode, blocks_per_sm, chunk_cap, rows_cap, use_graph)
+
+    def config(self):
+        return _s.sgep_batch_get_config(self.b)
+
+    def autotune(self, Xs, Ys=None, rows=None, labels=None, sx=None, sy=None, reps=3):
+        rows = [x.shape[0] for x in Xs] if rows is None else rows
+        return _s.sgep_batch_autotune(self.b, Xs, Ys, rows, labels, sx, sy, reps)
+
+    def launches(self) -> int:
+        return _s.sgep_batch_launch_count(self.b)
