@@ -57,7 +57,7 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--pool-rows", type=int, default=0, help="override the resident row pool")
     p.add_argument("--no-tte", action="store_true", help="skip the time-to-1e-3 measurements")
-    p.add_argument("--no-forms", action="store_true", help="skip the BF16 tensor-core workload")
+    p.add_argument("--no-forms", action="store_true", help="skip the BF16 tensor-core and batching workloads")
     p.add_argument("--tte-max-steps", type=int, default=80_000)
     return p.parse_args()
 
@@ -335,6 +335,105 @@ def measure_throughput(workload, steps, warmup, dev, rank=0, path=0):
     return out
 
 
+def measure_batch(dtype, steps, warmup, dev, seed=0, n_instances=64):
+    """Batching workload: 64 uneven instances (half CCA, half LDA), b = 512 each, advanced by
+    one batched launch per step (configuration from the autotuner), against the same
+    instances stepped one handle at a time. Rows: two resident minibatches per instance."""
+    import torch
+    from paper_2206_04993_gb300 import Batch, Solver, sgep
+    insts = synth.config_c4(seed=seed, n_instances=n_instances)
+    tdt = torch.bfloat16 if dtype == "bf16" else torch.float32
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed + 17)
+    rows = []  # per instance: list of (X, Y, labels) for two minibatches
+    for it in insts:
+        b = it["b"]
+        m = it["model"]
+        mbs = []
+        for _ in range(2):
+            if it["kind"] == "cca":
+                Wx = torch.tensor(m.Qx * m.s, dtype=torch.float32, device=dev)
+                Wy = torch.tensor(m.Qy * m.s, dtype=torch.float32, device=dev)
+                z = torch.randn(b, m.s.size, device=dev, generator=g)
+                X = z @ Wx.T + m.sigma * torch.randn(b, it["d_x"], device=dev, generator=g)
+                Y = z @ Wy.T + m.sigma * torch.randn(b, it["d_y"], device=dev, generator=g)
+                mbs.append((X.to(tdt).contiguous(), Y.to(tdt).contiguous(), None))
+            else:
+                C = it["n_classes"]
+                lab = torch.randint(0, C, (b,), device=dev, generator=g, dtype=torch.int32)
+                means = torch.tensor(m["means"], dtype=torch.float32, device=dev)
+                sc = torch.tensor(m["scales"], dtype=torch.float32, device=dev)
+                X = means[lab.long()] + torch.randn(b, it["d_x"], device=dev, generator=g) * sc
+                mbs.append((X.to(tdt).contiguous(), None, lab))
+        rows.append(mbs)
+    dt = sgep.SGEP_BF16 if dtype == "bf16" else sgep.SGEP_F32
+
+    def make():
+        out = []
+        for i, it in enumerate(insts):
+            out.append(Solver(kind=sgep.SGEP_CCA if it["kind"] == "cca" else sgep.SGEP_LDA, d_x=it["d_x"],
+                              d_y=it["d_y"], k=it["k"], n_classes=it.get("n_classes", 0), max_b=it["b"], dtype=dt,
+                              path=sgep.SGEP_PATH_GENERIC, eta0=0.05, gamma0=0.3, seed=i))
+        return out
+
+    def args_of(j):
+        return ([r[j][0] for r in rows], [r[j][1] for r in rows], [it["b"] for it in insts],
+                [r[j][2] for r in rows])
+
+    samples = sum(it["b"] for it in insts)
+    alg = sum(it["b"] * (it["d_x"] + it["d_y"]) * (2 if dtype == "bf16" else 4) for it in insts)
+    solvers = make()
+    out = {"unit": "samples/s", "dtype": dtype, "instances": len(insts),
+           "config": {"kinds": "even CCA (d 64..4096, d_x = d_y), odd LDA (10 classes)", "k": "4..32 (LDA <= 9)",
+                      "b": 512, "d_total": int(sum(it["d_x"] + it["d_y"] for it in insts))}}
+    with Batch(solvers) as bt:
+        X0, Y0, R0, L0 = args_of(0)
+        bt.configure(use_graph=1)
+        out["autotuned"] = dict(zip(["mode", "blocks_per_sm", "chunk_cap", "rows_cap", "use_graph"],
+                                    bt.autotune(X0, Y0, R0, labels=L0, reps=3)))
+        for i in range(warmup):
+            Xs, Ys, Rs, Ls = args_of(i % 2)
+            bt.step(Xs, Ys, Rs, labels=Ls)
+        bt.sync()
+        torch.cuda.synchronize()
+        l0 = bt.launches()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for i in range(steps):
+            Xs, Ys, Rs, Ls = args_of(i % 2)
+            bt.step(Xs, Ys, Rs, labels=Ls)
+        e1.record()
+        torch.cuda.synchronize()
+        bt.sync()
+        ms = e0.elapsed_time(e1) / steps
+        out.update({"value": samples / (ms / 1e3), "ms_per_step": ms,
+                    "gpu_launches_per_step": (bt.launches() - l0) / steps,
+                    "algorithmic_GBps": alg / (ms / 1e3) / 1e9})
+    # the same instances stepped one handle at a time (generic path, one stream)
+    for i in range(warmup):
+        Xs, Ys, Rs, Ls = args_of(i % 2)
+        for s, x, y, r, lb in zip(solvers, Xs, Ys, Rs, Ls):
+            s.step(x, y, r, labels=lb)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    seq_steps = max(3, steps // 4)
+    e0.record()
+    for i in range(seq_steps):
+        Xs, Ys, Rs, Ls = args_of(i % 2)
+        for s, x, y, r, lb in zip(solvers, Xs, Ys, Rs, Ls):
+            s.step(x, y, r, labels=lb)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_seq = e0.elapsed_time(e1) / seq_steps
+    out["one_by_one"] = {"value": samples / (ms_seq / 1e3), "ms_per_step": ms_seq, "steps": seq_steps}
+    out["speedup_vs_one_by_one"] = ms_seq / ms
+    for s in solvers:
+        s.close()
+    del rows
+    torch.cuda.empty_cache()
+    return out
+
+
 def cpu_cores():
     for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         if os.environ.get(var):
@@ -500,7 +599,9 @@ def run_native(args):
     if rank == 0 and not args.no_forms and args.workload == DEFAULT_WORKLOAD:
         del X, Y
         torch.cuda.empty_cache()
-        forms = {"cca_d32768_k32_b4096_bf16": measure_throughput("cca_d32768_k32_b4096_bf16", 60, 5, dev, rank)}
+        forms = {"cca_d32768_k32_b4096_bf16": measure_throughput("cca_d32768_k32_b4096_bf16", 60, 5, dev, rank),
+                 "batch64_cca_lda_b512_f32": measure_batch("f32", 40, 3, dev, seed=rank),
+                 "batch64_cca_lda_b512_bf16": measure_batch("bf16", 40, 3, dev, seed=rank)}
 
     if rank == 0:
         line = {

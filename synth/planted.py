@@ -125,14 +125,15 @@ def planted_pca(d: int, spectrum, sigma: float = 0.1, seed: int = 0):
     return {"Q": Q, "spectrum": spectrum, "sigma": float(sigma), "seed": seed}
 
 
-def planted_lda(d: int, n_classes: int = 10, sigma_b: float = 1.0, seed: int = 0):
-    """C Gaussian classes, equal priors, means N(0, sigma_b^2 I), shared covariance L L^T."""
+def planted_lda(d: int, n_classes: int = 10, sigma_b: float = 1.0, seed: int = 0, rotate: bool = True):
+    """C Gaussian classes, equal priors, means N(0, sigma_b^2 I), shared covariance L L^T
+    (L = rotation x diag(1..0.5); rotate=False keeps L diagonal, for large d)."""
     rng = _rng(seed, _STREAM_MODEL)
     means = sigma_b * rng.standard_normal((n_classes, d))
     means -= means.mean(axis=0, keepdims=True)   # zero overall mean
     scales = np.linspace(1.0, 0.5, d)
-    L = _orthonormal(rng, d, d) * scales[None, :]
-    return {"means": means, "L": L, "seed": seed}
+    L = _orthonormal(rng, d, d) * scales[None, :] if rotate else np.diag(scales)
+    return {"means": means, "L": L, "scales": scales, "seed": seed}
 
 
 def draw_rows(model, n: int, batch: int, dtype=np.float64):
@@ -238,3 +239,23 @@ def quantize_e4m3_rows(X):
     code = np.where(pick_hi, hi, lo).astype(np.uint8)
     code = np.where(Z < 0, code | 0x80, code).astype(np.uint8)
     return code, scales
+
+
+def config_c4(seed: int = 0, n_instances: int = 64):
+    """Batching workload: independent instances, even ones CCA (d uniform in 64..4096,
+    d_x = d_y = d / 2, planted with 16 latent directions, correlations 0.9..0.3) and odd
+    ones LDA (10 Gaussian classes, d uniform in 64..4096, diagonal within-class covariance);
+    k uniform in 4..32, clamped to 9 for LDA (rank of the between-class scatter); b = 512."""
+    rng = _rng(seed, _STREAM_MODEL + 7)
+    out = []
+    for i in range(n_instances):
+        d = int(rng.integers(64, 4097))
+        k = int(rng.integers(4, 33))
+        if i % 2 == 0:
+            dx = max(16, d // 2)
+            out.append({"kind": "cca", "d_x": dx, "d_y": dx, "k": min(k, dx), "b": 512,
+                        "model": planted_cca(dx, dx, np.linspace(0.9, 0.3, 16), sigma=0.5, seed=seed * 1000 + i)})
+        else:
+            out.append({"kind": "lda", "d_x": d, "d_y": 0, "k": min(k, 9), "b": 512, "n_classes": 10,
+                        "model": planted_lda(d, n_classes=10, seed=seed * 1000 + i, rotate=False)})
+    return out
