@@ -255,6 +255,52 @@ int sgep_batch_autotune(sgep_batch_t b, const void* const* X, const void* const*
 /* Kernel launches issued by the batch so far (a graph replay counts its kernels). */
 int64_t sgep_batch_launch_count(sgep_batch_t b);
 
+/* ---- learned warm start --------------------------------------------------
+ * Not in the paper, which starts from random players (Alg. 2): a random sketch of
+ * the first minibatch is mapped row by row to an initial V by a small network
+ * trained on the plain solver's solutions; the plain iteration then runs from it
+ * (sgep_set_V), and stays the fallback. */
+typedef struct sgep_mlp_ctx* sgep_mlp_t;
+
+/* Sketch S = Z^T (Z Omega) / n of n rows Z = [X Y] (device, dtype SGEP_F32 or
+ * SGEP_BF16; Y NULL when d_y = 0), Omega device d x m row-major float (d = d_x + d_y,
+ * m <= 32); every column of S is then divided by its root mean square over the d
+ * rows. out: device d x m row-major float. Synchronous. */
+int sgep_sketch(const void* X, const void* Y, int dtype, int64_t n, int64_t d_x, int64_t d_y,
+                const float* omega, int m, float* out, void* stream);
+
+/* Per-row network in_dim (m <= 32) -> 64 -> 64 -> out_dim (k <= 32) with ReLUs;
+ * weights used in BF16 (FP32 master copies), FP32 accumulation; seeded He
+ * initialisation. Errors: SGEP_EINVAL, SGEP_ENOMEM. */
+int sgep_mlp_create(int in_dim, int out_dim, uint64_t seed, sgep_mlp_t* out);
+int sgep_mlp_destroy(sgep_mlp_t m);
+
+/* Number of parameters P; their layout (row-major): W1 (64 x m) | b1 (64) |
+ * W2 (64 x 64) | b2 (64) | W3 (k x 64) | b3 (k). */
+int sgep_mlp_param_count(sgep_mlp_t m);
+
+/* Copy the parameters as used (weights rounded to BF16) to host `host` (P floats). */
+int sgep_mlp_get_params(sgep_mlp_t m, float* host);
+
+/* Set the master parameters from host (P floats; weights are used rounded to BF16)
+ * and reset the optimiser state. Synchronous. */
+int sgep_mlp_set_params(sgep_mlp_t m, const float* host);
+
+/* out (device rows x k) = network applied to every row of S (device rows x m). */
+int sgep_mlp_forward(sgep_mlp_t m, const float* S, int64_t rows, float* out, void* stream);
+
+/* Loss and gradients on a batch of instances: rows seg[i] .. seg[i+1] - 1 of S
+ * (device, rows x m) and of the targets V (device, rows x k) belong to instance i
+ * (seg: host, n_inst + 1 increasing offsets, seg[0] = 0). Loss = mean over the
+ * instances of sum_i (1 - (o_i . v_i)^2 / (|o_i|^2 |v_i|^2)) (sign- and scale-
+ * invariant per column). The gradients stay on the device for sgep_mlp_adam_step;
+ * grad_host (P floats, may be NULL) receives a copy. Synchronous. */
+int sgep_mlp_loss_grad(sgep_mlp_t m, const float* S, const float* V, const int64_t* seg, int n_inst,
+                       double* loss, float* grad_host, void* stream);
+
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) with the last gradients. */
+int sgep_mlp_adam_step(sgep_mlp_t m, float lr, void* stream);
+
 /* Serialise the state (versioned header, V, [Bv], step counter; LDA also its
  * class sums, C x d doubles, and counts, C doubles) into `buf`.
  * If buf is NULL, only writes the required size to *nbytes. Synchronous. */

@@ -6,4 +6,4 @@ include/sgep.h; `paper_2206_04993_gb300.sgep` binds it with ctypes and
 `paper_2206_04993_gb300.solver.Solver` is a small convenience wrapper.
 """
 from . import sgep  # noqa: F401
-from .solver import Batch, Solver  # noqa: F401
+from .solver import Batch, Solver, WarmStart  # noqa: F401

@@ -131,6 +131,20 @@ int generic_project(Ctx& c, const void* X, const void* Y, int64_t n, cudaStream_
 int generic_lda_within(Ctx& c, const void* X, const int32_t* labels, int64_t n, cudaStream_t s,
                        const float* sx = nullptr);
 
+// Learned warm start (kernels_warm.cu).
+struct MlpCtx;
+int mlp_create(int m, int k, uint64_t seed, MlpCtx** out);
+void mlp_free(MlpCtx* M);
+int mlp_set(MlpCtx& M, const float* host);
+int mlp_get(const MlpCtx& M, float* host);
+int mlp_param_count(const MlpCtx& M);
+int mlp_forward(MlpCtx& M, const float* S, int64_t rows, float* O, cudaStream_t s);
+int mlp_loss_grad(MlpCtx& M, const float* S, const float* V, const int64_t* seg_host, int n_inst, double* loss_out,
+                  float* grad_host, cudaStream_t s);
+int mlp_adam(MlpCtx& M, float lr, cudaStream_t s);
+int sketch_rows(const void* X, const void* Y, int dtype, int64_t n, int64_t dx, int64_t dy, const float* om, int m,
+                float* out, int num_sms, int* dflag, cudaStream_t s);
+
 // Batching form (kernels_batch.cu).
 struct BatchCtx;
 int batch_create(Ctx** hs, int n, BatchCtx** out);

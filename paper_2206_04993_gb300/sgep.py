@@ -68,6 +68,16 @@ _SIGS = {
     "sgep_batch_get_config": (ctypes.c_int, [_P, _P]),
     "sgep_batch_autotune": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, ctypes.c_int, _P]),
     "sgep_batch_launch_count": (ctypes.c_int64, [_P]),
+    "sgep_sketch": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _P,
+                                   ctypes.c_int, _P, _P]),
+    "sgep_mlp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_uint64, ctypes.POINTER(_P)]),
+    "sgep_mlp_destroy": (ctypes.c_int, [_P]),
+    "sgep_mlp_param_count": (ctypes.c_int, [_P]),
+    "sgep_mlp_get_params": (ctypes.c_int, [_P, _P]),
+    "sgep_mlp_set_params": (ctypes.c_int, [_P, _P]),
+    "sgep_mlp_forward": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P]),
+    "sgep_mlp_loss_grad": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, _P, _P, _P]),
+    "sgep_mlp_adam_step": (ctypes.c_int, [_P, ctypes.c_float, _P]),
     "sgep_get_state": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_size_t)]),
     "sgep_set_state": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
     "sgep_step_count": (ctypes.c_int64, [_P]),
@@ -312,3 +322,48 @@ def sgep_batch_autotune(b, X, Y=None, rows=None, labels=None, sx=None, sy=None, 
 
 def sgep_batch_launch_count(b) -> int:
     return int(lib().sgep_batch_launch_count(b))
+
+
+# ---- learned warm start ------------------------------------------------------------
+
+def sgep_sketch(X, Y, dtype, n, d_x, d_y, omega, m, out, stream=None) -> None:
+    check(lib().sgep_sketch(_ptr(X), _ptr(Y), int(dtype), int(n), int(d_x), int(d_y), _ptr(omega), int(m),
+                            _ptr(out), _stream(stream)), "sgep_sketch")
+
+
+def sgep_mlp_create(in_dim, out_dim, seed=0):
+    out = ctypes.c_void_p()
+    check(lib().sgep_mlp_create(int(in_dim), int(out_dim), int(seed), ctypes.byref(out)), "sgep_mlp_create")
+    return out
+
+
+def sgep_mlp_destroy(m) -> None:
+    check(lib().sgep_mlp_destroy(m), "sgep_mlp_destroy")
+
+
+def sgep_mlp_param_count(m) -> int:
+    return int(lib().sgep_mlp_param_count(m))
+
+
+def sgep_mlp_get_params(m, out) -> None:
+    check(lib().sgep_mlp_get_params(m, _ptr(out)), "sgep_mlp_get_params")
+
+
+def sgep_mlp_set_params(m, params) -> None:
+    check(lib().sgep_mlp_set_params(m, _ptr(params)), "sgep_mlp_set_params")
+
+
+def sgep_mlp_forward(m, S, rows, out, stream=None) -> None:
+    check(lib().sgep_mlp_forward(m, _ptr(S), int(rows), _ptr(out), _stream(stream)), "sgep_mlp_forward")
+
+
+def sgep_mlp_loss_grad(m, S, V, seg, n_inst, grad_out=None, stream=None) -> float:
+    loss = ctypes.c_double(0.0)
+    seg_arr = (ctypes.c_int64 * len(seg))(*[int(x) for x in seg])
+    check(lib().sgep_mlp_loss_grad(m, _ptr(S), _ptr(V), seg_arr, int(n_inst), ctypes.byref(loss), _ptr(grad_out),
+                                   _stream(stream)), "sgep_mlp_loss_grad")
+    return loss.value
+
+
+def sgep_mlp_adam_step(m, lr, stream=None) -> None:
+    check(lib().sgep_mlp_adam_step(m, ctypes.c_float(lr), _stream(stream)), "sgep_mlp_adam_step")

@@ -157,3 +157,61 @@ class Batch:
 
     def launches(self) -> int:
         return _s.sgep_batch_launch_count(self.b)
+
+
+class WarmStart:
+    """Sketch-to-players network (hand-written CUDA kernels): rows of the sketch
+    Z^T (Z Omega) / n of a first minibatch map to rows of an initial V."""
+
+    def __init__(self, m=16, k=16, seed=0):
+        self.m, self.k = m, k
+        self.h = _s.sgep_mlp_create(m, k, seed)
+        self.P = _s.sgep_mlp_param_count(self.h)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            _s.sgep_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _stream():
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+
+    def params(self) -> np.ndarray:
+        out = np.empty(self.P, dtype=np.float32)
+        _s.sgep_mlp_get_params(self.h, out)
+        return out
+
+    def set_params(self, p):
+        _s.sgep_mlp_set_params(self.h, np.ascontiguousarray(p, dtype=np.float32))
+
+    @staticmethod
+    def sketch(X, Y, omega, dtype=0):
+        """Device sketch (d x m float32) of device rows X (and Y) with device Omega (d x m)."""
+        import torch
+        d = X.shape[1] + (0 if Y is None else Y.shape[1])
+        out = torch.empty((d, omega.shape[1]), dtype=torch.float32, device=X.device)
+        _s.sgep_sketch(X, Y, dtype, X.shape[0], X.shape[1], 0 if Y is None else Y.shape[1], omega, omega.shape[1],
+                       out, WarmStart._stream())
+        return out
+
+    def forward(self, S):
+        import torch
+        out = torch.empty((S.shape[0], self.k), dtype=torch.float32, device=S.device)
+        _s.sgep_mlp_forward(self.h, S, S.shape[0], out, self._stream())
+        return out
+
+    def loss_grad(self, S, V, seg, grads=False):
+        g = np.empty(self.P, dtype=np.float32) if grads else None
+        loss = _s.sgep_mlp_loss_grad(self.h, S, V, seg, len(seg) - 1, g, self._stream())
+        return (loss, g) if grads else loss
+
+    def adam_step(self, lr):
+        _s.sgep_mlp_adam_step(self.h, lr, self._stream())

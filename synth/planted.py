@@ -259,3 +259,31 @@ def config_c4(seed: int = 0, n_instances: int = 64):
             out.append({"kind": "lda", "d_x": d, "d_y": 0, "k": min(k, 9), "b": 512, "n_classes": 10,
                         "model": planted_lda(d, n_classes=10, seed=seed * 1000 + i, rotate=False)})
     return out
+
+
+def config_c5(seed: int = 0, d_x: int = 1024, k: int = 16, latent: int = 16, n_theta: int = 8,
+              spread: float = 0.3):
+    """Warm-start family: CCA instances whose mixing matrices are a fixed smooth function
+    of theta ~ U[-1, 1]^n_theta: Q_view(theta) = orthonormalise(W0 + spread * sum_m theta_m W_m)
+    (d_x = d_y, `latent` planted directions, correlations 0.9..0.3, noise 0.5). Returns a
+    function theta -> PlantedCCA, a sampler of theta, and the sketch matrix Omega (d x 16)."""
+    rng = _rng(seed, _STREAM_MODEL + 11)
+    d = 2 * d_x
+    W0 = [rng.standard_normal((d_x, latent)) for _ in range(2)]
+    Wm = [[rng.standard_normal((d_x, latent)) for _ in range(n_theta)] for _ in range(2)]
+    rhos = np.linspace(0.9, 0.3, latent)
+    s = np.sqrt(0.25 * rhos / (1.0 - rhos))
+    omega = rng.standard_normal((d, 16))
+
+    def model(theta):
+        Q = []
+        for v in range(2):
+            M = W0[v] + spread * sum(theta[m] * Wm[v][m] for m in range(n_theta))
+            q, r = np.linalg.qr(M)
+            Q.append(q * np.sign(np.diag(r))[None, :])
+        return PlantedCCA(Q[0], Q[1], s.copy(), 0.5, rhos.copy(), seed)
+
+    def thetas(n, stream):
+        return _rng(seed, _STREAM_MODEL + 100 + stream).uniform(-1.0, 1.0, size=(n, n_theta))
+
+    return {"model": model, "thetas": thetas, "omega": omega, "d_x": d_x, "k": k, "latent": latent}
