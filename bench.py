@@ -434,6 +434,134 @@ def measure_batch(dtype, steps, warmup, dev, seed=0, n_instances=64):
     return out
 
 
+def measure_warm(dev, seed=0, n_train=128, n_eval=16, max_steps=8000, check_every=200, target=1e-3):
+    """Learned warm start on a planted CCA family (d_x = d_y = 64, k = 4, 8 latent directions,
+    mixing matrices a smooth function of theta in [-1, 1]^8; reduced from the full-size family,
+    d_x = d_y = 1024, k = 16, 4096 instances, to fit the bench's time budget). The network is
+    trained on the plain solver's solutions of n_train instances; on n_eval held-out instances
+    the plain iteration runs from the network's V0 (warm) and from random V0 (cold) with the
+    same schedule; truth = the exact solution of each instance's resident row pool."""
+    import torch
+    from paper_2206_04993_gb300 import Batch, Solver, WarmStart, sgep
+    fam = synth.config_c5(seed=seed + 1, d_x=64, k=4, latent=8, spread=0.3)
+    d_x, k, b, nmb = 64, 4, 512, 32
+    d = 2 * d_x
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed + 29)
+    om = torch.tensor(fam["omega"], dtype=torch.float32, device=dev)
+
+    def pool(model):
+        Wx = torch.tensor(model.Qx * model.s, dtype=torch.float32, device=dev)
+        Wy = torch.tensor(model.Qy * model.s, dtype=torch.float32, device=dev)
+        z = torch.randn(nmb * b, model.s.size, device=dev, generator=g)
+        X = z @ Wx.T + 0.5 * torch.randn(nmb * b, d_x, device=dev, generator=g)
+        Y = z @ Wy.T + 0.5 * torch.randn(nmb * b, d_x, device=dev, generator=g)
+        # b/2 wrap-around rows so that odd epochs can shift the minibatch grid by b/2
+        return torch.cat([X, X[:b // 2]]).contiguous(), torch.cat([Y, Y[:b // 2]]).contiguous()
+
+    def solvers(n, V0=None):
+        # hold then harmonic: eta_t = 0.2 (100 + 20) / (t + 20) after t = 100 (the 64-dim workload's schedule)
+        ss = [Solver(kind=sgep.SGEP_CCA, d_x=d_x, d_y=d_x, k=k, max_b=b, path=sgep.SGEP_PATH_GENERIC, eta0=0.2,
+                     gamma0=0.3, rho=1e-6, schedule=sgep.SGEP_SCHED_HOLD_HARMONIC, t_c=100, T=max_steps,
+                     eta_T=0.2 * 120.0 / (max_steps + 20.0), seed=500 + i) for i in range(n)]
+        if V0 is not None:
+            for s_, v in zip(ss, V0):
+                s_.set_V(v)
+        return ss
+
+    def run(bt, pools, t0, count):
+        # odd epochs shift the grid by b/2 so that every row estimates A and B equally often
+        for t in range(t0, t0 + count):
+            o = (t // nmb) % 2 * (b // 2) + (t % nmb) * b
+            bt.step([X[o:o + b] for X, _ in pools], [Y[o:o + b] for _, Y in pools], [b] * len(pools))
+
+    train = [fam["model"](t) for t in fam["thetas"](n_train, 0)]
+    held = [fam["model"](t) for t in fam["thetas"](n_eval, 1)]
+    tp = [pool(m) for m in train]
+    ts = solvers(n_train)
+    with Batch(ts) as bt:
+        run(bt, tp, 0, 1000)
+        bt.sync()
+    targets = torch.tensor(np.concatenate([s_.V() for s_ in ts]), device=dev)
+    for s_ in ts:
+        s_.close()
+    t_start = time.time()
+    sk_train = torch.cat([WarmStart.sketch(X[:2048], Y[:2048], om) for X, Y in tp])
+    del tp
+    ws = WarmStart(m=16, k=k, seed=seed + 3)
+    seg = [i * d for i in range(n_train + 1)]
+    first = ws.loss_grad(sk_train, targets, seg)
+    for _ in range(300):
+        last = ws.loss_grad(sk_train, targets, seg)
+        ws.adam_step(3e-3)
+    train_s = time.time() - t_start
+    hp = [pool(m) for m in held]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ws.forward(WarmStart.sketch(hp[0][0][:2048], hp[0][1][:2048], om))  # warm-up (first-call set-up)
+    torch.cuda.synchronize()
+    t_inf = time.time()
+    e0.record()
+    outs = [ws.forward(WarmStart.sketch(X[:2048], Y[:2048], om)) for X, Y in hp]  # sketch + network
+    e1.record()
+    torch.cuda.synchronize()
+    infer_ms = (time.time() - t_inf) * 1e3 / n_eval
+    infer_dev_ms = e0.elapsed_time(e1) / n_eval
+    V0 = []
+    for o in outs:  # unit columns (the players' sphere)
+        v = o.cpu().numpy().astype(np.float64)
+        V0.append((v / np.linalg.norm(v, axis=0, keepdims=True)).astype(np.float32))
+    truths = []
+    for X, Y in hp:  # exact top-k solution of the pool (scipy, FP64), the unique rows only
+        Z = torch.cat([X[:nmb * b], Y[:nmb * b]], dim=1).double()
+        C = (Z.T @ Z / Z.shape[0]).cpu().numpy()
+        A = np.zeros_like(C)
+        A[:d_x, d_x:] = C[:d_x, d_x:]
+        A[d_x:, :d_x] = C[d_x:, :d_x]
+        B = np.zeros_like(C)
+        B[:d_x, :d_x] = C[:d_x, :d_x]
+        B[d_x:, d_x:] = C[d_x:, d_x:]
+        import scipy.linalg as sla
+        w, U = sla.eigh(A, B)
+        truths.append((U[:, ::-1][:, :k], B))
+    out = {"scale": "reduced: d_x = d_y = 64, k = 4, latent 8, 128 training / 16 held-out instances",
+           "train_loss": [first, last], "train_seconds_host": train_s,
+           "warm_start_inference_ms_per_instance": {"wall": infer_ms, "device": infer_dev_ms},
+           "target": target, "truth": "exact solution of each held-out instance's resident row pool"}
+    for name, init in (("cold", None), ("warm", V0)):
+        ss = solvers(n_eval, init)
+        reached = [None] * n_eval
+        err0 = [gen_subspace_error(Vt, s_.V().astype(np.float64), B) for s_, (Vt, B) in zip(ss, truths)]
+        dev_ms = 0.0
+        curve = []
+        with Batch(ss) as bt:
+            t = 0
+            while t < max_steps and any(r is None for r in reached):
+                e0.record()
+                run(bt, hp, t, check_every)
+                e1.record()
+                torch.cuda.synchronize()
+                dev_ms += e0.elapsed_time(e1)
+                t += check_every
+                errs = []
+                for i, (s_, (Vt, B)) in enumerate(zip(ss, truths)):
+                    e = gen_subspace_error(Vt, s_.V().astype(np.float64), B)
+                    errs.append(e)
+                    if reached[i] is None and e <= target:
+                        reached[i] = t
+                if t % (5 * check_every) == 0:
+                    curve.append([t, round(float(np.median(errs)), 6)])
+            bt.sync()
+        steps = [r for r in reached if r is not None]
+        out[name] = {"initial_error_median": float(np.median(err0)), "reached": len(steps), "of": n_eval,
+                     "median_steps": float(np.median(steps)) if steps else None,
+                     "device_seconds_all_instances": dev_ms / 1e3, "steps_run": t, "median_error_curve": curve}
+        for s_ in ss:
+            s_.close()
+    ws.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def cpu_cores():
     for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         if os.environ.get(var):
@@ -601,7 +729,8 @@ def run_native(args):
         torch.cuda.empty_cache()
         forms = {"cca_d32768_k32_b4096_bf16": measure_throughput("cca_d32768_k32_b4096_bf16", 60, 5, dev, rank),
                  "batch64_cca_lda_b512_f32": measure_batch("f32", 40, 3, dev, seed=rank),
-                 "batch64_cca_lda_b512_bf16": measure_batch("bf16", 40, 3, dev, seed=rank)}
+                 "batch64_cca_lda_b512_bf16": measure_batch("bf16", 40, 3, dev, seed=rank),
+                 "warm_start_cca_family": measure_warm(dev, seed=rank)}
 
     if rank == 0:
         line = {

@@ -587,9 +587,10 @@ int sketch_rows(const void* X, const void* Y, int dtype, int64_t n, int64_t dx, 
   const int64_t d = dx + dy;
   float* PQ = nullptr;
   float* rms = nullptr;
-  SGEP_CUDA_TRY(cudaMalloc((void**)&PQ, (size_t)n * 2 * m * sizeof(float)));
-  if (cudaMalloc((void**)&rms, m * sizeof(float)) != cudaSuccess) {
-    cudaFree(PQ);
+  // stream-ordered allocations: no device-wide synchronisation
+  SGEP_CUDA_TRY(cudaMallocAsync((void**)&PQ, (size_t)n * 2 * m * sizeof(float), s));
+  if (cudaMallocAsync((void**)&rms, m * sizeof(float), s) != cudaSuccess) {
+    cudaFreeAsync(PQ, s);
     return SGEP_ENOMEM;
   }
   int rc = SGEP_OK;
@@ -618,9 +619,9 @@ int sketch_rows(const void* X, const void* Y, int dtype, int64_t n, int64_t dx, 
   k_sk_rms<<<m, kThreads, 0, s>>>(out, d, m, rms);
   k_sk_scale<<<(unsigned)std::min<int64_t>((d * m + 255) / 256, 4LL * num_sms), 256, 0, s>>>(out, d, m, rms);
   if (cudaGetLastError() != cudaSuccess) rc = SGEP_ECUDA;
+  cudaFreeAsync(PQ, s);
+  cudaFreeAsync(rms, s);
   if (!rc && cudaStreamSynchronize(s) != cudaSuccess) rc = SGEP_ECUDA;
-  cudaFree(PQ);
-  cudaFree(rms);
   return rc;
 }
 
@@ -650,12 +651,13 @@ int sgep_sketch(const void* X, const void* Y, int dtype, int64_t n, int64_t d_x,
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))
     return warm_fail(SGEP_ECUDA, "no CUDA device");
-  int* flag = nullptr;
-  if (cudaMalloc((void**)&flag, sizeof(int)) != cudaSuccess) return warm_fail(SGEP_ENOMEM, "cudaMalloc");
-  cudaMemset(flag, 0, sizeof(int));
-  int rc = sgep::sketch_rows(X, d_y > 0 ? Y : nullptr, dtype, n, d_x, d_y, omega, m, out, sms, flag,
-                             (cudaStream_t)stream);
-  cudaFree(flag);
+  int* flag = nullptr;  // the sketch passes no labels, so nothing is ever flagged here
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMallocAsync((void**)&flag, sizeof(int), s) != cudaSuccess) return warm_fail(SGEP_ENOMEM, "cudaMallocAsync");
+  cudaMemsetAsync(flag, 0, sizeof(int), s);
+  int rc = sgep::sketch_rows(X, d_y > 0 ? Y : nullptr, dtype, n, d_x, d_y, omega, m, out, sms, flag, s);
+  cudaFreeAsync(flag, s);
+  cudaStreamSynchronize(s);
   return rc ? warm_fail(rc, "sketch failed") : SGEP_OK;
 }
 
