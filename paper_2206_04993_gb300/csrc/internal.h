@@ -78,6 +78,20 @@ struct Ctx {
   int tc_bar_reset = 0;            // the barrier count must be cleared before the next launch
   int tc_fused_dirty = 0;          // the replicas must be cleared before the next launch
   size_t tc_smem_p = 0, tc_smem_b = 0;
+  // one-read streamed products (kernels_tc_stream.cu)
+  int tc_st_ok = 0;                // the streamed kernel is set up for this handle
+  unsigned* tc_st_cnt = nullptr;   // [max_b / 128] contributions, then [max_b / 128] operand-ready flags
+  unsigned tc_st_epoch = 0;        // launches since the counters were last cleared
+  int tc_st_reset = 0;             // clear the counters (and the row sums) before the next launch
+  int tc_pq_dirty = 0;             // P and Q hold values another kernel left behind
+  unsigned long long* tc_st_trace = nullptr;  // SGEP_TRACE=1: per-CTA, per-chunk event times
+  int tc_st_nchunk = 0;            // chunks of the most recent streamed launch
+  int tc_st_grid = 0;              // its CTAs (streaming + builder helpers)
+  int tc_st_lag = 5, tc_st_helpers = 24;  // tuning knobs (SGEP_TC_LAG, SGEP_TC_HELPERS)
+  int tc_st_fuse = 1;              // the streamed launch also applies the update (SGEP_TC_STREAM_UPDATE)
+  int tc_st_updated = 0;           // the most recent streamed launch applied the step's update
+  int64_t tc_st_last_b = 0;        // minibatch size the counters were last used with
+  int tc_acc_stale = 0;            // acc does not hold the last step's products (not kept)
 
   // LDA: running class statistics (exact cumulative sums over every row seen)
   double* lda_sum = nullptr;  // C x d class sums
@@ -184,8 +198,9 @@ int make_map_bf16(CUtensorMap* map, const void* base, int64_t rows, int64_t cols
 bool tc_supported(const Ctx& c, const char** why);
 int tc_alloc(Ctx& c);
 void tc_free(Ctx& c);
-// acc <- [A_t V ; B_t V] of a BF16 minibatch on the tensor cores.
-int tc_products(Ctx& c, const void* X, const void* Y, int64_t b, cudaStream_t s);
+// acc <- [A_t V ; B_t V] of a BF16 minibatch on the tensor cores. eta, gamma: the step's
+// sizes, used when the streamed launch also applies the update.
+int tc_products(Ctx& c, const void* X, const void* Y, int64_t b, cudaStream_t s, float eta, float gamma);
 // k x k terms of the tensor-core path, double-buffered by step parity.
 struct TcTerms {
   float *a, *b, *norms, *G, *vv;
@@ -198,6 +213,15 @@ bool tc_fused_supported(const Ctx& c, int64_t b);
 int tc_fused_setup(Ctx& c);
 int tc_fused_products(Ctx& c, const CUtensorMap& mX, const CUtensorMap& mY, const CUtensorMap& mX64,
                       const CUtensorMap& mY64, const CUtensorMap& mVt, int64_t b, cudaStream_t s);
+// One-read streamed products (kernels_tc_stream.cu): acc, and the row-side terms a and b.
+bool tc_stream_supported(const Ctx& c, int64_t b);
+int tc_stream_setup(Ctx& c);
+void tc_stream_free(Ctx& c);
+int tc_stream_products(Ctx& c, const CUtensorMap& mX, const CUtensorMap& mY, const CUtensorMap& mX64,
+                       const CUtensorMap& mY64, const CUtensorMap& mVt, const CUtensorMap& mPt,
+                       const CUtensorMap& mQt, float* a_terms, float* b_terms, int64_t b, float eta,
+                       float gamma, cudaStream_t s);
+void tc_stream_trace_report(Ctx& c);
 // Update from acc with the k x k terms the tensor-core products accumulated.
 int tc_update(Ctx& c, float eta, float gamma, cudaStream_t s);
 

@@ -1021,10 +1021,13 @@ int tc_alloc(Ctx& c) {
   // two-pass products.
   const char* fused = getenv("SGEP_TC_FUSED");
   if (fused && fused[0] == '1') return tc_fused_setup(c);
-  return SGEP_OK;
+  // The streamed one-read kernel is the default where the shape allows it
+  // (SGEP_TC_STREAM=0 keeps the two-pass products).
+  return tc_stream_setup(c);
 }
 
 void tc_free(Ctx& c) {
+  tc_stream_free(c);
   cudaFree(c.tc_Vt);
   cudaFree(c.tc_PQ);
   cudaFree(c.tc_Pt);
@@ -1050,9 +1053,11 @@ void tc_free(Ctx& c) {
   c.tc_Pt = c.tc_Qt = nullptr;
 }
 
-int tc_products(Ctx& c, const void* X, const void* Y, int64_t b, cudaStream_t s) {
+int tc_products(Ctx& c, const void* X, const void* Y, int64_t b, cudaStream_t s, float eta, float gamma) {
   const int split = c.cfg.split_AB ? 1 : 0;
   const int64_t nA = split ? b / 2 : b;
+  c.tc_st_updated = 0;
+  c.tc_acc_stale = 0;
   if (b % 128 || ((uintptr_t)X & 15) || ((uintptr_t)Y & 15) || (split && nA % 64)) {
     c.tc_generic_step = 1;
     return generic_products(c, X, Y, b, s);
@@ -1078,6 +1083,14 @@ int tc_products(Ctx& c, const void* X, const void* Y, int64_t b, cudaStream_t s)
   if (!rc) rc = make_map_bf16(&mX2, X, b, c.d_x, c.d_x, 64, 64);
   if (!rc) rc = make_map_bf16(&mY2, Y, b, c.d_y, c.d_y, 64, 64);
   if (rc) return rc;
+  if (tc_stream_supported(c, b)) {
+    // one read of the minibatch from HBM: products and row-side terms in one persistent launch
+    rc = make_map_bf16(&mPt, c.tc_Pt, 2 * kTcKP, b, c.cfg.max_b, 64, 64);
+    if (!rc) rc = make_map_bf16(&mQt, c.tc_Qt, 2 * kTcKP, b, c.cfg.max_b, 64, 64);
+    if (!rc) rc = tc_stream_products(c, mX1, mY1, mX2, mY2, mVt, mPt, mQt, tt.a, tt.b, b, eta, gamma, s);
+    return rc;
+  }
+  c.tc_pq_dirty = 1;  // the kernels below leave P and Q non-zero
   if (c.tc_fused_buf && tc_fused_supported(c, b)) {
     // one read of the minibatch: products in one persistent launch, then the row-side terms
     rc = tc_fused_products(c, mX1, mY1, mX2, mY2, mVt, b, s);
@@ -1140,6 +1153,11 @@ int tc_products(Ctx& c, const void* X, const void* Y, int64_t b, cudaStream_t s)
 }
 
 int tc_update(Ctx& c, float eta, float gamma, cudaStream_t s) {
+  if (c.tc_st_updated) {  // the streamed launch applied the update and prepared the next step
+    c.tc_st_updated = 0;
+    c.tc_chain = 1;
+    return SGEP_OK;
+  }
   const int k = c.k;
   const int slot = (int)(c.t & 1);
   const TcTerms tt = tc_terms(c, slot);

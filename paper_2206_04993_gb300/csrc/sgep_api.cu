@@ -106,6 +106,7 @@ static int check_flag(Ctx& c) {
     if (flag & kFlagTimeout) {
       c.tc_fused_dirty = 1;  // an aborted one-read launch may leave partial sums behind
       c.tc_bar_reset = 1;    // ... and an aborted update a short barrier count
+      c.tc_st_reset = 1;     // ... and an aborted streamed launch short counters and row sums
       c.tc_chain = 0;
       return fail(SGEP_ETIMEOUT, "a bounded device-side wait gave up");
     }
@@ -329,7 +330,7 @@ static int do_step(Ctx& c, const void* X, const void* Y, const float* sx, const 
     rc = cluster_step(c, X, Y, b, eta, gamma, s);
   } else {
     if (c.path == SGEP_PATH_TC) {
-      rc = tc_products(c, X, Y, b, s);
+      rc = tc_products(c, X, Y, b, s, eta, gamma);
       if (!rc && c.tc_generic_step) c.tc_chain = 0;
       if (!rc) rc = c.tc_generic_step ? generic_update(c, eta, gamma, s) : tc_update(c, eta, gamma, s);
     } else {
@@ -375,6 +376,7 @@ int sgep_sync(sgep_t h, void* stream) {
   if (h->trace) cluster_trace_report(*h);
   if (h->tc_trace) tc_fused_trace_report(*h);
   if (h->tc_upd_trace) tc_update_trace_report(*h);
+  if (h->tc_st_trace) tc_stream_trace_report(*h);
   return rc;
 }
 
@@ -603,6 +605,8 @@ int sgep_debug_products(sgep_t h, float* AV, float* BV) {
     SGEP_CUDA_TRY(cudaDeviceSynchronize());
     return cluster_products(c, AV, BV, (cudaStream_t)0);
   }
+  if (c.tc_acc_stale)
+    return fail(SGEP_ESTATE, "the tensor-core step kept no products (create the handle with debug = 1)");
   SGEP_CUDA_TRY(cudaDeviceSynchronize());
   SGEP_CUDA_TRY(cudaMemcpy(AV, c.acc, dk * sizeof(float), cudaMemcpyDeviceToHost));
   if (c.b_is_identity) {

@@ -79,3 +79,70 @@ def test_tc_full_size_step_matches_oracle():
     print(err)
     for name, e in err.items():
         assert e <= TC_TOL, (name, e, err)
+
+
+# Shapes the one-read streamed products take (d_x a multiple of 512, b of 256): one and
+# several 256-row chunks, more row tiles than builder CTAs (d_x = 512, b = 1024), odd k.
+@pytest.mark.parametrize("dx,k,b", [(512, 32, 256), (512, 32, 512), (1024, 17, 768), (512, 4, 1024),
+                                    (2048, 32, 1024), (1536, 8, 512)])
+@pytest.mark.parametrize("fuse", ["1", "0"])
+def test_tc_stream_single_step_matches_oracle(dx, k, b, fuse, monkeypatch):
+    """One step of the streamed path, with the update in the same launch (fuse = 1) or in the
+    separate fused-update kernel (fuse = 0)."""
+    monkeypatch.setenv("SGEP_TC_STREAM_UPDATE", fuse)
+    model = synth.planted_cca(dx, dx, np.linspace(0.9, 0.3, 8), seed=dx + k + 1)
+    X, Y = synth.draw_rows(model, b, batch=4)
+    V0 = synth.random_unit_columns(2 * dx, k, seed=k + 7)
+    S0 = 0.8 * V0 + 0.05 * synth.random_unit_columns(2 * dx, k, seed=k + 8)
+    with _tc_solver(dx, k, eta0=0.3, gamma0=0.4, rho=1e-3, max_b=b) as s:
+        assert s.path == S.SGEP_PATH_TC
+        err = step_errors(s, V0, S0, X, Y, "cca", 0.3, 0.4, 1e-3, dtype="bf16")
+        # a chained step of the streamed path is one launch (products and update) or two
+        Xd = torch.from_numpy(X.astype(np.float32)).cuda().to(torch.bfloat16)
+        Yd = torch.from_numpy(Y.astype(np.float32)).cuda().to(torch.bfloat16)
+        l0 = s.launches
+        s.step(Xd, Yd)
+        s.sync()
+        assert s.launches - l0 == (1 if fuse == "1" else 2)
+    print(err)
+    for name, e in err.items():
+        assert e <= TC_TOL, (name, e, err)
+
+
+def test_tc_stream_matches_two_pass_over_steps(monkeypatch):
+    """Twenty steps of the streamed products and of the two-pass products on the same
+    BF16 minibatches (only the order of the FP32 sums differs)."""
+    from paper_2206_04993_gb300 import Solver
+    model = synth.planted_cca(1024, 1024, np.linspace(0.9, 0.3, 16), seed=9)
+    X, Y = synth.draw_rows(model, 512 * 20, batch=2)
+    Xd = torch.from_numpy(X.astype(np.float32)).cuda().to(torch.bfloat16)
+    Yd = torch.from_numpy(Y.astype(np.float32)).cuda().to(torch.bfloat16)
+    V0 = synth.random_unit_columns(2048, 32, seed=3).astype(np.float32)
+    out, launches = [], []
+    for env in ("0", "1"):
+        monkeypatch.setenv("SGEP_TC_STREAM", env)
+        with Solver(kind=S.SGEP_CCA, d_x=1024, d_y=1024, k=32, dtype=S.SGEP_BF16, path=S.SGEP_PATH_TC,
+                    eta0=0.2, gamma0=0.5, max_b=512) as s:
+            s.set_V(V0)
+            l0 = s.launches
+            s.step_many(Xd, Yd, 512, 20)
+            s.sync()
+            launches.append(s.launches - l0)
+            out.append(s.V())
+    assert launches[1] < launches[0], launches
+    assert np.linalg.norm(out[1] - out[0]) / np.linalg.norm(out[0]) < 1e-4
+
+
+def test_tc_stream_products_not_kept_without_debug(monkeypatch):
+    """Without debug the fused streamed step keeps no A_t V / B_t V; readback says so."""
+    from paper_2206_04993_gb300 import Solver
+    monkeypatch.setenv("SGEP_TC_STREAM_UPDATE", "1")
+    model = synth.planted_cca(512, 512, np.linspace(0.9, 0.3, 8), seed=4)
+    X, Y = synth.draw_rows(model, 256, batch=1)
+    with Solver(kind=S.SGEP_CCA, d_x=512, d_y=512, k=8, dtype=S.SGEP_BF16, path=S.SGEP_PATH_TC,
+                max_b=256) as s:
+        s.step(torch.from_numpy(X.astype(np.float32)).cuda().to(torch.bfloat16),
+               torch.from_numpy(Y.astype(np.float32)).cuda().to(torch.bfloat16))
+        s.sync()
+        with pytest.raises(S.SgepError):
+            s.products()
