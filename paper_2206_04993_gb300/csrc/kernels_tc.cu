@@ -425,19 +425,18 @@ __global__ void k_tc_normalize(const float* __restrict__ Vtmp, const float* __re
 
 // Update, retraction and the next step's V-side preparation in one launch, for
 // large-d problems (k <= 32). Blocks of 256 threads own 128 rows of V; all blocks
-// are resident (cooperative launch) and meet at two grid barriers. No atomics: every
-// cross-block sum goes through per-block partials.
+// are resident (cooperative launch) and meet at one grid barrier.
 //   phase 1: coefficients of Eq. (update) from a, G, b (and |v_i|^2 when eps_B > 0);
-//            v' = v + eta grad and the [Bv] step S' = S + gamma (BV - S) per row; the
-//            rows stay in shared memory; per-block column sums of v'^2 are stored.
-//   barrier 1; every block adds the column sums (the retraction needs all rows).
-//   phase 2: v = v' / |v'| written out, with its BF16 hi/lo pairs (the next step's
-//            transposed V operand); per-block partials of the next step's d-side
-//            terms G = V^T S' and |v_i|^2.
-//   barrier 2; block j adds entries [j per, (j + 1) per) of those partials.
-// The k x k terms are double-buffered by step parity: this launch reads slot `slot`
-// and writes slot 1 - slot. Block 0 clears a and b (accumulated by the next step's
-// row-side kernel) after barrier 1, when every block has read them.
+//            v' = v + eta grad and the [Bv] step S' = S + gamma (BV - S) per row, kept in
+//            shared memory; the block's column sums of v'^2 are added into norms[slot]
+//            (one atomic per column) and its partial of U = V'^T S' is stored.
+//   barrier;
+//   phase 2: v = v' / |v'| written out with its BF16 hi/lo pairs (the next step's
+//            transposed V operand); block j adds a slice of the U partials over all blocks:
+//            the next step's G = V^T S' = diag(1/|v'|) U, and |v_i|^2 = |v'_i|^2 / |v'_i|^2.
+// The k x k terms are double-buffered by step parity: this launch reads slot `slot` and
+// writes slot 1 - slot. After the barrier block 0 clears a and b (accumulated by the next
+// step's products) and norms[1 - slot] (accumulated by the next update).
 struct TcUpdArgs {
   const float* V;
   float* Vout;
@@ -445,7 +444,7 @@ struct TcUpdArgs {
   const float* AV;
   const float* BV;
   float* terms;   // a (kk) | b (k) | norms [2][k] | G [2][kk] | vv [2][k]
-  float* part;    // per-block partials: [grid][32] column sums, then [grid][32 * 32 + 32] terms
+  float* part;    // per-block partials of U: [grid][32 * 32]
   float* dbg;     // a | G | b as used by this update (debug), or null
   float* grad_out;
   __nv_bfloat16* Vt;
@@ -453,7 +452,7 @@ struct TcUpdArgs {
   int k, slot;
   float rho, eta, gamma, eps_B;
   unsigned long long* bar;  // grid-barrier arrivals (monotone)
-  unsigned long long bar_target;  // arrivals that complete barrier 1 (barrier 2: + grid)
+  unsigned long long bar_target;  // arrivals that complete this launch's barrier
   int* dflag;
   unsigned long long* trace;  // [grid][8] globaltimer stamps of the phases, or null
 };
@@ -474,12 +473,12 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* bar, unsigned l
 
 __global__ void __launch_bounds__(256) k_tc_update_fused(const TcUpdArgs u) {
   constexpr int R = 128;
-  constexpr int KT = kTcKP * kTcKP + kTcKP;  // terms per block partial
-  __shared__ float T[kTcKP * kTcKP];
-  __shared__ float cb[kTcKP], cac[kTcKP], inv_s[kTcKP], inv_n[kTcKP];
-  __shared__ float red[8][kTcKP];
-  __shared__ float vs[R][kTcKP + 1];
-  __shared__ float ss[R][kTcKP + 1];
+  constexpr int KP = kTcKP;
+  __shared__ float T[KP * KP];
+  __shared__ float cb[KP], cac[KP], inv_s[KP], inv_n[KP], nsq[KP];
+  __shared__ float red[8][KP];
+  __shared__ float vs[R][KP + 1];
+  __shared__ float ss[R][KP + 1];
   __shared__ int ok_s;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int k = u.k, kk = k * k, slot = u.slot;
@@ -495,28 +494,49 @@ __global__ void __launch_bounds__(256) k_tc_update_fused(const TcUpdArgs u) {
   float* vvs = Gs + 2 * kk;        // [2][k]
   const float* G = Gs + slot * kk;
   const float* vv = vvs + slot * k;
-  float* part_n = u.part;                      // [nblk][32]
-  float* part_t = u.part + (size_t)nblk * 32;  // [nblk][KT]
+  float* nsum = nrm + slot * k;    // column sums of v'^2 of this update (zero on entry)
+  float* part_t = u.part;          // [nblk][KP * KP]
   {
-    // a and G staged in shared memory (vs and ss are free until phase 1): one round trip
+    // a and G staged in shared memory (vs and ss are free until phase 1): every load in
+    // flight before the first store
     float* As = &vs[0][0];
     float* Gm = &ss[0][0];
-    for (int p = tid; p < kk; p += 256) {
-      As[p] = __ldcg(a + p);
-      Gm[p] = __ldcg(G + p);
+    float xa[4], xg[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int p = tid + 256 * q;
+      xa[q] = p < kk ? __ldcg(a + p) : 0.f;
+      xg[q] = p < kk ? __ldcg(G + p) : 0.f;
     }
-    if (tid < k) cb[tid] = fmaf(u.eps_B, __ldcg(vv + tid), __ldcg(bt + tid));
+    const float xb = tid < k ? __ldcg(bt + tid) : 0.f;
+    const float xv = tid < k ? __ldcg(vv + tid) : 0.f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int p = tid + 256 * q;
+      if (p < kk) {
+        As[p] = xa[q];
+        Gm[p] = xg[q];
+      }
+    }
+    if (tid < k) cb[tid] = fmaf(u.eps_B, xv, xb);
     __syncthreads();
     if (tid < k) inv_s[tid] = 1.f / fmaxf(Gm[tid * k + tid], u.rho);
     __syncthreads();
     for (int p = tid; p < kk; p += 256) {
       const int j = p / k, i = p % k;
-      T[j * kTcKP + i] = j < i ? cb[i] * As[i * k + j] * inv_s[j] : 0.f;
+      T[j * KP + i] = j < i ? cb[i] * As[i * k + j] * inv_s[j] : 0.f;
     }
     if (tid < k) {
       float c = 0.f;
       for (int j = 0; j < tid; ++j) c = fmaf(As[tid * k + j] * Gm[tid * k + j], inv_s[j], c);
       cac[tid] = As[tid * k + tid] - c;
+    }
+    if (blockIdx.x == 0 && u.dbg) {  // the terms as used (debug)
+      for (int p = tid; p < kk; p += 256) {
+        u.dbg[p] = As[p];
+        u.dbg[kk + p] = Gm[p];
+      }
+      if (tid < k) u.dbg[2 * kk + tid] = xb;
     }
     __syncthreads();
   }
@@ -563,53 +583,44 @@ __global__ void __launch_bounds__(256) k_tc_update_fused(const TcUpdArgs u) {
   }
   red[wid][lane] = nr;
   __syncthreads();
-  if (tid < kTcKP) {
+  if (tid < k) {
     float s2 = 0.f;
     for (int w = 0; w < 8; ++w) s2 += red[w][tid];
-    part_n[(size_t)blockIdx.x * 32 + tid] = s2;
+    atomicAdd(nsum + tid, s2);
+  }
+  {
+    // the block's partial of U = V'^T S': thread -> (row i of U, four consecutive columns)
+    const int i = tid >> 3, j0 = 4 * (tid & 7);
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+    for (int r = 0; r < R; ++r) {
+      const float x = vs[r][i];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = fmaf(x, ss[r][j0 + q], acc[q]);
+    }
+    *reinterpret_cast<float4*>(part_t + (size_t)blockIdx.x * KP * KP + i * KP + j0) =
+        make_float4(acc[0], acc[1], acc[2], acc[3]);
   }
   stamp(1);
   if (!grid_barrier(u.bar, u.bar_target, u.dflag, &ok_s)) return;
   stamp(2);
-  if (blockIdx.x == 0) {  // every block has read a, G and b: keep them (debug) and clear a and b
-    if (u.dbg) {
-      for (int p = tid; p < kk; p += 256) {
-        u.dbg[p] = __ldcg(a + p);
-        u.dbg[kk + p] = __ldcg(G + p);
-      }
-      if (tid < k) u.dbg[2 * kk + tid] = __ldcg(bt + tid);
-      __syncthreads();
-    }
+  if (blockIdx.x == 0) {  // every block has read a and b: clear them, and next update's sums
     for (int p = tid; p < kk; p += 256) a[p] = 0.f;
-    if (tid < k) bt[tid] = 0.f;
-  }
-  // column sums of v'^2 over all blocks (eight independent loads in flight per thread)
-  {
-    float s2 = 0.f;
-    for (int blk0 = wid; blk0 < nblk; blk0 += 64) {
-      float x[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int blk = blk0 + 8 * q;
-        x[q] = blk < nblk ? __ldcg(part_n + (size_t)blk * 32 + lane) : 0.f;
-      }
-#pragma unroll
-      for (int q = 0; q < 8; ++q) s2 += x[q];
+    if (tid < k) {
+      bt[tid] = 0.f;
+      nrm[(1 - slot) * k + tid] = 0.f;
     }
-    red[wid][lane] = s2;
   }
-  __syncthreads();
-  if (tid < kTcKP) {
-    float s2 = 0.f;
-    for (int w = 0; w < 8; ++w) s2 += red[w][tid];
+  if (tid < KP) {
+    const float s2 = tid < k ? __ldcg(nsum + tid) : 0.f;
+    nsq[tid] = s2;
     inv_n[tid] = tid < k ? 1.f / sqrtf(s2) : 0.f;
-    if (blockIdx.x == 0 && tid < k) nrm[slot * k + tid] = s2;
   }
   __syncthreads();
   // ---- phase 2 -----------------------------------------------------------------
   bool bad = false;
-  for (int e = tid; e < R * kTcKP; e += 256) {
-    const int r = e / kTcKP, i = e % kTcKP;
+  for (int e = tid; e < R * KP; e += 256) {
+    const int r = e / KP, i = e % KP;
     const float v = vs[r][i] * inv_n[i];
     vs[r][i] = v;
     if (i < k && c0 + r < u.d) {
@@ -620,12 +631,12 @@ __global__ void __launch_bounds__(256) k_tc_update_fused(const TcUpdArgs u) {
   if (bad) atomicOr(u.dflag, kFlagNonFinite);
   __syncthreads();
   // transposed BF16 pairs: thread -> (operand row n, two consecutive rows of V)
-  for (int e = tid; e < 2 * kTcKP * (R / 2); e += 256) {
+  for (int e = tid; e < 2 * KP * (R / 2); e += 256) {
     const int n = e / (R / 2), rp = 2 * (e % (R / 2));
     if (c0 + rp >= u.d) continue;  // d is even: rp + 1 < d as well
-    const float v0 = vs[rp][n % kTcKP], v1 = vs[rp + 1][n % kTcKP];
+    const float v0 = vs[rp][n % KP], v1 = vs[rp + 1][n % KP];
     __nv_bfloat162 w;
-    if (n < kTcKP) {
+    if (n < KP) {
       w = __floats2bfloat162_rn(v0, v1);
     } else {
       const float h0 = __bfloat162float(__float2bfloat16(v0)), h1 = __bfloat162float(__float2bfloat16(v1));
@@ -633,78 +644,30 @@ __global__ void __launch_bounds__(256) k_tc_update_fused(const TcUpdArgs u) {
     }
     *reinterpret_cast<__nv_bfloat162*>(u.Vt + (int64_t)n * u.d + c0 + rp) = w;
   }
-  // block partial of G = V^T S' (4 x 4 register tiles over four groups of 32 rows) and |v_i|^2
+  // entries [j per, (j + 1) per) of U over all blocks -> the next step's G and |v|^2
   {
-    const int tl = tid & 63, rg = tid >> 6;
-    const int i0 = 4 * (tl & 7), j0 = 4 * (tl >> 3);
-    float acc[4][4] = {};
-    for (int r = 32 * rg; r < 32 * rg + 32; ++r) {
-      float x[4], y[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        x[q] = vs[r][i0 + q];
-        y[q] = ss[r][j0 + q];
-      }
-#pragma unroll
-      for (int p = 0; p < 4; ++p)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(x[p], y[q], acc[p][q]);
-    }
-    float nv = 0.f;
-    if (tid < 128) {  // |v_i|^2: column i = tid % 32 over rows 32 (tid / 32) ..
-      const int i = tid & 31, g4 = tid >> 5;
-      for (int r = 32 * g4; r < 32 * g4 + 32; ++r) nv = fmaf(vs[r][i], vs[r][i], nv);
-    }
-    __syncthreads();  // vs is reused as the reduction buffer below
-    float* rbuf = &vs[0][0];  // [4][KT]
-#pragma unroll
-    for (int p = 0; p < 4; ++p)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) rbuf[rg * KT + (i0 + p) * kTcKP + j0 + q] = acc[p][q];
-    if (tid < 128) rbuf[(tid >> 5) * KT + kTcKP * kTcKP + (tid & 31)] = nv;
-    __syncthreads();
-    for (int e = tid; e < KT; e += 256)
-      part_t[(size_t)blockIdx.x * KT + e] = rbuf[e] + rbuf[KT + e] + rbuf[2 * KT + e] + rbuf[3 * KT + e];
-  }
-  stamp(3);
-  if (!grid_barrier(u.bar, u.bar_target + (unsigned long long)nblk, u.dflag, &ok_s)) return;
-  stamp(4);
-  // ---- entries [j per, (j + 1) per) of the next step's terms -------------------
-  {
-    __shared__ float sums[KT];
-    const int per = (KT + nblk - 1) / nblk;
+    const int per = (KP * KP + nblk - 1) / nblk;
     const int e0 = (int)blockIdx.x * per;
-    const int ne = max(0, min(per, KT - e0));
-    // warp per entry, lanes over the blocks (eight loads in flight per lane), shuffle sum
-    for (int el = wid; el < ne; el += 8) {
+    const int ne = max(0, min(per, KP * KP - e0));
+    float* Gn = Gs + (1 - slot) * kk;
+    for (int el = wid; el < ne; el += 8) {  // warp per entry, lanes over the blocks
       float s2 = 0.f;
       for (int blk0 = lane; blk0 < nblk; blk0 += 256) {
         float x[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const int blk = blk0 + 32 * q;
-          x[q] = blk < nblk ? __ldcg(part_t + (size_t)blk * KT + e0 + el) : 0.f;
+          x[q] = blk < nblk ? __ldcg(part_t + (size_t)blk * KP * KP + e0 + el) : 0.f;
         }
 #pragma unroll
         for (int q = 0; q < 8; ++q) s2 += x[q];
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-      if (lane == 0) sums[el] = s2;
+      const int te = e0 + el, i = te / KP, j = te % KP;
+      if (lane == 0 && i < k && j < k) Gn[i * k + j] = inv_n[i] * s2;
     }
-    __syncthreads();
-    float* Gn = Gs + (1 - slot) * kk;
-    float* vvn = vvs + (1 - slot) * k;
-    for (int e = tid; e < ne; e += 256) {
-      const int te = e0 + e;
-      if (te < kTcKP * kTcKP) {
-        const int i = te / kTcKP, j = te % kTcKP;
-        if (i < k && j < k) Gn[i * k + j] = sums[e];
-      } else {
-        const int i = te - kTcKP * kTcKP;
-        if (i < k) vvn[i] = sums[e];
-      }
-    }
+    if (blockIdx.x == 0 && tid < k) vvs[(1 - slot) * k + tid] = nsq[tid] * inv_n[tid] * inv_n[tid];
   }
   stamp(5);
 }
@@ -1200,7 +1163,7 @@ int tc_update(Ctx& c, float eta, float gamma, cudaStream_t s) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     SGEP_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_tc_update_fused, u));
-    c.tc_bar_base += 2 * (unsigned long long)grid;  // two barriers
+    c.tc_bar_base += (unsigned long long)grid;  // one barrier
     c.tc_chain = 1;
     ++c.launches;
     return SGEP_OK;
@@ -1310,10 +1273,11 @@ void tc_update_trace_report(Ctx& c) {
   unsigned long long g0 = ~0ull;
   for (int b = 0; b < n; ++b) g0 = std::min(g0, t[(size_t)b * 8]);
   std::fprintf(stderr, "[sgep trace] fused update, %d blocks (us from first start, median/max):", n);
-  const char* names[6] = {"start", "phase1", "bar1", "phase2", "bar2", "end"};
-  for (int ph = 0; ph < 6; ++ph) {
+  const char* names[4] = {"start", "phase1", "barrier", "end"};
+  const int ev[4] = {0, 1, 2, 5};
+  for (int ph = 0; ph < 4; ++ph) {
     std::vector<double> v;
-    for (int b = 0; b < n; ++b) v.push_back((t[(size_t)b * 8 + ph] - g0) / 1e3);
+    for (int b = 0; b < n; ++b) v.push_back((t[(size_t)b * 8 + ev[ph]] - g0) / 1e3);
     std::sort(v.begin(), v.end());
     std::fprintf(stderr, " %s %.2f/%.2f", names[ph], v[v.size() / 2], v.back());
   }
