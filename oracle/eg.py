@@ -9,6 +9,9 @@ Test infrastructure only (see the package header).
   v_i + eta_t grad_i followed by the retraction to the unit sphere, and the
   auxiliary step [Bv]_i + gamma_t (B_t v_i - [Bv]_i). All players read the
   state of step t (the parfor of Alg. 2), so V and [Bv] are updated together.
+* `eg_step_variant` adds the two variants of the paper: Adam on the players with the
+  warm-up / harmonic schedule (App. H.2.2) and the smooth denominators of Alg. 3
+  (App. E.2, extra scalars z_i).
 * `alg1_step` is the deterministic variant (Alg. 1) with exact A and B.
 * `utility` is Eq. util_new; `schedule_eta` is the warm-up plus harmonic decay
   of App. H.2.2.
@@ -207,6 +210,74 @@ def eg_step(V: np.ndarray, S: np.ndarray, Amv, Bmv, eta: float, gamma: float,
     if return_parts:
         return V_next, S_next, {"AV": AV, "BV": BV, "grad": grad}
     return V_next, S_next
+
+
+def smooth_denominator(z: np.ndarray, rho: float, nu: float) -> np.ndarray:
+    """[<v, B v>]_j of Alg. 3: exp(log rho + (log nu - log rho) sigmoid(z_j)), in (rho, nu)."""
+    z = np.asarray(z, dtype=np.float64)
+    sig = 1.0 / (1.0 + np.exp(-z))
+    return np.exp(np.log(rho) + (np.log(nu) - np.log(rho)) * sig)
+
+
+def eg_step_variant(V: np.ndarray, S: np.ndarray, Amv, Bmv, eta: float, gamma: float, rho: float,
+                    adam: dict | None = None, smooth: dict | None = None, return_parts: bool = False):
+    """One iteration of Alg. 2 (M = 1) with the two variants the paper describes.
+
+    smooth = {"z": z (k,), "nu": nu}: Alg. 3 (App. E.2). Player j's denominator is
+    s_j = exp(log rho + (log nu - log rho) sigmoid(z_j)) instead of max(<v_j, [Bv]_j>, rho);
+    every player also takes z_i <- z_i + gamma (<v_i, [Bv]_i> - s_i) s_i (log nu - log rho)
+    sigmoid(z_i) (1 - sigmoid(z_i)), with the state of step t.
+    adam = {"m": m, "s": s (d x k), "t": t (steps taken so far), "b1", "b2", "eps"}: the player
+    step of App. H.2.2 ("Adam on v_i"): with the update direction g_i of the step,
+    m_i <- b1 m_i + (1 - b1) g_i, s_i <- b2 s_i + (1 - b2) g_i^2 (elementwise),
+    v_i' = v_i + eta (m_i / (1 - b1^(t+1))) / (sqrt(s_i / (1 - b2^(t+1))) + eps), then v_i' / |v_i'|.
+    Reading: Adam replaces the plain step v_i + eta g_i of Alg. 2 and the retraction stays.
+    Returns (V_next, S_next, state) with state = {"adam": ..., "smooth": ...} (new dicts), and
+    with return_parts also a dict with AV, BV and grad.
+    """
+    V = np.asarray(V, dtype=np.float64)
+    S = np.asarray(S, dtype=np.float64)
+    d, k = V.shape
+    AV = Amv(V)
+    BV = Bmv(V)
+    if smooth is not None:
+        den = smooth_denominator(smooth["z"], rho, smooth["nu"])
+    else:
+        den = np.array([max(V[:, j] @ S[:, j], rho) for j in range(k)])
+    grad = np.zeros_like(V)
+    for i in range(k):
+        vi, Avi, Bvi = V[:, i], AV[:, i], BV[:, i]
+        vBv = vi @ Bvi
+        vAv = vi @ Avi
+        rewards = vBv * Avi - vAv * Bvi
+        penalties = np.zeros(d)
+        for j in range(i):
+            yj = V[:, j] / np.sqrt(den[j])
+            Byj = S[:, j] / np.sqrt(den[j])
+            penalties += (Avi @ yj) * (vBv * Byj - (vi @ Byj) * Bvi)
+        grad[:, i] = rewards - penalties
+    state = {}
+    if adam is not None:
+        b1, b2, eps, t = adam["b1"], adam["b2"], adam["eps"], int(adam["t"]) + 1
+        m = b1 * np.asarray(adam["m"], np.float64) + (1.0 - b1) * grad
+        s = b2 * np.asarray(adam["s"], np.float64) + (1.0 - b2) * grad * grad
+        step = (m / (1.0 - b1 ** t)) / (np.sqrt(s / (1.0 - b2 ** t)) + eps)
+        state["adam"] = {"m": m, "s": s, "t": t, "b1": b1, "b2": b2, "eps": eps}
+    else:
+        step = grad
+    Vp = V + eta * step
+    V_next = Vp / np.linalg.norm(Vp, axis=0, keepdims=True)
+    S_next = S + gamma * (BV - S)
+    if smooth is not None:
+        z = np.asarray(smooth["z"], np.float64)
+        nu = smooth["nu"]
+        sig = 1.0 / (1.0 + np.exp(-z))
+        c = np.array([V[:, i] @ S[:, i] for i in range(k)])
+        gz = (c - den) * den * (np.log(nu) - np.log(rho)) * sig * (1.0 - sig)
+        state["smooth"] = {"z": z + gamma * gz, "nu": nu}
+    if return_parts:
+        return V_next, S_next, state, {"AV": AV, "BV": BV, "grad": grad}
+    return V_next, S_next, state
 
 
 def alg1_step(V: np.ndarray, A: np.ndarray, B: np.ndarray, eta: float) -> np.ndarray:
