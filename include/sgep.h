@@ -77,6 +77,11 @@ extern "C" {
 #define SGEP_SCHED_WARMUP_HARMONIC 2 /* linear warm-up to eta0 at t_c, then as above   */
 
 /* ---- kernel path selection --------------------------------------------- */
+#define SGEP_OPT_SGD  0  /* player step of Alg. 2                                       */
+#define SGEP_OPT_ADAM 1  /* Adam on the players (App. H.2.2)                           */
+#define SGEP_ALG2     0  /* clipped denominators (Alg. 2)                              */
+#define SGEP_ALG3     1  /* smooth denominators with scalars z_j (Alg. 3, App. E.2)    */
+
 #define SGEP_PATH_AUTO    0  /* pick by shape and dtype                         */
 #define SGEP_PATH_GENERIC 1  /* multi-kernel SIMT path, any shape               */
 #define SGEP_PATH_CLUSTER 2  /* one fused cluster kernel per step, d <= 4096    */
@@ -107,11 +112,24 @@ typedef struct {
   uint64_t seed;       /* seed of the initial V (Philox-4x32-10 + Box-Muller)      */
   int64_t  max_b;      /* largest minibatch (rows) a step or readout chunk may use */
   int32_t  debug;      /* 1: keep update directions and k x k terms for sgep_debug_update */
-  int32_t  reserved[7];
+  int32_t  optimizer;  /* SGEP_OPT_SGD: Alg. 2's step v + eta grad; SGEP_OPT_ADAM: Adam on the */
+                       /* players (App. H.2.2): v + eta m_hat / (sqrt(s_hat) + adam_eps)        */
+  float    adam_b1;    /* Adam moment decays and floor (defaults 0.9, 0.999, 1e-8; App. H.2.2) */
+  float    adam_b2;
+  float    adam_eps;
+  int32_t  variant;    /* SGEP_ALG2: clipped denominators max(<v_j,[Bv]_j>, rho) (Alg. 2);     */
+                       /* SGEP_ALG3: smooth denominators exp(log rho + (log nu - log rho)       */
+                       /* sigmoid(z_j)) with one scalar z_j per player (Alg. 3, App. E.2)       */
+  float    nu;         /* Alg. 3: upper bound on lambda_max(B), > rho                           */
+  int32_t  reserved[1];
 } sgep_config;
 
 /* Fill `cfg` with defaults: CCA, F32, k = 1, eta0 = 0.1, gamma0 = 1, rho = 1e-6,
- * eps_B = 0, constant schedule, split_AB = 1, path AUTO, seed 0, max_b 4096.
+ * eps_B = 0, constant schedule, split_AB = 1, path AUTO, seed 0, max_b 4096,
+ * optimizer SGD (Adam decays 0.9, 0.999, floor 1e-8), variant Alg. 2.
+ * Adam and Alg. 3 run on the generic and tensor-core paths (AUTO avoids the cluster
+ * path for them); their state (Adam moments, z) is reset by sgep_set_V / sgep_set_VS
+ * and travels in the state blob.
  * Returns SGEP_EINVAL if cfg is NULL. */
 int sgep_config_default(sgep_config* cfg);
 
@@ -208,7 +226,8 @@ int sgep_rayleigh_ritz(sgep_t h, const void* X, const void* Y, const float* row_
 typedef struct sgep_batch_ctx* sgep_batch_t;
 
 /* Group n handles (host array) into a batch. Synchronises every handle first.
- * Errors: SGEP_EINVAL (NULL, duplicate, non-generic handle), SGEP_ENOMEM. */
+ * Errors: SGEP_EINVAL (NULL, duplicate, non-generic handle), SGEP_ENOTSUP (a handle
+ * with Adam or Alg. 3), SGEP_ENOMEM. */
 int sgep_batch_create(const sgep_t* handles, int n, sgep_batch_t* out);
 
 /* Free the batch (not the handles). NULL is accepted. */
@@ -369,7 +388,8 @@ int sgep_tc_selftest(int mode, double* max_rel_err);
  *    whose work overlaps on the GPU (other streams, other host threads) race
  *    on it and corrupt each other's results: serialise them.
  *  - Asynchronous on `stream`; non-finite values are not reported (inspect
- *    V_out). Errors: SGEP_EINVAL, SGEP_ECUDA. */
+ *    V_out). Errors: SGEP_EINVAL (also for cfg->optimizer = Adam or
+ *    cfg->variant = Alg. 3, whose state does not fit this call), SGEP_ECUDA. */
 #define SGEP_NOALLOC_SCRATCH_BYTES 4194304
 int sgep_step_noalloc(const sgep_config* cfg, const void* X, const void* Y, int64_t b,
                       const float* V, const float* S, float* V_out, float* S_out,

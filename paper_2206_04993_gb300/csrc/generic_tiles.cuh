@@ -25,7 +25,7 @@ constexpr int kProjectSmem = 32 * 33 + 32 * kMaxK;
 constexpr int kBackprojectSmem = 32 * 64 + 32 * 2 * kMaxK;
 __host__ __device__ constexpr int gram_smem(int k) { return 3 * 32 * k; }
 __host__ __device__ constexpr int update_smem(int k) {
-  return k * k + 3 * k + (kThreads / k > 1 ? kThreads / k : 1) * k;
+  return k * k + 4 * k + (kThreads / k > 1 ? kThreads / k : 1) * k;
 }
 __host__ __device__ constexpr int lda_stats_smem(int C) { return C * kThreads + kThreads; }
 constexpr int kLdaWSmem = kMaxClasses * 33 + 32 * (kMaxK + 1);
@@ -297,14 +297,20 @@ __device__ inline void gram_tile(const float* __restrict__ V, const float* __res
 __device__ inline void update_tile(const float* __restrict__ V, float* __restrict__ S, const float* __restrict__ AV,
                                    const float* __restrict__ BV, float* gram, int64_t d, int k, float eta,
                                    float gamma, float rho, float eps_B, int b_is_identity, float* __restrict__ Vtmp,
-                                   float* __restrict__ grad_out, int bx, int nb, float* smem) {
+                                   float* __restrict__ grad_out, int bx, int nb, float* smem,
+                                   const UpdVariant& var = UpdVariant()) {
   float* T = smem;               // k*k
   float* cb = T + k * k;         // k
   float* cac = cb + k;           // k
   float* nrm = cac + k;          // k
+  float* sden = nrm + k;         // k: Alg. 3 denominators
   const int rows = max(1, kThreads / k);
-  float* Ss = nrm + k;           // rows x k
-  eg_coefficients(gram, k, rho, cb, cac, T);
+  float* Ss = sden + k;          // rows x k
+  if (var.z) {
+    for (int j = threadIdx.x; j < k; j += blockDim.x) sden[j] = smooth_den(var.z[j], var.log_rho, var.log_nu);
+    __syncthreads();
+  }
+  eg_coefficients(gram, k, rho, cb, cac, T, var.z ? sden : nullptr);
   for (int i = threadIdx.x; i < k; i += blockDim.x) nrm[i] = 0.f;
   __syncthreads();
   const int tid = threadIdx.x;
@@ -324,7 +330,14 @@ __device__ inline void update_tile(const float* __restrict__ V, float* __restric
       float pen = 0.f;
       for (int j = 0; j < i; ++j) pen = fmaf(Ss[rl * k + j], T[j * k + i], pen);
       const float gr = cb[i] * AV[idx] - cac[i] * bv - pen;
-      const float vn = fmaf(eta, gr, v);
+      float step = gr;
+      if (var.m) {  // Adam on the players
+        float m = var.m[idx], s2 = var.s[idx];
+        step = adam_increment(gr, m, s2, var.b1, var.b2, var.eps, var.bc1, var.bc2);
+        var.m[idx] = m;
+        var.s[idx] = s2;
+      }
+      const float vn = fmaf(eta, step, v);
       Vtmp[idx] = vn;
       S[idx] = fmaf(gamma, bv - s_old, s_old);
       if (grad_out) grad_out[idx] = gr;
@@ -338,10 +351,16 @@ __device__ inline void update_tile(const float* __restrict__ V, float* __restric
 }
 
 // Retraction: v_i <- v'_i / ||v'_i||; flags non-finite norms. Grid-stride: tile `bx` of `nb`.
+// With Alg. 3 (var.z) tile 0 also takes the z step from the k x k terms G_ii = <v_i, [Bv]_i>
+// of step t (the update tiles have read z before this launch).
 __device__ inline void normalize_tile(const float* __restrict__ Vtmp, const float* __restrict__ gram,
-                                      float* __restrict__ V, int64_t d, int k, int* dflag, int bx, int nb) {
+                                      float* __restrict__ V, int64_t d, int k, int* dflag, int bx, int nb,
+                                      const UpdVariant& var = UpdVariant(), float gamma = 0.f) {
   const int64_t n = d * k;
   const float* norms = gram + 2 * k * k + k;
+  if (var.z && bx == 0)
+    for (int i = threadIdx.x; i < k; i += blockDim.x)
+      var.z[i] = smooth_z_step(var.z[i], gram[k * k + i * k + i], gamma, var.log_rho, var.log_nu);
   for (int64_t e = (int64_t)bx * blockDim.x + threadIdx.x; e < n; e += (int64_t)nb * blockDim.x) {
     const int i = (int)(e % k);
     const float v = Vtmp[e] / sqrtf(norms[i]);

@@ -13,6 +13,17 @@
 namespace sgep {
 
 // Per-handle device state. All device buffers are allocated once by sgep_init.
+// Variant parameters of one update (Adam on the players, App. H.2.2; smooth
+// denominators, Alg. 3). Null pointers select Alg. 2's plain step / clipping.
+struct UpdVariant {
+  float* m = nullptr;  // d x k Adam moments (read and written)
+  float* s = nullptr;
+  float b1 = 0.f, b2 = 0.f, eps = 0.f;
+  float bc1 = 1.f, bc2 = 1.f;  // 1 - b1^t, 1 - b2^t for this step
+  float* z = nullptr;  // k scalars of Alg. 3 (updated after the step)
+  float log_rho = 0.f, log_nu = 0.f;
+};
+
 struct Ctx {
   sgep_config cfg;
   int64_t d_x = 0, d_y = 0, d = 0;
@@ -32,6 +43,10 @@ struct Ctx {
   float* grad = nullptr;   // d x k update directions (debug only)
   double* rq = nullptr;    // 2k doubles: Rayleigh numerator / denominator sums
   int* dflag = nullptr;    // device error word: bit 0 non-finite, bit 1 timeout
+  float* adam_m = nullptr; // Adam: d x k first moments, then (adam_s) d x k second moments
+  float* adam_s = nullptr;
+  int64_t adam_t = 0;      // Adam steps since the moments were last reset
+  float* z = nullptr;      // Alg. 3: k scalars z_i
 
   // cluster path: ping-pong state buffers and three accumulator slots
   float* cl_V[2] = {nullptr, nullptr};
@@ -126,6 +141,8 @@ int cuda_fail(cudaError_t e, const char* what);
 
 // Step-size schedule (App. H.2.2), evaluated on the host.
 double schedule_eta(const sgep_config& c, int64_t t);
+// The variant parameters of the next update (advances the Adam step count).
+UpdVariant next_variant(Ctx& c);
 
 // ---- generic SIMT path (kernels_generic.cu) ----
 // Products of one minibatch: acc <- [A_t V ; B_t V], PQ scratch.

@@ -57,15 +57,16 @@ __global__ void __launch_bounds__(kThreads) k_update(const float* __restrict__ V
                                                      const float* __restrict__ AV, const float* __restrict__ BV,
                                                      float* gram, int64_t d, int k, float eta, float gamma,
                                                      float rho, float eps_B, int b_is_identity,
-                                                     float* __restrict__ Vtmp, float* __restrict__ grad_out) {
+                                                     float* __restrict__ Vtmp, float* __restrict__ grad_out,
+                                                     const UpdVariant var) {
   extern __shared__ float smem[];
   gt::update_tile(V, S, AV, BV, gram, d, k, eta, gamma, rho, eps_B, b_is_identity, Vtmp, grad_out, blockIdx.x,
-                  gridDim.x, smem);
+                  gridDim.x, smem, var);
 }
 
 __global__ void k_normalize(const float* __restrict__ Vtmp, const float* __restrict__ gram, float* __restrict__ V,
-                            int64_t d, int k, int* dflag) {
-  gt::normalize_tile(Vtmp, gram, V, d, k, dflag, blockIdx.x, gridDim.x);
+                            int64_t d, int k, int* dflag, const UpdVariant var, float gamma) {
+  gt::normalize_tile(Vtmp, gram, V, d, k, dflag, blockIdx.x, gridDim.x, var, gamma);
 }
 
 // k_rayleigh: num_i += sum_r 2 P_ri Q_ri (CCA, PLS) or P_ri^2 (PCA, and LDA's B rows);
@@ -193,12 +194,13 @@ int generic_update(Ctx& c, float eta, float gamma, cudaStream_t s) {
   const int rows = std::max(1, kThreads / k);
   const int ublocks = (int)std::min<int64_t>((c.d + rows - 1) / rows, grid_cap(c, 4));
   const size_t usm = sizeof(float) * gt::update_smem(k);
+  const UpdVariant var = next_variant(c);
   k_update<<<ublocks, kThreads, usm, s>>>(c.V, c.S, AV, BV, c.gram, c.d, k, eta, gamma, c.cfg.rho,
                                           c.cfg.eps_B, c.b_is_identity ? 1 : 0, c.Vtmp,
-                                          c.cfg.debug ? c.grad : nullptr);
+                                          c.cfg.debug ? c.grad : nullptr, var);
   SGEP_CUDA_TRY(cudaGetLastError());
   const int nblocks = (int)std::min<int64_t>((c.d * k + 255) / 256, grid_cap(c, 4));
-  k_normalize<<<nblocks, 256, 0, s>>>(c.Vtmp, c.gram, c.V, c.d, k, c.dflag);
+  k_normalize<<<nblocks, 256, 0, s>>>(c.Vtmp, c.gram, c.V, c.d, k, c.dflag, var, gamma);
   SGEP_CUDA_TRY(cudaGetLastError());
   c.launches += 3;
   return SGEP_OK;
@@ -206,7 +208,7 @@ int generic_update(Ctx& c, float eta, float gamma, cudaStream_t s) {
 
 int generic_normalize(Ctx& c, cudaStream_t s) {
   const int nblocks = (int)std::min<int64_t>((c.d * c.k + 255) / 256, grid_cap(c, 4));
-  k_normalize<<<nblocks, 256, 0, s>>>(c.Vtmp, c.gram, c.V, c.d, c.k, c.dflag);
+  k_normalize<<<nblocks, 256, 0, s>>>(c.Vtmp, c.gram, c.V, c.d, c.k, c.dflag, UpdVariant(), 0.f);
   SGEP_CUDA_TRY(cudaGetLastError());
   c.launches += 2;
   return SGEP_OK;

@@ -455,6 +455,7 @@ struct TcUpdArgs {
   unsigned long long bar_target;  // arrivals that complete this launch's barrier
   int* dflag;
   unsigned long long* trace;  // [grid][8] globaltimer stamps of the phases, or null
+  UpdVariant var;             // Adam on the players / Alg. 3 denominators, or plain Alg. 2
 };
 
 // Bounded grid barrier: returns false (and flags a timeout) when the wait gives up.
@@ -475,7 +476,7 @@ __global__ void __launch_bounds__(256) k_tc_update_fused(const TcUpdArgs u) {
   constexpr int R = 128;
   constexpr int KP = kTcKP;
   __shared__ float T[KP * KP];
-  __shared__ float cb[KP], cac[KP], inv_s[KP], inv_n[KP], nsq[KP];
+  __shared__ float cb[KP], cac[KP], inv_s[KP], inv_n[KP], nsq[KP], gdiag[KP];
   __shared__ float red[8][KP];
   __shared__ float vs[R][KP + 1];
   __shared__ float ss[R][KP + 1];
@@ -520,7 +521,11 @@ __global__ void __launch_bounds__(256) k_tc_update_fused(const TcUpdArgs u) {
     }
     if (tid < k) cb[tid] = fmaf(u.eps_B, xv, xb);
     __syncthreads();
-    if (tid < k) inv_s[tid] = 1.f / fmaxf(Gm[tid * k + tid], u.rho);
+    if (tid < k) {
+      gdiag[tid] = Gm[tid * k + tid];  // <v_i, [Bv]_i> of step t (Alg. 3's z step)
+      inv_s[tid] = 1.f / (u.var.z ? smooth_den(u.var.z[tid], u.var.log_rho, u.var.log_nu)
+                                  : fmaxf(Gm[tid * k + tid], u.rho));
+    }
     __syncthreads();
     for (int p = tid; p < kk; p += 256) {
       const int j = p / k, i = p % k;
@@ -558,6 +563,15 @@ __global__ void __launch_bounds__(256) k_tc_update_fused(const TcUpdArgs u) {
       bv[q] = ok ? __ldcg(u.BV + g) : 0.f;
       pen[q] = 0.f;
     }
+    float am[U], as2[U];  // Adam moments of the rows
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const int r = wid + 8 * q;
+      const int64_t g = (c0 + r) * k + lane;
+      const bool ok = u.var.m && on && c0 + r < u.d;
+      am[q] = ok ? u.var.m[g] : 0.f;
+      as2[q] = ok ? u.var.s[g] : 0.f;
+    }
     for (int j = 0; j < k; ++j) {
       const float t = T[j * kTcKP + lane];
 #pragma unroll
@@ -570,11 +584,17 @@ __global__ void __launch_bounds__(256) k_tc_update_fused(const TcUpdArgs u) {
       const bool ok = on && c0 + r < u.d;
       const float bve = fmaf(u.eps_B, v[q], bv[q]);
       const float gr = cb[lane] * av[q] - cac[lane] * bve - pen[q];
-      const float vn = ok ? fmaf(u.eta, gr, v[q]) : 0.f;
+      float step = gr;
+      if (u.var.m) step = adam_increment(gr, am[q], as2[q], u.var.b1, u.var.b2, u.var.eps, u.var.bc1, u.var.bc2);
+      const float vn = ok ? fmaf(u.eta, step, v[q]) : 0.f;
       const float sn = ok ? fmaf(u.gamma, bve - sv[q], sv[q]) : 0.f;
       if (ok) {
         u.S[g] = sn;
         if (u.grad_out) u.grad_out[g] = gr;
+        if (u.var.m) {
+          u.var.m[g] = am[q];
+          u.var.s[g] = as2[q];
+        }
       }
       vs[r][lane] = vn;
       ss[r][lane] = sn;
@@ -604,11 +624,12 @@ __global__ void __launch_bounds__(256) k_tc_update_fused(const TcUpdArgs u) {
   stamp(1);
   if (!grid_barrier(u.bar, u.bar_target, u.dflag, &ok_s)) return;
   stamp(2);
-  if (blockIdx.x == 0) {  // every block has read a and b: clear them, and next update's sums
+  if (blockIdx.x == 0) {  // every block has read a, b and z: clear a, b and next update's sums
     for (int p = tid; p < kk; p += 256) a[p] = 0.f;
     if (tid < k) {
       bt[tid] = 0.f;
       nrm[(1 - slot) * k + tid] = 0.f;
+      if (u.var.z) u.var.z[tid] = smooth_z_step(u.var.z[tid], gdiag[tid], u.gamma, u.var.log_rho, u.var.log_nu);
     }
   }
   if (tid < KP) {
@@ -1153,6 +1174,7 @@ int tc_update(Ctx& c, float eta, float gamma, cudaStream_t s) {
     u.bar_target = c.tc_bar_base + grid;
     u.trace = c.tc_upd_trace;
     u.dflag = c.dflag;
+    u.var = next_variant(c);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(256);

@@ -968,7 +968,7 @@ int tc_stream_setup(Ctx& c) {
   // SGEP_TC_STREAM_UPDATE=1 applies the update in the same launch (four warps per SM run it,
   // which is slower on GB300 than the separate fused-update kernel's 2048 warps)
   const char* fu = getenv("SGEP_TC_STREAM_UPDATE");
-  c.tc_st_fuse = (fu && fu[0] == '1') ? 1 : 0;
+  c.tc_st_fuse = (fu && fu[0] == '1' && !c.adam_m && !c.z) ? 1 : 0;  // the in-launch update is Alg. 2's
   // tuning knobs: SGEP_TC_LAG (chunks the projection may run ahead, 2..8; each chunk is
   // 256 rows of the minibatch kept in L2) and SGEP_TC_HELPERS (builder CTAs, 1..24)
   const char* lag = getenv("SGEP_TC_LAG");

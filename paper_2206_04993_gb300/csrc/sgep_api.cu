@@ -95,6 +95,8 @@ static void free_ctx(sgep_ctx* c) {
   cudaFree(c->grad);
   cudaFree(c->rq);
   cudaFree(c->dflag);
+  cudaFree(c->adam_m);
+  cudaFree(c->z);
   delete c;
 }
 
@@ -128,6 +130,26 @@ static int complete(Ctx& c, cudaStream_t s) {
   return check_flag(c);
 }
 
+UpdVariant next_variant(Ctx& c) {
+  UpdVariant v;
+  if (c.adam_m) {
+    ++c.adam_t;
+    v.m = c.adam_m;
+    v.s = c.adam_s;
+    v.b1 = c.cfg.adam_b1;
+    v.b2 = c.cfg.adam_b2;
+    v.eps = c.cfg.adam_eps;
+    v.bc1 = (float)(1.0 - std::pow((double)c.cfg.adam_b1, (double)c.adam_t));
+    v.bc2 = (float)(1.0 - std::pow((double)c.cfg.adam_b2, (double)c.adam_t));
+  }
+  if (c.z) {
+    v.z = c.z;
+    v.log_rho = std::log(c.cfg.rho);
+    v.log_nu = std::log(c.cfg.nu);
+  }
+  return v;
+}
+
 }  // namespace sgep
 
 using namespace sgep;
@@ -157,6 +179,12 @@ int sgep_config_default(sgep_config* cfg) {
   cfg->seed = 0;
   cfg->max_b = 4096;
   cfg->debug = 0;
+  cfg->optimizer = SGEP_OPT_SGD;
+  cfg->adam_b1 = 0.9f;
+  cfg->adam_b2 = 0.999f;
+  cfg->adam_eps = 1e-8f;
+  cfg->variant = SGEP_ALG2;
+  cfg->nu = 0.f;
   return SGEP_OK;
 }
 
@@ -186,6 +214,15 @@ int sgep_init(const sgep_config* cfg, sgep_t* out) {
     return fail(SGEP_EINVAL, "schedule needs 1 <= t_c < T and 0 < eta_T < eta0");
   if (g.max_b < 2 || g.max_b > (1LL << 24)) return fail(SGEP_EINVAL, "max_b out of range");
   if (g.path < 0 || g.path > 3) return fail(SGEP_EINVAL, "unknown path");
+  if (g.optimizer != SGEP_OPT_SGD && g.optimizer != SGEP_OPT_ADAM) return fail(SGEP_EINVAL, "unknown optimizer");
+  if (g.optimizer == SGEP_OPT_ADAM &&
+      (!(g.adam_b1 >= 0.f && g.adam_b1 < 1.f) || !(g.adam_b2 >= 0.f && g.adam_b2 < 1.f) || !(g.adam_eps >= 0.f) ||
+       !std::isfinite(g.adam_eps)))
+    return fail(SGEP_EINVAL, "Adam needs 0 <= b1, b2 < 1 and a finite eps >= 0");
+  if (g.variant != SGEP_ALG2 && g.variant != SGEP_ALG3) return fail(SGEP_EINVAL, "unknown variant");
+  if (g.variant == SGEP_ALG3 && !(g.nu > g.rho && std::isfinite(g.nu)))
+    return fail(SGEP_EINVAL, "Alg. 3 needs a finite nu > rho");
+  const bool variants = g.optimizer == SGEP_OPT_ADAM || g.variant == SGEP_ALG3;
 
   sgep_ctx* c = new (std::nothrow) sgep_ctx();
   if (!c) return fail(SGEP_ENOMEM, "host allocation failed");
@@ -231,6 +268,23 @@ int sgep_init(const sgep_config* cfg, sgep_t* out) {
       return cuda_fail(e, "cudaMalloc (debug)");
     }
   }
+  if (g.optimizer == SGEP_OPT_ADAM) {  // Adam moments, zero at the start
+    e = cudaMalloc((void**)&c->adam_m, 2 * dk * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(c->adam_m, 0, 2 * dk * sizeof(float));
+    if (e != cudaSuccess) {
+      free_ctx(c);
+      return cuda_fail(e, "cudaMalloc (Adam moments)");
+    }
+    c->adam_s = c->adam_m + dk;
+  }
+  if (g.variant == SGEP_ALG3) {  // z_i = 0 at the start (Alg. 3)
+    e = cudaMalloc((void**)&c->z, (size_t)g.k * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(c->z, 0, (size_t)g.k * sizeof(float));
+    if (e != cudaSuccess) {
+      free_ctx(c);
+      return cuda_fail(e, "cudaMalloc (Alg. 3 scalars)");
+    }
+  }
   cudaMemset(c->dflag, 0, sizeof(int));
   cudaMemset(c->acc, 0, 2 * dk * sizeof(float));
 
@@ -252,8 +306,13 @@ int sgep_init(const sgep_config* cfg, sgep_t* out) {
   } else if (generic_only) {
     // FP8 rows: the generic kernels dequantise with the per-row scales
   } else if (g.path == SGEP_PATH_AUTO) {
-    c->path = cl_ok ? SGEP_PATH_CLUSTER : (tc_supported(*c, nullptr) ? SGEP_PATH_TC : SGEP_PATH_GENERIC);
+    c->path = (cl_ok && !variants) ? SGEP_PATH_CLUSTER
+                                   : (tc_supported(*c, nullptr) ? SGEP_PATH_TC : SGEP_PATH_GENERIC);
   } else if (g.path == SGEP_PATH_CLUSTER) {
+    if (variants) {
+      free_ctx(c);
+      return fail(SGEP_ENOTSUP, "cluster path: Adam and Alg. 3 run on the generic and tensor-core paths");
+    }
     if (!cl_ok) {
       free_ctx(c);
       return fail(SGEP_ENOTSUP, std::string("cluster path: ") + (why ? why : "unsupported"));
@@ -274,6 +333,15 @@ int sgep_init(const sgep_config* cfg, sgep_t* out) {
     if (rc) {
       free_ctx(c);
       return rc;
+    }
+    if (c->path == SGEP_PATH_TC && variants && !c->tc_upd_fused) {
+      // Adam and Alg. 3 are in the fused tensor-core update, which needs every block resident
+      if (g.path == SGEP_PATH_TC) {
+        free_ctx(c);
+        return fail(SGEP_ENOTSUP, "tensor-core path: Adam / Alg. 3 need the fused update (d too large)");
+      }
+      tc_free(*c);
+      c->path = SGEP_PATH_GENERIC;
     }
   }
 
@@ -414,6 +482,10 @@ int sgep_set_VS(sgep_t h, const float* V, const float* S, int on_device, void* s
   const cudaMemcpyKind kd = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   SGEP_CUDA_TRY(cudaMemcpyAsync(c.V, V, sizeof(float) * c.d * c.k, kd, s));
   SGEP_CUDA_TRY(cudaMemcpyAsync(c.S, S, sizeof(float) * c.d * c.k, kd, s));
+  // a new start: Adam's moments and Alg. 3's scalars restart from zero as at sgep_init
+  if (c.adam_m) SGEP_CUDA_TRY(cudaMemsetAsync(c.adam_m, 0, 2 * sizeof(float) * c.d * c.k, s));
+  if (c.z) SGEP_CUDA_TRY(cudaMemsetAsync(c.z, 0, sizeof(float) * c.k, s));
+  c.adam_t = 0;
   SGEP_CUDA_TRY(cudaStreamSynchronize(s));
   c.debug_valid = 0;
   c.tc_chain = 0;
@@ -487,6 +559,12 @@ int sgep_get_eigenvalues(sgep_t h, const void* X, const void* Y, const float* ro
 static size_t lda_state_bytes(const Ctx& c) {
   return c.cfg.kind == SGEP_LDA ? ((size_t)c.cfg.n_classes * c.d + c.cfg.n_classes) * sizeof(double) : 0;
 }
+// Adam moments (2 d k floats) and their step count; Alg. 3's k scalars z.
+static size_t variant_state_bytes(const Ctx& c) {
+  const size_t dk = (size_t)c.d * c.k;
+  return (c.adam_m ? 2 * dk * sizeof(float) + sizeof(int64_t) : 0) + (c.z ? (size_t)c.k * sizeof(float) : 0);
+}
+static int32_t variant_flags(const Ctx& c) { return (c.adam_m ? 1 : 0) | (c.z ? 2 : 0); }
 
 struct StateHeader {
   char magic[8];
@@ -494,7 +572,7 @@ struct StateHeader {
   int32_t kind;
   int64_t d_x, d_y;
   int32_t k;
-  int32_t pad;
+  int32_t variants;  // bit 0: Adam moments follow, bit 1: Alg. 3 scalars follow
   int64_t t;
 };
 
@@ -521,7 +599,7 @@ int sgep_get_state(sgep_t h, void* buf, size_t* nbytes) {
   if (!h || !nbytes) return fail(SGEP_EINVAL, "NULL argument");
   Ctx& c = *h;
   const size_t dk = (size_t)c.d * c.k;
-  const size_t need = sizeof(StateHeader) + 2 * dk * sizeof(float) + lda_state_bytes(c);
+  const size_t need = sizeof(StateHeader) + 2 * dk * sizeof(float) + lda_state_bytes(c) + variant_state_bytes(c);
   if (!buf) {
     *nbytes = need;
     return SGEP_OK;
@@ -537,6 +615,7 @@ int sgep_get_state(sgep_t h, void* buf, size_t* nbytes) {
   hd.d_x = c.d_x;
   hd.d_y = c.d_y;
   hd.k = c.k;
+  hd.variants = variant_flags(c);
   hd.t = c.t;
   char* p = (char*)buf;
   std::memcpy(p, &hd, sizeof(hd));
@@ -549,6 +628,15 @@ int sgep_get_state(sgep_t h, void* buf, size_t* nbytes) {
     SGEP_CUDA_TRY(cudaMemcpy(q, c.lda_sum, cd * sizeof(double), cudaMemcpyDeviceToHost));
     SGEP_CUDA_TRY(cudaMemcpy(q + cd * sizeof(double), c.lda_cnt, c.cfg.n_classes * sizeof(double),
                              cudaMemcpyDeviceToHost));
+  }
+  {
+    char* q = p + sizeof(hd) + 2 * dk * sizeof(float) + lda_state_bytes(c);
+    if (c.adam_m) {  // m, s, step count
+      SGEP_CUDA_TRY(cudaMemcpy(q, c.adam_m, 2 * dk * sizeof(float), cudaMemcpyDeviceToHost));
+      std::memcpy(q + 2 * dk * sizeof(float), &c.adam_t, sizeof(int64_t));
+      q += 2 * dk * sizeof(float) + sizeof(int64_t);
+    }
+    if (c.z) SGEP_CUDA_TRY(cudaMemcpy(q, c.z, (size_t)c.k * sizeof(float), cudaMemcpyDeviceToHost));
   }
   *nbytes = need;
   return SGEP_OK;
@@ -565,7 +653,9 @@ int sgep_set_state(sgep_t h, const void* buf, size_t nbytes) {
     return fail(SGEP_ESTATE, "not a state blob of this version");
   if (hd.kind != c.cfg.kind || hd.d_x != c.d_x || hd.d_y != c.d_y || hd.k != c.k)
     return fail(SGEP_ESTATE, "state blob has a different kind or shape");
-  if (nbytes != sizeof(StateHeader) + 2 * dk * sizeof(float) + lda_state_bytes(c))
+  if (hd.variants != variant_flags(c))
+    return fail(SGEP_ESTATE, "state blob has a different optimizer or variant");
+  if (nbytes != sizeof(StateHeader) + 2 * dk * sizeof(float) + lda_state_bytes(c) + variant_state_bytes(c))
     return fail(SGEP_ESTATE, "state blob has the wrong size");
   int rc = complete(c, (cudaStream_t)0);
   if (rc) return rc;
@@ -581,6 +671,15 @@ int sgep_set_state(sgep_t h, const void* buf, size_t nbytes) {
     rc = lda_refresh(c, (cudaStream_t)0);
     if (rc) return rc;
     SGEP_CUDA_TRY(cudaDeviceSynchronize());
+  }
+  {
+    const char* q = p + 2 * dk * sizeof(float) + lda_state_bytes(c);
+    if (c.adam_m) {
+      SGEP_CUDA_TRY(cudaMemcpy(c.adam_m, q, 2 * dk * sizeof(float), cudaMemcpyHostToDevice));
+      std::memcpy(&c.adam_t, q + 2 * dk * sizeof(float), sizeof(int64_t));
+      q += 2 * dk * sizeof(float) + sizeof(int64_t);
+    }
+    if (c.z) SGEP_CUDA_TRY(cudaMemcpy(c.z, q, (size_t)c.k * sizeof(float), cudaMemcpyHostToDevice));
   }
   c.t = hd.t;
   c.debug_valid = 0;

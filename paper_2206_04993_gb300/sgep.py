@@ -23,6 +23,8 @@ SGEP_PCA, SGEP_CCA, SGEP_PLS, SGEP_LDA = 0, 1, 2, 3
 SGEP_F32, SGEP_BF16, SGEP_FP8E4M3 = 0, 1, 2
 SGEP_SCHED_CONST, SGEP_SCHED_HOLD_HARMONIC, SGEP_SCHED_WARMUP_HARMONIC = 0, 1, 2
 SGEP_PATH_AUTO, SGEP_PATH_GENERIC, SGEP_PATH_CLUSTER, SGEP_PATH_TC = 0, 1, 2, 3
+SGEP_OPT_SGD, SGEP_OPT_ADAM = 0, 1
+SGEP_ALG2, SGEP_ALG3 = 0, 1
 
 
 class sgep_config(ctypes.Structure):
@@ -35,7 +37,9 @@ class sgep_config(ctypes.Structure):
         ("schedule", ctypes.c_int32), ("split_AB", ctypes.c_int32),
         ("t_c", ctypes.c_int64), ("T", ctypes.c_int64), ("eta_T", ctypes.c_float),
         ("path", ctypes.c_int32), ("seed", ctypes.c_uint64), ("max_b", ctypes.c_int64),
-        ("debug", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7),
+        ("debug", ctypes.c_int32), ("optimizer", ctypes.c_int32), ("adam_b1", ctypes.c_float),
+        ("adam_b2", ctypes.c_float), ("adam_eps", ctypes.c_float), ("variant", ctypes.c_int32),
+        ("nu", ctypes.c_float), ("reserved", ctypes.c_int32 * 1),
     ]
 
 
