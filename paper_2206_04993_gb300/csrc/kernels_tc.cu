@@ -472,7 +472,9 @@ __device__ __forceinline__ bool grid_barrier(unsigned long long* bar, unsigned l
   return *ok_s != 0;
 }
 
-__global__ void __launch_bounds__(256) k_tc_update_fused(const TcUpdArgs u) {
+// kVar: the Adam / Alg. 3 code is compiled in (the plain Alg. 2 update keeps its registers).
+template <bool kVar>
+__global__ void __launch_bounds__(256, 2) k_tc_update_fused(const TcUpdArgs u) {
   constexpr int R = 128;
   constexpr int KP = kTcKP;
   __shared__ float T[KP * KP];
@@ -523,8 +525,8 @@ __global__ void __launch_bounds__(256) k_tc_update_fused(const TcUpdArgs u) {
     __syncthreads();
     if (tid < k) {
       gdiag[tid] = Gm[tid * k + tid];  // <v_i, [Bv]_i> of step t (Alg. 3's z step)
-      inv_s[tid] = 1.f / (u.var.z ? smooth_den(u.var.z[tid], u.var.log_rho, u.var.log_nu)
-                                  : fmaxf(Gm[tid * k + tid], u.rho));
+      inv_s[tid] = 1.f / ((kVar && u.var.z) ? smooth_den(u.var.z[tid], u.var.log_rho, u.var.log_nu)
+                                            : fmaxf(Gm[tid * k + tid], u.rho));
     }
     __syncthreads();
     for (int p = tid; p < kk; p += 256) {
@@ -563,14 +565,16 @@ __global__ void __launch_bounds__(256) k_tc_update_fused(const TcUpdArgs u) {
       bv[q] = ok ? __ldcg(u.BV + g) : 0.f;
       pen[q] = 0.f;
     }
-    float am[U], as2[U];  // Adam moments of the rows
+    float am[kVar ? U : 1], as2[kVar ? U : 1];  // Adam moments of the rows
+    if constexpr (kVar) {
 #pragma unroll
-    for (int q = 0; q < U; ++q) {
-      const int r = wid + 8 * q;
-      const int64_t g = (c0 + r) * k + lane;
-      const bool ok = u.var.m && on && c0 + r < u.d;
-      am[q] = ok ? u.var.m[g] : 0.f;
-      as2[q] = ok ? u.var.s[g] : 0.f;
+      for (int q = 0; q < U; ++q) {
+        const int r = wid + 8 * q;
+        const int64_t g = (c0 + r) * k + lane;
+        const bool ok = u.var.m && on && c0 + r < u.d;
+        am[q] = ok ? u.var.m[g] : 0.f;
+        as2[q] = ok ? u.var.s[g] : 0.f;
+      }
     }
     for (int j = 0; j < k; ++j) {
       const float t = T[j * kTcKP + lane];
@@ -585,15 +589,19 @@ __global__ void __launch_bounds__(256) k_tc_update_fused(const TcUpdArgs u) {
       const float bve = fmaf(u.eps_B, v[q], bv[q]);
       const float gr = cb[lane] * av[q] - cac[lane] * bve - pen[q];
       float step = gr;
-      if (u.var.m) step = adam_increment(gr, am[q], as2[q], u.var.b1, u.var.b2, u.var.eps, u.var.bc1, u.var.bc2);
+      if constexpr (kVar) {
+        if (u.var.m) step = adam_increment(gr, am[q], as2[q], u.var.b1, u.var.b2, u.var.eps, u.var.bc1, u.var.bc2);
+      }
       const float vn = ok ? fmaf(u.eta, step, v[q]) : 0.f;
       const float sn = ok ? fmaf(u.gamma, bve - sv[q], sv[q]) : 0.f;
       if (ok) {
         u.S[g] = sn;
         if (u.grad_out) u.grad_out[g] = gr;
-        if (u.var.m) {
-          u.var.m[g] = am[q];
-          u.var.s[g] = as2[q];
+        if constexpr (kVar) {
+          if (u.var.m) {
+            u.var.m[g] = am[q];
+            u.var.s[g] = as2[q];
+          }
         }
       }
       vs[r][lane] = vn;
@@ -629,7 +637,8 @@ __global__ void __launch_bounds__(256) k_tc_update_fused(const TcUpdArgs u) {
     if (tid < k) {
       bt[tid] = 0.f;
       nrm[(1 - slot) * k + tid] = 0.f;
-      if (u.var.z) u.var.z[tid] = smooth_z_step(u.var.z[tid], gdiag[tid], u.gamma, u.var.log_rho, u.var.log_nu);
+      if (kVar && u.var.z)
+        u.var.z[tid] = smooth_z_step(u.var.z[tid], gdiag[tid], u.gamma, u.var.log_rho, u.var.log_nu);
     }
   }
   if (tid < KP) {
@@ -988,7 +997,9 @@ int tc_alloc(Ctx& c) {
     // the fused update needs every block resident at once
     int per_sm = 0;
     const int grid = (int)((c.d + 127) / 128);
-    c.tc_upd_fused = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_update_fused, 256, 0) ==
+    const bool var = c.adam_m || c.z;
+    c.tc_upd_fused = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                         &per_sm, var ? k_tc_update_fused<true> : k_tc_update_fused<false>, 256, 0) ==
                              cudaSuccess &&
                          grid <= per_sm * c.num_sms
                      ? 1
@@ -1184,7 +1195,8 @@ int tc_update(Ctx& c, float eta, float gamma, cudaStream_t s) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    SGEP_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_tc_update_fused, u));
+    if (u.var.m || u.var.z) SGEP_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_tc_update_fused<true>, u));
+    else SGEP_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_tc_update_fused<false>, u));
     c.tc_bar_base += (unsigned long long)grid;  // one barrier
     c.tc_chain = 1;
     ++c.launches;

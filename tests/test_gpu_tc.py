@@ -76,6 +76,14 @@ def test_tc_full_size_step_matches_oracle():
     S0 = 0.8 * V0 + 0.05 * synth.random_unit_columns(32768, 32, seed=1)
     with _tc_solver(16384, 32, eta0=0.3, gamma0=0.3, rho=1e-6, max_b=4096) as s:
         err = step_errors(s, V0, S0, X, Y, "cca", 0.3, 0.3, 1e-6, dtype="bf16")
+        # at this size the update must still be the one-launch fused kernel (all of its
+        # blocks resident): a chained step is the streamed products plus that update
+        Xd = torch.from_numpy(np.asarray(X, np.float32)).cuda().to(torch.bfloat16)
+        Yd = torch.from_numpy(np.asarray(Y, np.float32)).cuda().to(torch.bfloat16)
+        l0 = s.launches
+        s.step(Xd, Yd)
+        s.sync()
+        assert s.launches - l0 == 2
     print(err)
     for name, e in err.items():
         assert e <= TC_TOL, (name, e, err)
