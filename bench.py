@@ -728,9 +728,13 @@ def run_native(args):
         del X, Y
         torch.cuda.empty_cache()
         forms = {"cca_d32768_k32_b4096_bf16": measure_throughput("cca_d32768_k32_b4096_bf16", 60, 5, dev, rank),
+                 # the plain FP32 form of the same problem (generic SIMT path; no FP32 tensor-core path)
+                 "cca_d32768_k32_b4096_f32": measure_throughput("cca_d32768_k32_b4096_f32", 8, 2, dev, rank),
                  "batch64_cca_lda_b512_f32": measure_batch("f32", 40, 3, dev, seed=rank),
                  "batch64_cca_lda_b512_bf16": measure_batch("bf16", 40, 3, dev, seed=rank),
                  "warm_start_cca_family": measure_warm(dev, seed=rank)}
+        forms["bf16_vs_f32_step_speedup_d32768"] = (forms["cca_d32768_k32_b4096_f32"]["ms_per_step"] /
+                                                    forms["cca_d32768_k32_b4096_bf16"]["ms_per_step"])
 
     if rank == 0:
         line = {
