@@ -15,6 +15,7 @@ Test infrastructure only (see the package header).
 * `alg1_step` is the deterministic variant (Alg. 1) with exact A and B.
 * `utility` is Eq. util_new; `schedule_eta` is the warm-up plus harmonic decay
   of App. H.2.2.
+* `ica_ops` is the ICA pencil of Sec. 1 with the quarter reading of independent batches.
 * The operators `*_ops` build the minibatch mat-vecs U -> A_t U and U -> B_t U
   from data rows without forming A_t or B_t (Sec. 1: A and B are expectations
   of outer products, applied through matrix-vector products). "Independent
@@ -84,6 +85,41 @@ def pca_ops(X: np.ndarray, eps_B: float = 0.0):
         return X.T @ (X @ np.asarray(U, dtype=np.float64)) / b
 
     return Amv, (lambda U: (1.0 + eps_B) * np.asarray(U, dtype=np.float64))
+
+
+def ica_ops(X: np.ndarray, split: bool = True, eps_B: float = 0.0):
+    """ICA minibatch operators (Sec. 1, ICA): A = E[<x,x> x x^T] - tr(B) B - 2 B^2, B = E[x x^T].
+
+    A holds products of expectations, so "independent data batches" (Alg. 2) is read with the
+    rows in four quarters Q1..Q4 (the last takes the remainder): the kurtosis term of A from Q1,
+    tr(B) and the outer B of B^2 from Q2, the B multiplying them from Q3, and B_t from Q4. Every
+    product then pairs independent rows and A_t, B_t are unbiased. Without the split every
+    term uses every row (the finite-sample pencil of those rows).
+    """
+    X = np.asarray(X, dtype=np.float64)
+    b = X.shape[0]
+    if split:
+        q = b // 4
+        X1, X2, X3, X4 = X[:q], X[q:2 * q], X[2 * q:3 * q], X[3 * q:]
+    else:
+        X1 = X2 = X3 = X4 = X
+
+    def Bq(Z, U):
+        return Z.T @ (Z @ U) / Z.shape[0]
+
+    w1 = np.einsum("rd,rd->r", X1, X1)
+    tr2 = np.einsum("rd,rd->", X2, X2) / X2.shape[0]
+
+    def Amv(U):
+        U = np.asarray(U, dtype=np.float64)
+        B3U = Bq(X3, U)
+        return (X1 * w1[:, None]).T @ (X1 @ U) / X1.shape[0] - tr2 * B3U - 2.0 * Bq(X2, B3U)
+
+    def Bmv(U):
+        U = np.asarray(U, dtype=np.float64)
+        return Bq(X4, U) + eps_B * U
+
+    return Amv, Bmv
 
 
 def matrix_ops(A: np.ndarray, B: np.ndarray):

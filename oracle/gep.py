@@ -196,6 +196,28 @@ def lda_population_AB(model):
     return A, L @ L.T
 
 
+def form_ica_AB(X: np.ndarray):
+    """ICA pencil of a finite set (Sec. 1, ICA): B = mean x x^T and
+    A = mean <x, x> x x^T - tr(B) B - 2 B^2 (excess kurtosis matrix)."""
+    X = np.asarray(X, dtype=np.float64)
+    n = X.shape[0]
+    B = X.T @ X / n
+    w = np.einsum("rd,rd->r", X, X)
+    A = (X * w[:, None]).T @ X / n - np.trace(B) * B - 2.0 * B @ B
+    return 0.5 * (A + A.T), B
+
+
+def ica_population_AB(model):
+    """Population ICA pencil of x = M s with independent unit-variance sources of excess
+    kurtosis kappa_j: B = M M^T, and the contraction of the fourth cumulant of x over one pair
+    of indices gives A = M diag(kappa_j |m_j|^2) M^T, so the generalized eigenvectors are the
+    rows of M^-1 with eigenvalues kappa_j |m_j|^2."""
+    M = np.asarray(model["M"], dtype=np.float64)
+    kap = np.asarray(model["kurtosis"], dtype=np.float64)
+    A = (M * (kap * np.sum(M * M, axis=0))[None, :]) @ M.T
+    return 0.5 * (A + A.T), M @ M.T
+
+
 def cca_population_AB(model):
     """Population A and B of a planted CCA model (x = W_x z + noise, y = W_y z + noise)."""
     if hasattr(model, "sigma"):

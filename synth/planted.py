@@ -165,6 +165,45 @@ def draw_lda_rows(model, n: int, batch: int, dtype=np.float64):
     return X.astype(dtype), labels
 
 
+# Source laws of the ICA model: unit variance, known excess kurtosis E[s^4] - 3.
+#   "rademacher": +-1 (kurtosis -2); "uniform": U[-sqrt 3, sqrt 3] (-1.2); "laplace": Laplace
+#   with scale 1/sqrt 2 (3); "sparse": 0 w.p. 3/4, +-2 w.p. 1/8 each (1); "gauss": N(0, 1) (0).
+ICA_KURTOSIS = {"rademacher": -2.0, "uniform": -1.2, "laplace": 3.0, "sparse": 1.0, "gauss": 0.0}
+
+
+def planted_ica(d: int, laws, seed: int = 0, cond: float = 3.0):
+    """Linear mixture x = M s of d independent unit-variance sources with the given laws
+    (stand-in for the mixed signals of the ICA experiment); M has singular values from 1 to
+    `cond` between random rotations."""
+    rng = _rng(seed, _STREAM_MODEL)
+    laws = list(laws)
+    assert len(laws) == d
+    U = _orthonormal(rng, d, d)
+    W = _orthonormal(rng, d, d)
+    M = (U * np.linspace(1.0, cond, d)[None, :]) @ W.T
+    return {"M": M, "laws": laws, "kurtosis": np.array([ICA_KURTOSIS[l] for l in laws]), "seed": seed}
+
+
+def _source(rng, law: str, n: int) -> np.ndarray:
+    if law == "rademacher":
+        return rng.choice([-1.0, 1.0], size=n)
+    if law == "uniform":
+        return rng.uniform(-np.sqrt(3.0), np.sqrt(3.0), size=n)
+    if law == "laplace":
+        return rng.laplace(0.0, 1.0 / np.sqrt(2.0), size=n)
+    if law == "sparse":
+        u = rng.uniform(size=n)
+        return np.where(u < 0.125, -2.0, np.where(u < 0.25, 2.0, 0.0))
+    return rng.standard_normal(n)
+
+
+def draw_ica_rows(model, n: int, batch: int, dtype=np.float64):
+    """Rows x = M s of minibatch number `batch`."""
+    rng = _rng(model["seed"], _STREAM_ROWS_BASE + batch)
+    Ssrc = np.stack([_source(rng, law, n) for law in model["laws"]], axis=1)
+    return (Ssrc @ model["M"].T).astype(dtype)
+
+
 def random_unit_columns(d: int, k: int, seed: int = 0, dtype=np.float64) -> np.ndarray:
     """Initial strategies: v_i ~ N(0, I_d) then scaled to unit norm (Alg. 2 init)."""
     V = _rng(seed, _STREAM_INIT).standard_normal((d, k))
