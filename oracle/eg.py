@@ -233,11 +233,11 @@ def eg_step(V: np.ndarray, S: np.ndarray, Amv, Bmv, eta: float, gamma: float,
         rewards = vBv * Avi - vAv * Bvi
         penalties = np.zeros(d)
         for j in range(i):
-            denom = np.sqrt(max(V[:, j] @ S[:, j], rho))
-            yj = V[:, j] / denom
+            denom = np.sqrt(max(V[:, j] @ S[:, j], rho))  # y_j = v_j / denom
             Byj = S[:, j] / denom
-            # v_i^T A_t y_j, using the symmetry of A_t: (A_t v_i)^T y_j
-            vAy = Avi @ yj
+            # v_i^T A_t y_j as Alg. 2 writes it (A_t y_j = A_t v_j / denom); an estimate A_t
+            # need not be symmetric (ICA's products of independent quarters are not)
+            vAy = vi @ AV[:, j] / denom
             penalties += vAy * (vBv * Byj - (vi @ Byj) * Bvi)
         grad[:, i] = rewards - penalties
     Vp = V + eta * grad
@@ -288,9 +288,8 @@ def eg_step_variant(V: np.ndarray, S: np.ndarray, Amv, Bmv, eta: float, gamma: f
         rewards = vBv * Avi - vAv * Bvi
         penalties = np.zeros(d)
         for j in range(i):
-            yj = V[:, j] / np.sqrt(den[j])
             Byj = S[:, j] / np.sqrt(den[j])
-            penalties += (Avi @ yj) * (vBv * Byj - (vi @ Byj) * Bvi)
+            penalties += (vi @ AV[:, j] / np.sqrt(den[j])) * (vBv * Byj - (vi @ Byj) * Bvi)
         grad[:, i] = rewards - penalties
     state = {}
     if adam is not None:
