@@ -58,6 +58,13 @@ extern "C" {
 #define SGEP_CCA 1  /* A = [[0, E xy^T], [E yx^T, 0]], B = blockdiag(E xx^T, E yy^T) */
 #define SGEP_PLS 2  /* A as CCA, B = I (reading of Sec. 1, which gives no formula) */
 #define SGEP_LDA 3  /* between-class A from running class means, within-class B  */
+#define SGEP_ICA 4  /* A = E[<x,x> x x^T] - tr(B) B - 2 B^2, B = E[x x^T] (excess kurtosis) */
+/* ICA (Sec. 1): d_y = 0, generic path. Reading of "independent data batches": with
+ * split_AB = 1 the rows form four quarters (the last takes the remainder, b >= 4): the
+ * kurtosis term of A_t from the first, tr(B) and the outer B of B^2 from the second, the
+ * inner B from the third, B_t from the fourth, so every product pairs independent rows.
+ * With split_AB = 0 every term uses every row. sgep_get_eigenvalues takes at most max_b
+ * rows for ICA (A is not a sum over rows); sgep_rayleigh_ritz does not take ICA. */
 /* LDA (Sec. 1 names it without estimators; reading): the handle keeps the exact
  * running class sums and counts of every row seen (FP64); a step first adds all
  * of its rows, then uses A = sum_c pi_c (mu_c - mu)(mu_c - mu)^T (pi_c = n_c / n,

@@ -137,6 +137,94 @@ int launch_backproject(Ctx& c, const T* X, const T* Y, int64_t b, cudaStream_t s
   return SGEP_OK;
 }
 
+// ---- ICA helpers ----
+// w[r] = ||x_r||^2 for r < n (one warp per row; FP8 rows times their scale).
+template <typename T>
+__global__ void k_row_sqnorm(const T* __restrict__ X, int64_t n, int64_t d, const float* __restrict__ rs,
+                             float* __restrict__ w) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n; r += nw) {
+    float s = 0.f;
+    for (int64_t c = lane; c < d; c += 32) {
+      const float x = gt::load_row_elem(X, rs, r, r * d + c);
+      s = fmaf(x, x, s);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) w[r] = s;
+  }
+}
+
+// PW[r, i] = w[r] PQ[r, i] for r < n, i < k (both with row stride 2k).
+__global__ void k_weight_rows(const float* __restrict__ PQ, const float* __restrict__ w, int64_t n, int k,
+                              float* __restrict__ PW) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * k; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / k;
+    const int i = (int)(e % k);
+    PW[r * 2 * k + i] = w[r] * PQ[r * 2 * k + i];
+  }
+}
+
+// out[0] = sum_{r < n} w[r] / n (one block, double accumulation).
+__global__ void k_mean(const float* __restrict__ w, int64_t n, float* __restrict__ out) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int64_t r = threadIdx.x; r < n; r += blockDim.x) s += w[r];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = (float)(red[0] / (double)n);
+}
+
+// A_t V = K - tr U - 2 W (kurtosis term, tr(B_2) B_3 V, B_2 B_3 V).
+__global__ void k_ica_combine(float* __restrict__ AV, const float* __restrict__ U, const float* __restrict__ W,
+                              const float* __restrict__ tr, int64_t n) {
+  const float t = tr[0];
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    AV[e] = AV[e] - t * U[e] - 2.f * W[e];
+}
+
+// out (n x 2k, first k columns used) = X M over n rows of one view, M d_x x k.
+template <typename T>
+int launch_project_with(Ctx& c, const T* X, int64_t n, const float* M, float* out, cudaStream_t s, const float* sx) {
+  SGEP_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(float) * n * 2 * c.k, s));
+  const int64_t row_tiles = (n + 31) / 32;
+  int64_t chunk = 1024;
+  while (chunk > 64 && row_tiles * ((c.d_x + chunk - 1) / chunk) < 2LL * c.num_sms) chunk /= 2;
+  const int nchunk_x = (int)((c.d_x + chunk - 1) / chunk);
+  const Centring none{nullptr, nullptr, 0, c.dflag};
+  dim3 grid((unsigned)row_tiles, (unsigned)nchunk_x);
+  k_project<T><<<grid, kThreads, gt::kProjectSmem * sizeof(float), s>>>(X, nullptr, n, c.d_x, 0, M, c.k, chunk,
+                                                                          nchunk_x, out, none, sx, nullptr);
+  SGEP_CUDA_TRY(cudaGetLastError());
+  ++c.launches;
+  return SGEP_OK;
+}
+
+// out (d_x x k) += scale X^T P over n rows of one view (P with row stride 2k).
+template <typename T>
+int launch_bp_rows(Ctx& c, const T* X, int64_t n, const float* P, float* out, float scale, cudaStream_t s,
+                   const float* sx) {
+  const int nblk = (int)((c.d_x + 63) / 64);
+  int splits = (int)((2LL * c.num_sms + nblk - 1) / nblk);
+  splits = (int)std::max<int64_t>(1, std::min<int64_t>(splits, (n + 31) / 32));
+  int64_t rows_per_split = (n + splits - 1) / splits;
+  rows_per_split = ((rows_per_split + 31) / 32) * 32;
+  splits = (int)((n + rows_per_split - 1) / rows_per_split);
+  const Centring none{nullptr, nullptr, 0, c.dflag};
+  dim3 grid((unsigned)nblk, (unsigned)splits);
+  k_backproject<T><<<grid, kThreads, gt::kBackprojectSmem * sizeof(float), s>>>(
+      X, nullptr, n, c.d_x, 0, n, SGEP_PCA, 0, P, c.k, nblk, rows_per_split, scale, scale, out, nullptr, none, sx,
+      nullptr);
+  SGEP_CUDA_TRY(cudaGetLastError());
+  ++c.launches;
+  return SGEP_OK;
+}
+
 }  // namespace
 
 // Dispatch on the handle's element type.
@@ -222,6 +310,64 @@ int generic_rayleigh_sums(Ctx& c, int64_t n, cudaStream_t s) {
   SGEP_CUDA_TRY(cudaGetLastError());
   ++c.launches;
   return SGEP_OK;
+}
+
+}  // namespace sgep
+
+namespace sgep {
+
+int ica_alloc(Ctx& c) {
+  const size_t mb = (size_t)c.cfg.max_b, dk = (size_t)c.d * c.k;
+  SGEP_CUDA_TRY(cudaMalloc((void**)&c.ica_buf, (mb + 2 * mb * c.k + 2 * dk + 4) * sizeof(float)));
+  return SGEP_OK;
+}
+
+// A_t V and B_t V of the ICA pencil (Sec. 1) from b rows: P = X V over every row, row norms
+// w, the kurtosis term X_1^T (w . P_1) / n_1, U = B_3 V, tr = mean_2 w, W = B_2 U,
+// A_t V = K - tr U - 2 W, B_t V = B_4 V. Quarters 1..4 of the rows when `split`, else all rows.
+int ica_products(Ctx& c, const void* X, int64_t b, cudaStream_t s, const float* sx, bool split) {
+  const int k = c.k;
+  const size_t dk = (size_t)c.d * k, mb = (size_t)c.cfg.max_b;
+  float* w = c.ica_buf;
+  float* PW = w + mb;
+  float* U = PW + 2 * mb * k;
+  float* W = U + dk;
+  float* tr = W + dk;
+  float* AV = c.acc;
+  float* BV = c.acc + dk;
+  const int64_t q = split ? b / 4 : b;
+  const int64_t lo[4] = {0, split ? q : 0, split ? 2 * q : 0, split ? 3 * q : 0};
+  const int64_t nr[4] = {q, q, q, split ? b - 3 * q : b};
+  SGEP_CUDA_TRY(cudaMemsetAsync(c.acc, 0, 2 * dk * sizeof(float), s));
+  SGEP_CUDA_TRY(cudaMemsetAsync(U, 0, 2 * dk * sizeof(float), s));
+  return by_dtype(c, [&](auto tag) {
+    using T = std::remove_const_t<std::remove_pointer_t<decltype(tag)>>;
+    const T* Xt = static_cast<const T*>(X);
+    auto rows = [&](int j) { return Xt + lo[j] * c.d_x; };
+    auto rsc = [&](int j) { return sx ? sx + lo[j] : (const float*)nullptr; };
+    int rc = launch_project_with<T>(c, Xt, b, c.V, c.PQ, s, sx);
+    if (rc) return rc;
+    const int64_t nw = split ? 2 * q : b;  // rows of the first two quarters
+    k_row_sqnorm<T><<<(unsigned)std::min<int64_t>((nw + 7) / 8, 4 * c.num_sms), 256, 0, s>>>(Xt, nw, c.d_x, sx, w);
+    SGEP_CUDA_TRY(cudaGetLastError());
+    k_mean<<<1, 256, 0, s>>>(w + lo[1], nr[1], tr);
+    SGEP_CUDA_TRY(cudaGetLastError());
+    k_weight_rows<<<(unsigned)std::min<int64_t>((nr[0] * k + 255) / 256, 4 * c.num_sms), 256, 0, s>>>(
+        c.PQ + lo[0] * 2 * k, w + lo[0], nr[0], k, PW);
+    SGEP_CUDA_TRY(cudaGetLastError());
+    c.launches += 3;
+    rc = launch_bp_rows<T>(c, rows(0), nr[0], PW, AV, 1.f / (float)nr[0], s, rsc(0));
+    if (!rc) rc = launch_bp_rows<T>(c, rows(2), nr[2], c.PQ + lo[2] * 2 * k, U, 1.f / (float)nr[2], s, rsc(2));
+    if (!rc) rc = launch_bp_rows<T>(c, rows(3), nr[3], c.PQ + lo[3] * 2 * k, BV, 1.f / (float)nr[3], s, rsc(3));
+    if (!rc) rc = launch_project_with<T>(c, rows(1), nr[1], U, PW, s, rsc(1));
+    if (!rc) rc = launch_bp_rows<T>(c, rows(1), nr[1], PW, W, 1.f / (float)nr[1], s, rsc(1));
+    if (rc) return rc;
+    k_ica_combine<<<(unsigned)std::min<int64_t>(((int64_t)dk + 255) / 256, 4 * c.num_sms), 256, 0, s>>>(AV, U, W,
+                                                                                                       tr, dk);
+    SGEP_CUDA_TRY(cudaGetLastError());
+    ++c.launches;
+    return SGEP_OK;
+  });
 }
 
 }  // namespace sgep

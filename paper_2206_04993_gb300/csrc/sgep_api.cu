@@ -97,6 +97,7 @@ static void free_ctx(sgep_ctx* c) {
   cudaFree(c->dflag);
   cudaFree(c->adam_m);
   cudaFree(c->z);
+  cudaFree(c->ica_buf);
   delete c;
 }
 
@@ -193,15 +194,15 @@ int sgep_init(const sgep_config* cfg, sgep_t* out) {
   *out = nullptr;
   if (!cfg) return fail(SGEP_EINVAL, "cfg is NULL");
   const sgep_config& g = *cfg;
-  if (g.kind != SGEP_PCA && g.kind != SGEP_CCA && g.kind != SGEP_PLS && g.kind != SGEP_LDA)
+  if (g.kind != SGEP_PCA && g.kind != SGEP_CCA && g.kind != SGEP_PLS && g.kind != SGEP_LDA && g.kind != SGEP_ICA)
     return fail(SGEP_EINVAL, "unknown kind");
   if (g.kind == SGEP_LDA && (g.n_classes < 2 || g.n_classes > kMaxClasses))
     return fail(SGEP_EINVAL, "LDA needs 2 <= n_classes <= 32");
   if (g.dtype != SGEP_F32 && g.dtype != SGEP_BF16 && g.dtype != SGEP_FP8E4M3)
     return fail(SGEP_EINVAL, "unknown dtype");
   if (g.d_x < 1) return fail(SGEP_EINVAL, "d_x must be >= 1");
-  const bool one_view = g.kind == SGEP_PCA || g.kind == SGEP_LDA;
-  if (one_view && g.d_y != 0) return fail(SGEP_EINVAL, "PCA and LDA require d_y = 0");
+  const bool one_view = g.kind == SGEP_PCA || g.kind == SGEP_LDA || g.kind == SGEP_ICA;
+  if (one_view && g.d_y != 0) return fail(SGEP_EINVAL, "PCA, LDA and ICA require d_y = 0");
   if (!one_view && g.d_y < 1) return fail(SGEP_EINVAL, "CCA/PLS require d_y >= 1");
   const int64_t d = g.d_x + g.d_y;
   if (g.k < 1 || g.k > 64 || g.k > d) return fail(SGEP_EINVAL, "k must satisfy 1 <= k <= min(64, d)");
@@ -232,7 +233,7 @@ int sgep_init(const sgep_config* cfg, sgep_t* out) {
   c->d = d;
   c->k = g.k;
   c->b_is_identity = (g.kind == SGEP_PCA || g.kind == SGEP_PLS);
-  c->has_y = (g.kind != SGEP_PCA && g.kind != SGEP_LDA);
+  c->has_y = !one_view;
   cudaError_t e = cudaGetDevice(&c->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
   if (e != cudaSuccess) {
@@ -291,13 +292,19 @@ int sgep_init(const sgep_config* cfg, sgep_t* out) {
   // Path selection.
   const char* why = nullptr;
   const bool cl_ok = cluster_supported(*c, &why);
-  const bool generic_only = g.kind == SGEP_LDA || g.dtype == SGEP_FP8E4M3;
+  const bool generic_only = g.kind == SGEP_LDA || g.kind == SGEP_ICA || g.dtype == SGEP_FP8E4M3;
   if (generic_only && g.path != SGEP_PATH_AUTO && g.path != SGEP_PATH_GENERIC) {
     free_ctx(c);
-    return fail(SGEP_ENOTSUP, "LDA and FP8 rows run on the generic path only");
+    return fail(SGEP_ENOTSUP, "LDA, ICA and FP8 rows run on the generic path only");
   }
   if (generic_only) c->path = SGEP_PATH_GENERIC;
-  if (g.kind == SGEP_LDA) {
+  if (g.kind == SGEP_ICA) {
+    int rc = ica_alloc(*c);
+    if (rc) {
+      free_ctx(c);
+      return rc;
+    }
+  } else if (g.kind == SGEP_LDA) {
     int rc = lda_alloc(*c);
     if (rc) {
       free_ctx(c);
@@ -382,8 +389,9 @@ static int step_checks(Ctx& c, const void* X, const void* Y, const float* sx, co
   if (c.has_y && !Y) return fail(SGEP_EINVAL, "Y is NULL");
   if (int rc = scale_checks(c, sx, sy)) return rc;
   if (c.cfg.kind == SGEP_LDA && !labels) return fail(SGEP_EINVAL, "LDA needs labels");
-  const bool split = (c.cfg.kind == SGEP_CCA || c.cfg.kind == SGEP_LDA) && c.cfg.split_AB;
-  if (b < (split ? 2 : 1)) return fail(SGEP_EINVAL, "b too small (split batches need b >= 2)");
+  const bool split = (c.cfg.kind == SGEP_CCA || c.cfg.kind == SGEP_LDA || c.cfg.kind == SGEP_ICA) && c.cfg.split_AB;
+  const int64_t bmin = split ? (c.cfg.kind == SGEP_ICA ? 4 : 2) : 1;
+  if (b < bmin) return fail(SGEP_EINVAL, "b too small (split batches need b >= 2, ICA quarters b >= 4)");
   if (b > c.cfg.max_b) return fail(SGEP_EINVAL, "b exceeds max_b");
   return SGEP_OK;
 }
@@ -402,7 +410,9 @@ static int do_step(Ctx& c, const void* X, const void* Y, const float* sx, const 
       if (!rc && c.tc_generic_step) c.tc_chain = 0;
       if (!rc) rc = c.tc_generic_step ? generic_update(c, eta, gamma, s) : tc_update(c, eta, gamma, s);
     } else {
-      rc = c.cfg.kind == SGEP_LDA ? lda_products(c, X, labels, b, s, sx) : generic_products(c, X, Y, b, s, sx, sy);
+      if (c.cfg.kind == SGEP_LDA) rc = lda_products(c, X, labels, b, s, sx);
+      else if (c.cfg.kind == SGEP_ICA) rc = ica_products(c, X, b, s, sx, c.cfg.split_AB != 0);
+      else rc = generic_products(c, X, Y, b, s, sx, sy);
       if (!rc) rc = generic_update(c, eta, gamma, s);
     }
     if (!rc) c.debug_valid = c.cfg.debug;
@@ -510,6 +520,30 @@ int sgep_get_eigenvalues(sgep_t h, const void* X, const void* Y, const float* ro
   int rc = complete(c, s);
   if (rc) return rc;
   const int k = c.k;
+  if (c.cfg.kind == SGEP_ICA) {
+    // A is not a sum over rows: the n rows form one unsplit estimate; v_i^T A v_i / v_i^T B v_i
+    if (n > c.cfg.max_b) return fail(SGEP_EINVAL, "ICA eigenvalues take at most max_b rows");
+    rc = ica_products(c, X, n, s, row_scale_x, false);
+    if (rc) return rc;
+    const size_t dk = (size_t)c.d * k;
+    std::vector<float> V(dk), AV(dk), BV(dk);
+    SGEP_CUDA_TRY(cudaMemcpyAsync(V.data(), c.V, dk * sizeof(float), cudaMemcpyDeviceToHost, s));
+    SGEP_CUDA_TRY(cudaMemcpyAsync(AV.data(), c.acc, dk * sizeof(float), cudaMemcpyDeviceToHost, s));
+    SGEP_CUDA_TRY(cudaMemcpyAsync(BV.data(), c.acc + dk, dk * sizeof(float), cudaMemcpyDeviceToHost, s));
+    SGEP_CUDA_TRY(cudaStreamSynchronize(s));
+    rc = check_flag(c);
+    if (rc) return rc;
+    for (int i = 0; i < k; ++i) {
+      double num = 0.0, den = 0.0;
+      for (int64_t r = 0; r < c.d; ++r) {
+        num += (double)V[r * k + i] * AV[r * k + i];
+        den += (double)V[r * k + i] * BV[r * k + i];
+      }
+      out_k[i] = num / den;
+    }
+    c.debug_valid = 0;
+    return SGEP_OK;
+  }
   SGEP_CUDA_TRY(cudaMemsetAsync(c.rq, 0, sizeof(double) * 2 * k, s));
   const size_t esz = elem_size(c);
   for (int64_t r0 = 0; r0 < n; r0 += c.cfg.max_b) {
@@ -583,6 +617,7 @@ int sgep_rayleigh_ritz(sgep_t h, const void* X, const void* Y, const float* row_
   Ctx& c = *h;
   if (!X || (c.has_y && !Y)) return fail(SGEP_EINVAL, "NULL argument");
   if (c.cfg.kind == SGEP_LDA && !labels) return fail(SGEP_EINVAL, "LDA needs labels");
+  if (c.cfg.kind == SGEP_ICA) return fail(SGEP_ENOTSUP, "the Rayleigh-Ritz correction does not take ICA");
   if (n < 1) return fail(SGEP_EINVAL, "n must be >= 1");
   if (int e = scale_checks(c, row_scale_x, row_scale_y)) return e;
   cudaStream_t s = (cudaStream_t)stream;

@@ -19,7 +19,7 @@ HEADER = os.path.join(os.path.dirname(_PKG), "include", "sgep.h")
 
 SGEP_OK, SGEP_EINVAL, SGEP_ENOMEM, SGEP_ECUDA = 0, -1, -2, -3
 SGEP_ETIMEOUT, SGEP_ENONFINITE, SGEP_ELAUNCH, SGEP_ESTATE, SGEP_ENOTSUP = -4, -5, -6, -7, -8
-SGEP_PCA, SGEP_CCA, SGEP_PLS, SGEP_LDA = 0, 1, 2, 3
+SGEP_PCA, SGEP_CCA, SGEP_PLS, SGEP_LDA, SGEP_ICA = 0, 1, 2, 3, 4
 SGEP_F32, SGEP_BF16, SGEP_FP8E4M3 = 0, 1, 2
 SGEP_SCHED_CONST, SGEP_SCHED_HOLD_HARMONIC, SGEP_SCHED_WARMUP_HARMONIC = 0, 1, 2
 SGEP_PATH_AUTO, SGEP_PATH_GENERIC, SGEP_PATH_CLUSTER, SGEP_PATH_TC = 0, 1, 2, 3
