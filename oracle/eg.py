@@ -144,6 +144,16 @@ def lda_stats_update(sums: np.ndarray, counts: np.ndarray, X: np.ndarray, labels
     return sums, counts
 
 
+def running_mean_update(sums: np.ndarray, count: float, Z: np.ndarray):
+    """Exact running mean of every row seen ("mean estimates are learned", App. H.2.2; the
+    methods assume zero-mean data, Sec. 1). Reading: a step first adds every row of its
+    minibatch (both halves), then centres those rows by the updated mean. Returns
+    (sums, count, mean)."""
+    sums = np.asarray(sums, dtype=np.float64) + np.asarray(Z, dtype=np.float64).sum(axis=0)
+    count = float(count) + Z.shape[0]
+    return sums, count, sums / count
+
+
 def lda_state(sums: np.ndarray, counts: np.ndarray):
     """Class means mu_c = sums_c / n_c (0 for a class not seen yet) and priors pi_c = n_c / n."""
     counts = np.asarray(counts, dtype=np.float64)

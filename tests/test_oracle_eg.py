@@ -226,3 +226,26 @@ def test_stochastic_cca_small_config_reaches_low_error():
         V, S = eg.eg_step(V, S, *eg.cca_ops(X[idx], Y[idx]), eta, cfg["gamma0"], cfg["rho"])
     err = gep.subspace_error(Vs, V, B)
     assert err < 3e-3, err
+
+
+def test_running_mean_centring_streams_the_exact_mean_and_removes_offsets():
+    """App. H.2.2's learned means: streaming every row of a finite set gives that set's mean,
+    and once a constant offset is absorbed by the running mean, centred rows (and so A_t, B_t)
+    do not depend on it."""
+    model = synth.planted_cca(6, 5, [0.9, 0.6], seed=2)
+    rows = [synth.draw_rows(model, 32, batch=b) for b in range(5)]
+    X = np.concatenate([r[0] for r in rows])
+    sx, n, mx = np.zeros(6), 0.0, None
+    for Xb, _ in rows:
+        sx, n, mx = eg.running_mean_update(sx, n, Xb)
+    np.testing.assert_allclose(mx, X.mean(axis=0), atol=1e-14)
+    off = np.linspace(-3.0, 5.0, 6)
+    s0, s1, n0, n1 = np.zeros(6), np.zeros(6), 0.0, 0.0
+    U = np.random.default_rng(0).standard_normal((11, 3))
+    for Xb, Yb in rows:
+        s0, n0, m0 = eg.running_mean_update(s0, n0, Xb)
+        s1, n1, m1 = eg.running_mean_update(s1, n1, Xb + off)
+        A0, B0 = eg.cca_ops(Xb - m0, Yb)
+        A1, B1 = eg.cca_ops(Xb + off - m1, Yb)
+        np.testing.assert_allclose(A1(U), A0(U), atol=1e-12)
+        np.testing.assert_allclose(B1(U), B0(U), atol=1e-12)
