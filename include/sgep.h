@@ -128,7 +128,10 @@ typedef struct {
                        /* SGEP_ALG3: smooth denominators exp(log rho + (log nu - log rho)       */
                        /* sigmoid(z_j)) with one scalar z_j per player (Alg. 3, App. E.2)       */
   float    nu;         /* Alg. 3: upper bound on lambda_max(B), > rho                           */
-  int32_t  reserved[1];
+  int32_t  center;     /* 1: centre every row by the exact running mean of all rows seen      */
+                       /* (App. H.2.2 "mean estimates are learned"; the pencils of Sec. 1     */
+                       /* assume zero-mean data). PCA, CCA, PLS on the generic path. A step   */
+                       /* adds its rows to the running sums first, then centres them.         */
 } sgep_config;
 
 /* Fill `cfg` with defaults: CCA, F32, k = 1, eta0 = 0.1, gamma0 = 1, rho = 1e-6,

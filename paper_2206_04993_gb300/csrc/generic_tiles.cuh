@@ -45,15 +45,19 @@ __device__ __forceinline__ float load_row_elem(const T* p, const float* scale, i
 
 // Class-mean centring of LDA rows: x - mu_{label}. A label outside [0, C) is
 // flagged and the row is left uncentred (the step then reports the bad label).
+// Running-mean centring (labels null): x - mean[col] for X rows, x - mean_y[col] for Y rows.
 struct Centring {
   const float* mean;      // C x ld class means, or null (no centring)
-  const int32_t* labels;  // labels of the rows passed to the kernel
+  const int32_t* labels;  // labels of the rows passed to the kernel, or null (running means)
   int C;
   int* dflag;
+  const float* mean_y = nullptr;  // running mean of the Y view
 };
 
-__device__ __forceinline__ float centred(const Centring& cz, float x, int64_t row, int64_t ld, int64_t col) {
+__device__ __forceinline__ float centred(const Centring& cz, float x, int64_t row, int64_t ld, int64_t col,
+                                         bool isY = false) {
   if (!cz.mean) return x;
+  if (!cz.labels) return x - (isY ? cz.mean_y : cz.mean)[col];
   const int lab = cz.labels[row];
   if ((unsigned)lab >= (unsigned)cz.C) {
     atomicOr(cz.dflag, kFlagBadLabel);
@@ -95,7 +99,8 @@ __device__ void project_tile(const T* __restrict__ X, const T* __restrict__ Y, i
       const int rr = e / TC, cc = e % TC;
       const int64_t row = row0 + rr, col = c0 + cc;
       Xs[rr][cc] =
-          (row < n && col < c_end) ? centred(cz, load_row_elem(Z, rs, row, row * ld + col), row, ld, col) : 0.f;
+          (row < n && col < c_end) ? centred(cz, load_row_elem(Z, rs, row, row * ld + col), row, ld, col, isY)
+                                   : 0.f;
     }
     for (int e = tid; e < TC * k; e += kThreads) {
       const int cc = e / k, i = e % k;
@@ -167,7 +172,8 @@ __device__ void backproject_tile(const T* __restrict__ X, const T* __restrict__ 
       const int rr = e / CB, cc = e % CB;
       const int64_t row = r0 + rr, cg = (int64_t)bidx * CB + cc;
       Zs[rr][cc] =
-          (row < r_end && cg < ld) ? centred(cz, load_row_elem(Z, rs, row, row * ld + cg), row, ld, cg) : 0.f;
+          (row < r_end && cg < ld) ? centred(cz, load_row_elem(Z, rs, row, row * ld + cg), row, ld, cg, isY)
+                                   : 0.f;
     }
     for (int e = tid; e < TR * 2 * k; e += kThreads) {
       const int rr = e / (2 * k), j = e % (2 * k);

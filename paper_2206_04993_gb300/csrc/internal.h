@@ -48,6 +48,9 @@ struct Ctx {
   int64_t adam_t = 0;      // Adam steps since the moments were last reset
   float* z = nullptr;      // Alg. 3: k scalars z_i
   float* ica_buf = nullptr;  // ICA: row norms (max_b) | weighted projections (max_b x 2k) | U, W (d x k each) | tr
+  double* cen_sum = nullptr; // running-mean centring: column sums of every row seen (X then Y, d)
+  float* cen_mean = nullptr; // their means (d)
+  double cen_count = 0.0;    // rows seen
 
   // cluster path: ping-pong state buffers and three accumulator slots
   float* cl_V[2] = {nullptr, nullptr};
@@ -159,6 +162,9 @@ int generic_update(Ctx& c, float eta, float gamma, cudaStream_t s);
 int generic_project(Ctx& c, const void* X, const void* Y, int64_t n, cudaStream_t s,
                     const float* center = nullptr, const int32_t* labels = nullptr, const float* sx = nullptr,
                     const float* sy = nullptr);
+// Running-mean centring (kernels_generic.cu): adds b rows to the running sums, refreshes the means.
+int centring_update(Ctx& c, const void* X, const void* Y, int64_t b, cudaStream_t s, const float* sx,
+                    const float* sy);
 // ICA (kernels_generic.cu): acc <- [A_t V ; B_t V] of b rows, quarters when `split`.
 int ica_alloc(Ctx& c);
 int ica_products(Ctx& c, const void* X, int64_t b, cudaStream_t s, const float* sx, bool split);

@@ -662,8 +662,8 @@ int sgep_batch_create(const sgep_t* handles, int n, sgep_batch_t* out) {
     if (hs[i]->path != SGEP_PATH_GENERIC)
       return batch_fail(SGEP_EINVAL, "batched instances must be created with path = SGEP_PATH_GENERIC");
     if (hs[i]->cfg.kind == SGEP_ICA) return batch_fail(SGEP_ENOTSUP, "batched instances cannot be ICA");
-    if (hs[i]->adam_m || hs[i]->z)
-      return batch_fail(SGEP_ENOTSUP, "batched instances take Alg. 2's plain step (no Adam, no Alg. 3)");
+    if (hs[i]->adam_m || hs[i]->z || hs[i]->cen_sum)
+      return batch_fail(SGEP_ENOTSUP, "batched instances take Alg. 2's plain step (no Adam, Alg. 3 or centring)");
     if (hs[i]->device != hs[0]->device) return batch_fail(SGEP_EINVAL, "instances on different devices");
     for (int j = 0; j < i; ++j)
       if (hs[j] == hs[i]) return batch_fail(SGEP_EINVAL, "a handle appears twice");

@@ -137,6 +137,26 @@ int launch_backproject(Ctx& c, const T* X, const T* Y, int64_t b, cudaStream_t s
   return SGEP_OK;
 }
 
+// ---- running-mean centring ----
+// sums[c] += sum_{r < n} x_rc (FP64) for the ld columns of one view; 256 columns per block,
+// rows split over gridDim.y.
+template <typename T>
+__global__ void k_colsum(const T* __restrict__ Z, int64_t n, int64_t ld, const float* __restrict__ rs,
+                         double* __restrict__ sums) {
+  const int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= ld) return;
+  const int64_t per = (n + gridDim.y - 1) / gridDim.y;
+  const int64_t r0 = (int64_t)blockIdx.y * per, r1 = min(n, r0 + per);
+  double acc = 0.0;
+  for (int64_t r = r0; r < r1; ++r) acc += (double)gt::load_row_elem(Z, rs, r, r * ld + col);
+  atomicAdd(&sums[col], acc);
+}
+
+__global__ void k_mean_from_sums(const double* __restrict__ sums, int64_t d, double count, float* __restrict__ mean) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < d; e += (int64_t)gridDim.x * blockDim.x)
+    mean[e] = count > 0.0 ? (float)(sums[e] / count) : 0.f;
+}
+
 // ---- ICA helpers ----
 // w[r] = ||x_r||^2 for r < n (one warp per row; FP8 rows times their scale).
 template <typename T>
@@ -235,10 +255,18 @@ int by_dtype(const Ctx& c, F&& f) {
   return f(static_cast<const float*>(nullptr));
 }
 
+// Rows centred by class means (center, labels), else by the running means of a centring
+// handle, else not centred.
+static Centring centring_of(const Ctx& c, const float* center, const int32_t* labels) {
+  if (center) return Centring{center, labels, c.cfg.n_classes, c.dflag};
+  if (c.cen_mean) return Centring{c.cen_mean, nullptr, 1, c.dflag, c.cen_mean + c.d_x};
+  return Centring{nullptr, nullptr, 0, c.dflag};
+}
+
 int generic_project(Ctx& c, const void* X, const void* Y, int64_t n, cudaStream_t s, const float* center,
                     const int32_t* labels, const float* sx, const float* sy) {
   SGEP_CUDA_TRY(cudaMemsetAsync(c.PQ, 0, sizeof(float) * n * 2 * c.k, s));
-  const Centring cz{center, labels, c.cfg.n_classes, c.dflag};
+  const Centring cz = centring_of(c, center, labels);
   return by_dtype(c, [&](auto tag) {
     using T = std::remove_const_t<std::remove_pointer_t<decltype(tag)>>;
     return launch_project<T>(c, (const T*)X, (const T*)Y, n, s, cz, sx, sy);
@@ -261,10 +289,10 @@ int generic_products(Ctx& c, const void* X, const void* Y, int64_t b, cudaStream
   int rc = generic_project(c, X, Y, b, s, nullptr, nullptr, sx, sy);
   if (rc) return rc;
   SGEP_CUDA_TRY(cudaMemsetAsync(c.acc, 0, sizeof(float) * 2 * c.d * c.k, s));
-  const Centring none{nullptr, nullptr, 0, c.dflag};
+  const Centring cz = centring_of(c, nullptr, nullptr);
   return by_dtype(c, [&](auto tag) {
     using T = std::remove_const_t<std::remove_pointer_t<decltype(tag)>>;
-    return launch_backproject<T>(c, (const T*)X, (const T*)Y, b, s, none, sx, sy);
+    return launch_backproject<T>(c, (const T*)X, (const T*)Y, b, s, cz, sx, sy);
   });
 }
 
@@ -368,6 +396,33 @@ int ica_products(Ctx& c, const void* X, int64_t b, cudaStream_t s, const float* 
     ++c.launches;
     return SGEP_OK;
   });
+}
+
+}  // namespace sgep
+
+namespace sgep {
+
+int centring_update(Ctx& c, const void* X, const void* Y, int64_t b, cudaStream_t s, const float* sx,
+                    const float* sy) {
+  const unsigned ysplit = (unsigned)std::max<int64_t>(1, std::min<int64_t>(64, (b + 255) / 256));
+  int rc = by_dtype(c, [&](auto tag) {
+    using T = std::remove_const_t<std::remove_pointer_t<decltype(tag)>>;
+    k_colsum<T><<<dim3((unsigned)((c.d_x + 255) / 256), ysplit), 256, 0, s>>>((const T*)X, b, c.d_x, sx, c.cen_sum);
+    SGEP_CUDA_TRY(cudaGetLastError());
+    if (c.has_y) {
+      k_colsum<T><<<dim3((unsigned)((c.d_y + 255) / 256), ysplit), 256, 0, s>>>((const T*)Y, b, c.d_y, sy,
+                                                                               c.cen_sum + c.d_x);
+      SGEP_CUDA_TRY(cudaGetLastError());
+    }
+    return SGEP_OK;
+  });
+  if (rc) return rc;
+  c.cen_count += (double)b;
+  k_mean_from_sums<<<(unsigned)std::min<int64_t>((c.d + 255) / 256, 4 * c.num_sms), 256, 0, s>>>(
+      c.cen_sum, c.d, c.cen_count, c.cen_mean);
+  SGEP_CUDA_TRY(cudaGetLastError());
+  c.launches += c.has_y ? 3 : 2;
+  return SGEP_OK;
 }
 
 }  // namespace sgep

@@ -96,8 +96,8 @@ extern "C" int sgep_step_noalloc(const sgep_config* cfg, const void* X, const vo
     return bad(("shape needs " + std::to_string(need) + " bytes of scratch, more than the fixed " +
                 std::to_string((size_t)SGEP_NOALLOC_SCRATCH_BYTES) + " (reduce b, d or k)").c_str());
 
-  if (g.optimizer != SGEP_OPT_SGD || g.variant != SGEP_ALG2)
-    return bad("Adam and Alg. 3 keep state beyond V and [Bv]; use a handle (sgep_step)");
+  if (g.optimizer != SGEP_OPT_SGD || g.variant != SGEP_ALG2 || g.center)
+    return bad("Adam, Alg. 3 and running-mean centring keep state beyond V and [Bv]; use a handle (sgep_step)");
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");

@@ -98,6 +98,8 @@ static void free_ctx(sgep_ctx* c) {
   cudaFree(c->adam_m);
   cudaFree(c->z);
   cudaFree(c->ica_buf);
+  cudaFree(c->cen_sum);
+  cudaFree(c->cen_mean);
   delete c;
 }
 
@@ -224,6 +226,9 @@ int sgep_init(const sgep_config* cfg, sgep_t* out) {
   if (g.variant == SGEP_ALG3 && !(g.nu > g.rho && std::isfinite(g.nu)))
     return fail(SGEP_EINVAL, "Alg. 3 needs a finite nu > rho");
   const bool variants = g.optimizer == SGEP_OPT_ADAM || g.variant == SGEP_ALG3;
+  if (g.center != 0 && g.center != 1) return fail(SGEP_EINVAL, "center must be 0 or 1");
+  if (g.center && g.kind != SGEP_PCA && g.kind != SGEP_CCA && g.kind != SGEP_PLS)
+    return fail(SGEP_EINVAL, "running-mean centring is for PCA, CCA and PLS (LDA centres by class means)");
 
   sgep_ctx* c = new (std::nothrow) sgep_ctx();
   if (!c) return fail(SGEP_ENOMEM, "host allocation failed");
@@ -292,10 +297,20 @@ int sgep_init(const sgep_config* cfg, sgep_t* out) {
   // Path selection.
   const char* why = nullptr;
   const bool cl_ok = cluster_supported(*c, &why);
-  const bool generic_only = g.kind == SGEP_LDA || g.kind == SGEP_ICA || g.dtype == SGEP_FP8E4M3;
+  const bool generic_only = g.kind == SGEP_LDA || g.kind == SGEP_ICA || g.dtype == SGEP_FP8E4M3 || g.center;
   if (generic_only && g.path != SGEP_PATH_AUTO && g.path != SGEP_PATH_GENERIC) {
     free_ctx(c);
-    return fail(SGEP_ENOTSUP, "LDA, ICA and FP8 rows run on the generic path only");
+    return fail(SGEP_ENOTSUP, "LDA, ICA, FP8 rows and running-mean centring run on the generic path only");
+  }
+  if (g.center) {  // running sums and means start at zero
+    e = cudaMalloc((void**)&c->cen_sum, (size_t)d * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemset(c->cen_sum, 0, (size_t)d * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->cen_mean, (size_t)d * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(c->cen_mean, 0, (size_t)d * sizeof(float));
+    if (e != cudaSuccess) {
+      free_ctx(c);
+      return cuda_fail(e, "cudaMalloc (running means)");
+    }
   }
   if (generic_only) c->path = SGEP_PATH_GENERIC;
   if (g.kind == SGEP_ICA) {
@@ -410,9 +425,12 @@ static int do_step(Ctx& c, const void* X, const void* Y, const float* sx, const 
       if (!rc && c.tc_generic_step) c.tc_chain = 0;
       if (!rc) rc = c.tc_generic_step ? generic_update(c, eta, gamma, s) : tc_update(c, eta, gamma, s);
     } else {
-      if (c.cfg.kind == SGEP_LDA) rc = lda_products(c, X, labels, b, s, sx);
-      else if (c.cfg.kind == SGEP_ICA) rc = ica_products(c, X, b, s, sx, c.cfg.split_AB != 0);
-      else rc = generic_products(c, X, Y, b, s, sx, sy);
+      rc = c.cen_sum ? centring_update(c, X, Y, b, s, sx, sy) : SGEP_OK;  // the step's rows first
+      if (!rc) {
+        if (c.cfg.kind == SGEP_LDA) rc = lda_products(c, X, labels, b, s, sx);
+        else if (c.cfg.kind == SGEP_ICA) rc = ica_products(c, X, b, s, sx, c.cfg.split_AB != 0);
+        else rc = generic_products(c, X, Y, b, s, sx, sy);
+      }
       if (!rc) rc = generic_update(c, eta, gamma, s);
     }
     if (!rc) c.debug_valid = c.cfg.debug;
@@ -593,12 +611,14 @@ int sgep_get_eigenvalues(sgep_t h, const void* X, const void* Y, const float* ro
 static size_t lda_state_bytes(const Ctx& c) {
   return c.cfg.kind == SGEP_LDA ? ((size_t)c.cfg.n_classes * c.d + c.cfg.n_classes) * sizeof(double) : 0;
 }
-// Adam moments (2 d k floats) and their step count; Alg. 3's k scalars z.
+// Adam moments (2 d k floats) and their step count; Alg. 3's k scalars z; the running
+// column sums (d doubles) and row count of a centring handle.
 static size_t variant_state_bytes(const Ctx& c) {
   const size_t dk = (size_t)c.d * c.k;
-  return (c.adam_m ? 2 * dk * sizeof(float) + sizeof(int64_t) : 0) + (c.z ? (size_t)c.k * sizeof(float) : 0);
+  return (c.adam_m ? 2 * dk * sizeof(float) + sizeof(int64_t) : 0) + (c.z ? (size_t)c.k * sizeof(float) : 0) +
+         (c.cen_sum ? ((size_t)c.d + 1) * sizeof(double) : 0);
 }
-static int32_t variant_flags(const Ctx& c) { return (c.adam_m ? 1 : 0) | (c.z ? 2 : 0); }
+static int32_t variant_flags(const Ctx& c) { return (c.adam_m ? 1 : 0) | (c.z ? 2 : 0) | (c.cen_sum ? 4 : 0); }
 
 struct StateHeader {
   char magic[8];
@@ -671,7 +691,14 @@ int sgep_get_state(sgep_t h, void* buf, size_t* nbytes) {
       std::memcpy(q + 2 * dk * sizeof(float), &c.adam_t, sizeof(int64_t));
       q += 2 * dk * sizeof(float) + sizeof(int64_t);
     }
-    if (c.z) SGEP_CUDA_TRY(cudaMemcpy(q, c.z, (size_t)c.k * sizeof(float), cudaMemcpyDeviceToHost));
+    if (c.z) {
+      SGEP_CUDA_TRY(cudaMemcpy(q, c.z, (size_t)c.k * sizeof(float), cudaMemcpyDeviceToHost));
+      q += (size_t)c.k * sizeof(float);
+    }
+    if (c.cen_sum) {
+      SGEP_CUDA_TRY(cudaMemcpy(q, c.cen_sum, (size_t)c.d * sizeof(double), cudaMemcpyDeviceToHost));
+      std::memcpy(q + (size_t)c.d * sizeof(double), &c.cen_count, sizeof(double));
+    }
   }
   *nbytes = need;
   return SGEP_OK;
@@ -714,7 +741,17 @@ int sgep_set_state(sgep_t h, const void* buf, size_t nbytes) {
       std::memcpy(&c.adam_t, q + 2 * dk * sizeof(float), sizeof(int64_t));
       q += 2 * dk * sizeof(float) + sizeof(int64_t);
     }
-    if (c.z) SGEP_CUDA_TRY(cudaMemcpy(c.z, q, (size_t)c.k * sizeof(float), cudaMemcpyHostToDevice));
+    if (c.z) {
+      SGEP_CUDA_TRY(cudaMemcpy(c.z, q, (size_t)c.k * sizeof(float), cudaMemcpyHostToDevice));
+      q += (size_t)c.k * sizeof(float);
+    }
+    if (c.cen_sum) {  // sums and count, then the means they give
+      SGEP_CUDA_TRY(cudaMemcpy(c.cen_sum, q, (size_t)c.d * sizeof(double), cudaMemcpyHostToDevice));
+      std::memcpy(&c.cen_count, q + (size_t)c.d * sizeof(double), sizeof(double));
+      rc = centring_update(c, nullptr, nullptr, 0, (cudaStream_t)0, nullptr, nullptr);
+      if (rc) return rc;
+      SGEP_CUDA_TRY(cudaDeviceSynchronize());
+    }
   }
   c.t = hd.t;
   c.debug_valid = 0;

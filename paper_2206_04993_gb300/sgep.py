@@ -39,7 +39,7 @@ class sgep_config(ctypes.Structure):
         ("path", ctypes.c_int32), ("seed", ctypes.c_uint64), ("max_b", ctypes.c_int64),
         ("debug", ctypes.c_int32), ("optimizer", ctypes.c_int32), ("adam_b1", ctypes.c_float),
         ("adam_b2", ctypes.c_float), ("adam_eps", ctypes.c_float), ("variant", ctypes.c_int32),
-        ("nu", ctypes.c_float), ("reserved", ctypes.c_int32 * 1),
+        ("nu", ctypes.c_float), ("center", ctypes.c_int32),
     ]
 
 
