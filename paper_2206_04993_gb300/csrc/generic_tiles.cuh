@@ -11,6 +11,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
+#include <type_traits>
+
 #include "eg_math.cuh"
 #include "internal.h"
 
@@ -20,9 +22,41 @@ namespace gt {
 constexpr int kThreads = 256;
 constexpr int kMaxK = 64;
 
-// Shared-memory floats each tile needs (k <= 64, C <= 32).
-constexpr int kProjectSmem = 32 * 33 + 32 * kMaxK;
-constexpr int kBackprojectSmem = 32 * 64 + 32 * 2 * kMaxK;
+// Register-tiled SIMT contractions (projection and back-projection). Both tiles stage a
+// block of rows and the players' weights in shared memory, rows padded by kPad floats so
+// every float4 read is aligned and the 8 lanes of one 128-bit access phase hit distinct
+// banks; every thread keeps a 4 x 4 micro-tile of accumulators, one float4 of data and one
+// float4 of weights per 16 FMAs. The k players form ceil(k/4) player quads; the threads
+// left after one thread per (data quad, player quad) split the contraction dimension, and
+// their partial sums are added in shared memory before one atomic per output. The next
+// stage's loads are issued before the current stage is computed: the data rows (any element
+// type, centred or scaled) into registers, the FP32 weights by cp.async into the other half
+// of a double buffer (zero-filled where masked).
+constexpr int kPad = 4;
+constexpr int kWS = kMaxK + kPad;  // staged row stride of V, P and Q (floats)
+constexpr int kProjRows = 64;      // rows of one projection tile
+constexpr int kProjCols = 32;      // columns staged per projection stage
+constexpr int kProjXS = kProjRows + kPad;
+constexpr int kBpRows = 32;        // rows staged per back-projection stage
+constexpr int kBpCols = 64;        // columns of one back-projection tile
+constexpr int kBpZS = kBpCols + kPad;
+constexpr int kRedFloats = kThreads * 16;  // split partials: splits x 64 x 4 ceil(k/4) <= 4096
+constexpr int cmax(int a, int b) { return a > b ? a : b; }
+
+// Plain FP32 rows (no centring, no row scale) skip the registers: rows and weights go to
+// shared memory by cp.async through a ring of stages, so several stages are in flight
+// while one is computed. The projection's ring keeps its rows row-major (stride kPRXS:
+// an odd number of float4, so 8 consecutive rows at one column quad hit distinct banks).
+constexpr int kProjRing = 4;
+constexpr int kBpRing = 3;
+constexpr int kPRXS = kProjCols + kPad;
+constexpr int kProjRingSmem = kProjRing * (kProjRows * kPRXS + kProjCols * kWS);
+constexpr int kBpRingSmem = kBpRing * (kBpRows * kBpZS + 2 * kBpRows * kWS);
+
+// Shared-memory floats each tile needs (k <= 64, C <= 32). The register path's weights are
+// double-buffered.
+constexpr int kProjectSmem = cmax(cmax(kProjCols * kProjXS + 2 * kProjCols * kWS, kRedFloats), kProjRingSmem);
+constexpr int kBackprojectSmem = cmax(cmax(kBpRows * kBpZS + 4 * kBpRows * kWS, kRedFloats), kBpRingSmem);
 __host__ __device__ constexpr int gram_smem(int k) { return 3 * 32 * k; }
 __host__ __device__ constexpr int update_smem(int k) {
   return k * k + 4 * k + (kThreads / k > 1 ? kThreads / k : 1) * k;
@@ -66,22 +100,310 @@ __device__ __forceinline__ float centred(const Centring& cz, float x, int64_t ro
   return x - cz.mean[(int64_t)lab * ld + col];
 }
 
+// acc[a][c] += x[a] w[c]: one 4 x 4 outer product.
+__device__ __forceinline__ void fma4x4(float (&acc)[4][4], const float4 x, const float4 w) {
+  const float xa[4] = {x.x, x.y, x.z, x.w};
+  const float wa[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[a][c] = fmaf(xa[a], wa[c], acc[a][c]);
+}
+
+__device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+
+// 4-byte asynchronous global -> shared copy; zero-fills the destination when !valid (no read).
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_all() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_pending() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Zero the player columns [k, 4 ceil(k/4)) of `rows` staged rows of stride kWS, so the
+// last player quad multiplies zeros.
+__device__ __forceinline__ void zero_player_pad(float* W, int rows, int k) {
+  const int pad = ((k + 3) & ~3) - k;
+  if (pad == 0) return;
+  for (int e = threadIdx.x; e < rows * pad; e += kThreads) W[(e / pad) * kWS + k + e % pad] = 0.f;
+}
+
+// Adds the split partials of the 4 x 4 micro-tiles (thread (o, sp): data group dq = o % 16,
+// player quad pq = o / 16; accumulator row a is data index r = rmul dq + astride a) and issues
+// one atomicAdd(out[orow(r) + i], scale * sum) per output r < 64 with valid(r), i < k.
+// `red` must not overlap data still being read.
+template <typename Valid, typename OutRow>
+__device__ __forceinline__ void reduce_quads(const float (&acc)[4][4], bool active, int splits, int sp, int dq,
+                                             int pq, int k, float scale, float* red, float* out, Valid valid,
+                                             OutRow orow, int rmul = 4, int astride = 1) {
+  const int kp = (k + 3) & ~3;
+  if (splits == 1) {
+    if (active) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const int r = rmul * dq + astride * a;
+        if (!valid(r)) continue;
+        const int64_t base = orow(r);
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (4 * pq + c < k) atomicAdd(&out[base + 4 * pq + c], scale * acc[a][c]);
+      }
+    }
+  } else {
+    if (active) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+        *reinterpret_cast<float4*>(red + ((sp * 64) + rmul * dq + astride * a) * kp + 4 * pq) =
+            make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 64 * k; e += kThreads) {
+      const int r = e / k, i = e % k;
+      if (!valid(r)) continue;
+      float sum = 0.f;
+      for (int s2 = 0; s2 < splits; ++s2) sum += red[(s2 * 64 + r) * kp + i];
+      atomicAdd(&out[orow(r) + i], scale * sum);
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Projection of plain FP32 rows through the cp.async ring (same tile and result as
+// project_tile). Stage st holds rows [row0, row0 + 64) x columns [c0, c0 + 32) row-major and
+// V's rows [c0, c0 + 32); a thread owns rows rq + 16a (a < 4) and one player quad, and per
+// column quad reads 4 float4 of rows and 4 float4 of V for 64 FMAs.
+__device__ inline void project_tile_ring(const float* __restrict__ X, const float* __restrict__ Y, int64_t n,
+                                         int64_t dx, int64_t dy, const float* __restrict__ V, int k, int64_t chunk,
+                                         int nchunk_x, float* __restrict__ PQ, int bx, int by, float* smem) {
+  constexpr int NS = kProjRing;
+  constexpr int kXStage = kProjRows * kPRXS, kVStage = kProjCols * kWS;
+  float* Xs = smem;                // [NS][kProjRows][kPRXS]
+  float* Vs = smem + NS * kXStage;  // [NS][kProjCols][kWS]
+  const int tid = threadIdx.x;
+  const int64_t row0 = (int64_t)bx * kProjRows;
+  const bool isY = by >= nchunk_x;
+  const int cidx = isY ? by - nchunk_x : by;
+  const float* Z = isY ? Y : X;
+  const int64_t ld = isY ? dy : dx;
+  const int64_t voff = isY ? dx : 0;
+  const int64_t c_begin = (int64_t)cidx * chunk;
+  const int64_t c_end = min(c_begin + chunk, ld);
+  const int nst = (int)((c_end - c_begin + kProjCols - 1) / kProjCols);
+  const int kp = (k + 3) & ~3;
+  const int nq = kp >> 2;
+  const int ot = 16 * nq;           // threads with one (row group, player quad)
+  const int splits = kThreads / ot;  // column-quad splits
+  const bool active = tid < ot * splits;
+  const int o = tid % ot, sp = tid / ot;
+  const int rq = o % 16, pq = o / 16;
+  // staging roles: rows xr + 8j at column xc; V rows vr + 4j at player vi
+  const int xc = tid % kProjCols, xr = tid / kProjCols;
+  const int vi = tid % 64, vr = tid / 64;
+  const float* zrow = Z + (row0 + xr) * ld;
+
+  auto issue = [&](int st) {
+    if (st < nst) {
+      float* xs = Xs + (st % NS) * kXStage;
+      float* vs = Vs + (st % NS) * kVStage;
+      const int64_t c0 = c_begin + (int64_t)st * kProjCols;
+      const int64_t col = c0 + xc;
+      const bool cv = col < c_end;
+#pragma unroll
+      for (int j = 0; j < kProjRows / 8; ++j) {
+        const bool v = cv && row0 + xr + 8 * j < n;
+        cp_async4(xs + (xr + 8 * j) * kPRXS + xc, v ? zrow + 8 * j * ld + col : Z, v);
+      }
+      if (vi < kp) {
+#pragma unroll
+        for (int j = 0; j < kProjCols / 4; ++j) {
+          const int64_t c = c0 + vr + 4 * j;
+          const bool v = vi < k && c < c_end;
+          cp_async4(vs + (vr + 4 * j) * kWS + vi, v ? V + (voff + c) * k + vi : V, v);
+        }
+      }
+    }
+    cp_async_commit_all();  // empty groups keep one group per stage
+  };
+
+  __syncthreads();  // the workspace may still be read by this block's previous tile
+  float acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[a][c] = 0.f;
+#pragma unroll
+  for (int st = 0; st < NS - 1; ++st) issue(st);
+  for (int st = 0; st < nst; ++st) {
+    cp_async_wait_pending<NS - 2>();
+    __syncthreads();       // stage st landed for every thread; stage st - 1 is no longer read
+    issue(st + NS - 1);    // into the slot of stage st - 1
+    if (active) {
+      const float* xs = Xs + (st % NS) * kXStage + rq * kPRXS;
+      const float* vs = Vs + (st % NS) * kVStage + 4 * pq;
+#pragma unroll 2
+      for (int q = sp; q < kProjCols / 4; q += splits) {
+        float4 xa[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) xa[a] = lds4(xs + 16 * a * kPRXS + 4 * q);
+        fma4x4(acc, make_float4(xa[0].x, xa[1].x, xa[2].x, xa[3].x), lds4(vs + (4 * q + 0) * kWS));
+        fma4x4(acc, make_float4(xa[0].y, xa[1].y, xa[2].y, xa[3].y), lds4(vs + (4 * q + 1) * kWS));
+        fma4x4(acc, make_float4(xa[0].z, xa[1].z, xa[2].z, xa[3].z), lds4(vs + (4 * q + 2) * kWS));
+        fma4x4(acc, make_float4(xa[0].w, xa[1].w, xa[2].w, xa[3].w), lds4(vs + (4 * q + 3) * kWS));
+      }
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  const int64_t pqoff = isY ? k : 0;
+  reduce_quads(
+      acc, active, splits, sp, rq, pq, k, 1.f, smem, PQ, [&](int r) { return row0 + r < n; },
+      [&](int r) { return (row0 + r) * 2 * k + pqoff; }, 1, 16);
+}
+
+// Back-projection of plain FP32 rows through the cp.async ring (same tile and result as
+// backproject_tile): stage st holds rows [r0, r0 + 32) of the 64-column block and their
+// P / Q weights, masked per estimate by zero-filled copies.
+__device__ inline void backproject_tile_ring(const float* __restrict__ X, const float* __restrict__ Y, int64_t b,
+                                             int64_t dx, int64_t dy, int64_t nA, int kind, int split,
+                                             const float* __restrict__ PQ, int k, int nblk_x,
+                                             int64_t rows_per_split, float inv_nA, float inv_nB,
+                                             float* __restrict__ AV, float* __restrict__ BV, int bx, int by,
+                                             float* smem) {
+  constexpr int NS = kBpRing;
+  constexpr int kZStage = kBpRows * kBpZS, kWStage = kBpRows * kWS;
+  float* Zs = smem;                      // [NS][kBpRows][kBpZS]
+  float* WA = smem + NS * kZStage;       // [NS][kBpRows][kWS]
+  float* WB = WA + NS * kWStage;         // [NS][kBpRows][kWS]
+  const int tid = threadIdx.x;
+  const bool isY = bx >= nblk_x;
+  const int bidx = isY ? bx - nblk_x : bx;
+  const float* Z = isY ? Y : X;
+  const int64_t ld = isY ? dy : dx;
+  const int64_t col0 = (int64_t)bidx * kBpCols;
+  const int64_t r_begin = (int64_t)by * rows_per_split;
+  const int64_t r_end = min(r_begin + rows_per_split, b);
+  const int nst = (int)((max(r_end - r_begin, (int64_t)0) + kBpRows - 1) / kBpRows);
+  const int own = isY ? k : 0;
+  const int cross = isY ? 0 : k;
+  const bool cca = kind == SGEP_CCA;
+  const bool lda = kind == SGEP_LDA;
+  const int offA = (kind == SGEP_PCA) ? 0 : cross;
+  const bool wantA = !lda, wantB = cca || lda;
+  const bool splitAB = cca && split;
+  const int kp = (k + 3) & ~3;
+  const int nq = kp >> 2;
+  const int ot = 16 * nq;           // threads with one (column quad, player quad)
+  const int splits = kThreads / ot;  // row splits
+  const bool active = tid < ot * splits;
+  const int o = tid % ot, sp = tid / ot;
+  const int cq = o % 16, pq = o / 16;
+  // staging roles: rows sr + 4j at column sc (data) or player sc (weights)
+  const int sc = tid % 64, sr = tid / 64;
+  const bool ccol = col0 + sc < ld;
+  const float* zcol = Z + col0 + sc;
+
+  auto issue = [&](int st) {
+    if (st < nst) {
+      const int64_t r0 = r_begin + (int64_t)st * kBpRows;
+      float* zs = Zs + (st % NS) * kZStage;
+      float* wa = WA + (st % NS) * kWStage;
+      float* wb = WB + (st % NS) * kWStage;
+#pragma unroll
+      for (int j = 0; j < kBpRows / 4; ++j) {
+        const int64_t row = r0 + sr + 4 * j;
+        const bool v = ccol && row < r_end;
+        cp_async4(zs + (sr + 4 * j) * kBpZS + sc, v ? zcol + row * ld : Z, v);
+      }
+      if (sc < kp) {
+#pragma unroll
+        for (int j = 0; j < kBpRows / 4; ++j) {
+          const int64_t row = r0 + sr + 4 * j;
+          const bool in = sc < k && row < r_end;
+          if (wantA) {
+            const bool v = in && (!splitAB || row < nA);
+            cp_async4(wa + (sr + 4 * j) * kWS + sc, v ? PQ + row * 2 * k + offA + sc : PQ, v);
+          }
+          if (wantB) {
+            const bool v = in && (!splitAB || row >= nA);
+            cp_async4(wb + (sr + 4 * j) * kWS + sc, v ? PQ + row * 2 * k + own + sc : PQ, v);
+          }
+        }
+      }
+    }
+    cp_async_commit_all();
+  };
+
+  __syncthreads();  // the workspace may still be read by this block's previous tile
+  float accA[4][4], accB[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) accA[a][c] = accB[a][c] = 0.f;
+#pragma unroll
+  for (int st = 0; st < NS - 1; ++st) issue(st);
+  for (int st = 0; st < nst; ++st) {
+    cp_async_wait_pending<NS - 2>();
+    __syncthreads();
+    issue(st + NS - 1);
+    const int64_t r0 = r_begin + (int64_t)st * kBpRows;
+    const int nr = (int)min((int64_t)kBpRows, r_end - r0);
+    const bool useA = wantA && (!splitAB || r0 < nA);
+    const bool useB = wantB && (!splitAB || r0 + nr > nA);
+    if (active) {
+      const float* zs = Zs + (st % NS) * kZStage + 4 * cq;
+      const float* wa = WA + (st % NS) * kWStage + 4 * pq;
+      const float* wb = WB + (st % NS) * kWStage + 4 * pq;
+      if (useA && useB) {
+#pragma unroll 2
+        for (int rr = sp; rr < nr; rr += splits) {
+          const float4 z = lds4(zs + rr * kBpZS);
+          fma4x4(accA, z, lds4(wa + rr * kWS));
+          fma4x4(accB, z, lds4(wb + rr * kWS));
+        }
+      } else if (useA) {
+#pragma unroll 4
+        for (int rr = sp; rr < nr; rr += splits) fma4x4(accA, lds4(zs + rr * kBpZS), lds4(wa + rr * kWS));
+      } else if (useB) {
+#pragma unroll 4
+        for (int rr = sp; rr < nr; rr += splits) fma4x4(accB, lds4(zs + rr * kBpZS), lds4(wb + rr * kWS));
+      }
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  const int64_t coff = isY ? dx : 0;
+  auto valid = [&](int c) { return col0 + c < ld; };
+  auto orow = [&](int c) { return (coff + col0 + c) * k; };
+  if (wantA) reduce_quads(accA, active, splits, sp, cq, pq, k, inv_nA, smem, AV, valid, orow);
+  if (wantB) reduce_quads(accB, active, splits, sp, cq, pq, k, inv_nB, smem, BV, valid, orow);
+}
+
 // ---------------------------------------------------------------------------
 // Projection: PQ[r, 0:k] += X[r, cols] V[cols, :], PQ[r, k:2k] += Y[r, cols] V[d_x + cols, :]
-// Tile (bx, by): rows [32 bx, 32 bx + 32), column chunk by (X chunks first, then Y
-// chunks), each `chunk` columns wide. PQ must be zeroed.
+// Tile (bx, by): rows [kProjRows bx, kProjRows (bx + 1)), column chunk by (X chunks first,
+// then Y chunks), each `chunk` columns wide. PQ must be zeroed. A thread owns 4 rows x 4
+// players; the rows are staged transposed (column-major) so its 4 rows are one float4.
 template <typename T>
 __device__ void project_tile(const T* __restrict__ X, const T* __restrict__ Y, int64_t n, int64_t dx, int64_t dy,
                              const float* __restrict__ V, int k, int64_t chunk, int nchunk_x, float* __restrict__ PQ,
                              const Centring& cz, const float* __restrict__ rsx, const float* __restrict__ rsy,
                              int bx, int by, float* smem) {
-  constexpr int BR = 32, TC = 32;
-  float(*Xs)[TC + 1] = reinterpret_cast<float(*)[TC + 1]>(smem);
-  float(*Vs)[kMaxK] = reinterpret_cast<float(*)[kMaxK]>(smem + BR * (TC + 1));
+  static_assert(kProjRows == 64 && kProjRows * kProjCols % (4 * kThreads) == 0, "projection staging");
+  if constexpr (std::is_same<T, float>::value) {
+    if (!cz.mean && !rsx && !rsy) {
+      project_tile_ring(X, Y, n, dx, dy, V, k, chunk, nchunk_x, PQ, bx, by, smem);
+      return;
+    }
+  }
+  float* Xt = smem;                        // [kProjCols][kProjXS]: Xt[c][r] = Z[row0 + r, c0 + c]
+  float* Vs = smem + kProjCols * kProjXS;  // [2][kProjCols][kWS]
   const int tid = threadIdx.x;
-  const int r = tid >> 3;   // 0..31
-  const int g = tid & 7;    // players g, g+8, ...
-  const int64_t row0 = (int64_t)bx * BR;
+  const int64_t row0 = (int64_t)bx * kProjRows;
   const bool isY = by >= nchunk_x;
   const int cidx = isY ? by - nchunk_x : by;
   const T* Z = isY ? Y : X;
@@ -90,43 +412,82 @@ __device__ void project_tile(const T* __restrict__ X, const T* __restrict__ Y, i
   const int64_t voff = isY ? dx : 0;
   const int64_t c_begin = (int64_t)cidx * chunk;
   const int64_t c_end = min(c_begin + chunk, ld);
-  float acc[kMaxK / 8];
-#pragma unroll
-  for (int m = 0; m < kMaxK / 8; ++m) acc[m] = 0.f;
+  const int nq = (k + 3) >> 2;
+  const int ot = (kProjRows / 4) * nq;  // threads with one (row quad, player quad)
+  const int splits = kThreads / ot;     // column splits
+  const bool active = tid < ot * splits;
+  const int o = tid % ot, sp = tid / ot;
+  const int rq = o % (kProjRows / 4), pq = o / (kProjRows / 4);
 
-  for (int64_t c0 = c_begin; c0 < c_end; c0 += TC) {
-    for (int e = tid; e < BR * TC; e += kThreads) {
-      const int rr = e / TC, cc = e % TC;
-      const int64_t row = row0 + rr, col = c0 + cc;
-      Xs[rr][cc] =
-          (row < n && col < c_end) ? centred(cz, load_row_elem(Z, rs, row, row * ld + col), row, ld, col, isY)
-                                   : 0.f;
-    }
-    for (int e = tid; e < TC * k; e += kThreads) {
-      const int cc = e / k, i = e % k;
-      const int64_t col = c0 + cc;
-      Vs[cc][i] = (col < c_end) ? V[(voff + col) * k + i] : 0.f;
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int cc = 0; cc < TC; ++cc) {
-      const float x = Xs[r][cc];
+  constexpr int kXR = kProjRows * kProjCols / (4 * kThreads);  // row quads staged per thread
+  float xr[kXR][4];
+  auto load_x = [&](int64_t c0) {
 #pragma unroll
-      for (int m = 0; m < kMaxK / 8; ++m) {
-        const int i = g + 8 * m;
-        if (i < k) acc[m] = fmaf(x, Vs[cc][i], acc[m]);
+    for (int j = 0; j < kXR; ++j) {
+      const int slot = tid + kThreads * j;
+      const int cc = slot % kProjCols, q = slot / kProjCols;
+      const int64_t col = c0 + cc;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const int64_t row = row0 + 4 * q + a;
+        xr[j][a] = (row < n && col < c_end) ? centred(cz, load_row_elem(Z, rs, row, row * ld + col), row, ld, col, isY)
+                                            : 0.f;
       }
     }
+  };
+  auto load_v = [&](int64_t c0, float* dst) {
+    for (int e = tid; e < kProjCols * k; e += kThreads) {
+      const int cc = e / k, i = e % k;
+      const int64_t col = c0 + cc;
+      cp_async4(dst + cc * kWS + i, col < c_end ? V + (voff + col) * k + i : V, col < c_end);
+    }
+    cp_async_commit_all();
+  };
+  auto store_x = [&]() {
+#pragma unroll
+    for (int j = 0; j < kXR; ++j) {
+      const int slot = tid + kThreads * j;
+      const int cc = slot % kProjCols, q = slot / kProjCols;
+      *reinterpret_cast<float4*>(Xt + cc * kProjXS + 4 * q) = make_float4(xr[j][0], xr[j][1], xr[j][2], xr[j][3]);
+    }
+  };
+
+  __syncthreads();  // the workspace may still be read by this block's previous tile
+  zero_player_pad(Vs, 2 * kProjCols, k);
+  float acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[a][c] = 0.f;
+  if (c_begin < c_end) {
+    load_v(c_begin, Vs);
+    load_x(c_begin);
+  }
+  int buf = 0;
+  for (int64_t c0 = c_begin; c0 < c_end; c0 += kProjCols, buf ^= 1) {
+    store_x();
+    cp_async_wait_all();
+    __syncthreads();
+    if (c0 + kProjCols < c_end) {
+      load_v(c0 + kProjCols, Vs + (buf ^ 1) * kProjCols * kWS);
+      load_x(c0 + kProjCols);
+    }
+    if (active) {
+      // column quads split across threads, columns in order within a quad: the same
+      // summation order as project_tile_ring, so both row paths give identical sums
+      const float* Vb = Vs + buf * kProjCols * kWS;
+#pragma unroll 2
+      for (int q = sp; q < kProjCols / 4; q += splits)
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          fma4x4(acc, lds4(Xt + (4 * q + c) * kProjXS + 4 * rq), lds4(Vb + (4 * q + c) * kWS + 4 * pq));
+    }
     __syncthreads();
   }
-  const int64_t row = row0 + r;
-  if (row < n) {
-#pragma unroll
-    for (int m = 0; m < kMaxK / 8; ++m) {
-      const int i = g + 8 * m;
-      if (i < k) atomicAdd(&PQ[row * 2 * k + (isY ? k : 0) + i], acc[m]);
-    }
-  }
+  const int64_t pqoff = isY ? k : 0;
+  reduce_quads(
+      acc, active, splits, sp, rq, pq, k, 1.f, smem, PQ, [&](int r) { return row0 + r < n; },
+      [&](int r) { return (row0 + r) * 2 * k + pqoff; });
 }
 
 // ---------------------------------------------------------------------------
@@ -136,7 +497,9 @@ __device__ void project_tile(const T* __restrict__ X, const T* __restrict__ Y, i
 // where (CCA) W_A = Q for X columns / P for Y columns and W_B = P for X / Q for Y;
 // (PCA) W_A = P over every row, no BV; (PLS) W_A as CCA over every row, no BV;
 // (LDA) every row passed is a B row, centred by its class mean: W_B = P, no AV.
-// Tile (bx, by): column block bx of 64 (X blocks then Y blocks), row split by.
+// Tile (bx, by): column block bx of kBpCols (X blocks then Y blocks), row split by.
+// A thread owns 4 columns x 4 players of each estimate; rows of the other estimate are
+// staged with zero weights, and a stage with no row of an estimate skips it.
 template <typename T>
 __device__ void backproject_tile(const T* __restrict__ X, const T* __restrict__ Y, int64_t b, int64_t dx,
                                  int64_t dy, int64_t nA, int kind, int split, const float* __restrict__ PQ, int k,
@@ -144,18 +507,24 @@ __device__ void backproject_tile(const T* __restrict__ X, const T* __restrict__ 
                                  float* __restrict__ AV, float* __restrict__ BV, const Centring& cz,
                                  const float* __restrict__ rsx, const float* __restrict__ rsy, int bx, int by,
                                  float* smem) {
-  constexpr int TR = 32, CB = 64;
-  float(*Zs)[CB] = reinterpret_cast<float(*)[CB]>(smem);
-  float(*Ws)[2 * kMaxK] = reinterpret_cast<float(*)[2 * kMaxK]>(smem + TR * CB);
+  static_assert(kBpCols == 64 && kBpRows * kBpCols % kThreads == 0, "back-projection staging");
+  if constexpr (std::is_same<T, float>::value) {
+    if (!cz.mean && !rsx && !rsy) {
+      backproject_tile_ring(X, Y, b, dx, dy, nA, kind, split, PQ, k, nblk_x, rows_per_split, inv_nA, inv_nB, AV, BV,
+                            bx, by, smem);
+      return;
+    }
+  }
+  float* Zs = smem;                       // [kBpRows][kBpZS]
+  float* WA = smem + kBpRows * kBpZS;     // [2][kBpRows][kWS]
+  float* WB = WA + 2 * kBpRows * kWS;     // [2][kBpRows][kWS]
   const int tid = threadIdx.x;
-  const int cl = tid & (CB - 1);
-  const int g = tid >> 6;  // players g, g+4, ...
   const bool isY = bx >= nblk_x;
   const int bidx = isY ? bx - nblk_x : bx;
   const T* Z = isY ? Y : X;
   const float* rs = isY ? rsy : rsx;
   const int64_t ld = isY ? dy : dx;
-  const int64_t col = (int64_t)bidx * CB + cl;
+  const int64_t col0 = (int64_t)bidx * kBpCols;
   const int64_t r_begin = (int64_t)by * rows_per_split;
   const int64_t r_end = min(r_begin + rows_per_split, b);
   // column offsets into a PQ row: own projection (P for X, Q for Y) and cross projection
@@ -163,71 +532,104 @@ __device__ void backproject_tile(const T* __restrict__ X, const T* __restrict__ 
   const int cross = isY ? 0 : k;
   const bool cca = kind == SGEP_CCA;
   const bool lda = kind == SGEP_LDA;
-  float accA[kMaxK / 4], accB[kMaxK / 4];
-#pragma unroll
-  for (int m = 0; m < kMaxK / 4; ++m) accA[m] = accB[m] = 0.f;
+  const int offA = (kind == SGEP_PCA) ? 0 : cross;
+  const bool wantA = !lda, wantB = cca || lda;
+  const bool splitAB = cca && split;
+  const int nq = (k + 3) >> 2;
+  const int ot = (kBpCols / 4) * nq;  // threads with one (column quad, player quad)
+  const int splits = kThreads / ot;   // row splits
+  const bool active = tid < ot * splits;
+  const int o = tid % ot, sp = tid / ot;
+  const int cq = o % (kBpCols / 4), pq = o / (kBpCols / 4);
 
-  for (int64_t r0 = r_begin; r0 < r_end; r0 += TR) {
-    for (int e = tid; e < TR * CB; e += kThreads) {
-      const int rr = e / CB, cc = e % CB;
-      const int64_t row = r0 + rr, cg = (int64_t)bidx * CB + cc;
-      Zs[rr][cc] =
-          (row < r_end && cg < ld) ? centred(cz, load_row_elem(Z, rs, row, row * ld + cg), row, ld, cg, isY)
-                                   : 0.f;
+  constexpr int kZR = kBpRows * kBpCols / kThreads;
+  float zr[kZR];
+  auto load_z = [&](int64_t r0) {
+#pragma unroll
+    for (int j = 0; j < kZR; ++j) {
+      const int slot = tid + kThreads * j;
+      const int cc = slot % kBpCols, rr = slot / kBpCols;
+      const int64_t row = r0 + rr, cg = col0 + cc;
+      zr[j] = (row < r_end && cg < ld) ? centred(cz, load_row_elem(Z, rs, row, row * ld + cg), row, ld, cg, isY)
+                                       : 0.f;
     }
-    for (int e = tid; e < TR * 2 * k; e += kThreads) {
-      const int rr = e / (2 * k), j = e % (2 * k);
+  };
+  // P / Q rows of the stage, each into the estimate(s) it feeds (zeros elsewhere)
+  auto load_w = [&](int64_t r0, int bsel) {
+    float* wa = WA + bsel * kBpRows * kWS;
+    float* wb = WB + bsel * kBpRows * kWS;
+    for (int e = tid; e < kBpRows * k; e += kThreads) {
+      const int rr = e / k, i = e % k;
       const int64_t row = r0 + rr;
-      Ws[rr][j] = (row < r_end) ? PQ[row * 2 * k + j] : 0.f;
+      const bool in = row < r_end;
+      if (wantA) {
+        const bool v = in && (!splitAB || row < nA);
+        cp_async4(wa + rr * kWS + i, v ? PQ + row * 2 * k + offA + i : PQ, v);
+      }
+      if (wantB) {
+        const bool v = in && (!splitAB || row >= nA);
+        cp_async4(wb + rr * kWS + i, v ? PQ + row * 2 * k + own + i : PQ, v);
+      }
     }
+    cp_async_commit_all();
+  };
+  auto store_z = [&]() {
+#pragma unroll
+    for (int j = 0; j < kZR; ++j) {
+      const int slot = tid + kThreads * j;
+      Zs[(slot / kBpCols) * kBpZS + slot % kBpCols] = zr[j];
+    }
+  };
+
+  __syncthreads();  // the workspace may still be read by this block's previous tile
+  zero_player_pad(WA, 4 * kBpRows, k);  // both buffers of WA and WB
+  float accA[4][4], accB[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) accA[a][c] = accB[a][c] = 0.f;
+  if (r_begin < r_end) {
+    load_w(r_begin, 0);
+    load_z(r_begin);
+  }
+  int buf = 0;
+  for (int64_t r0 = r_begin; r0 < r_end; r0 += kBpRows, buf ^= 1) {
+    store_z();
+    cp_async_wait_all();
     __syncthreads();
-    const int nr = (int)min((int64_t)TR, r_end - r0);
-    for (int rr = 0; rr < nr; ++rr) {
-      const int64_t row = r0 + rr;
-      const float z = Zs[rr][cl];
-      // which estimate(s) this row feeds
-      bool toA, toB;
-      if (lda) {
-        toA = false;
-        toB = true;
-      } else if (!cca) {
-        toA = true;
-        toB = false;
-      } else if (split) {
-        toA = row < nA;
-        toB = !toA;
-      } else {
-        toA = toB = true;
-      }
-      const int offA = (kind == SGEP_PCA) ? 0 : cross;
-      if (toA) {
-#pragma unroll
-        for (int m = 0; m < kMaxK / 4; ++m) {
-          const int i = g + 4 * m;
-          if (i < k) accA[m] = fmaf(z, Ws[rr][offA + i], accA[m]);
+    const int nr = (int)min((int64_t)kBpRows, r_end - r0);
+    const bool useA = wantA && (!splitAB || r0 < nA);
+    const bool useB = wantB && (!splitAB || r0 + nr > nA);
+    if (r0 + kBpRows < r_end) {
+      load_w(r0 + kBpRows, buf ^ 1);
+      load_z(r0 + kBpRows);
+    }
+    if (active) {
+      const float* wa = WA + buf * kBpRows * kWS + 4 * pq;
+      const float* wb = WB + buf * kBpRows * kWS + 4 * pq;
+      const float* zs = Zs + 4 * cq;
+      if (useA && useB) {
+#pragma unroll 2
+        for (int rr = sp; rr < nr; rr += splits) {
+          const float4 z = lds4(zs + rr * kBpZS);
+          fma4x4(accA, z, lds4(wa + rr * kWS));
+          fma4x4(accB, z, lds4(wb + rr * kWS));
         }
-      }
-      if (toB) {
-#pragma unroll
-        for (int m = 0; m < kMaxK / 4; ++m) {
-          const int i = g + 4 * m;
-          if (i < k) accB[m] = fmaf(z, Ws[rr][own + i], accB[m]);
-        }
+      } else if (useA) {
+#pragma unroll 4
+        for (int rr = sp; rr < nr; rr += splits) fma4x4(accA, lds4(zs + rr * kBpZS), lds4(wa + rr * kWS));
+      } else if (useB) {
+#pragma unroll 4
+        for (int rr = sp; rr < nr; rr += splits) fma4x4(accB, lds4(zs + rr * kBpZS), lds4(wb + rr * kWS));
       }
     }
     __syncthreads();
   }
-  if (col < ld) {
-    const int64_t gc = (isY ? dx : 0) + col;
-#pragma unroll
-    for (int m = 0; m < kMaxK / 4; ++m) {
-      const int i = g + 4 * m;
-      if (i < k) {
-        if (!lda) atomicAdd(&AV[gc * k + i], accA[m] * inv_nA);
-        if (cca || lda) atomicAdd(&BV[gc * k + i], accB[m] * inv_nB);
-      }
-    }
-  }
+  const int64_t coff = isY ? dx : 0;
+  auto valid = [&](int c) { return col0 + c < ld; };
+  auto orow = [&](int c) { return (coff + col0 + c) * k; };
+  if (wantA) reduce_quads(accA, active, splits, sp, cq, pq, k, inv_nA, smem, AV, valid, orow);
+  if (wantB) reduce_quads(accB, active, splits, sp, cq, pq, k, inv_nB, smem, BV, valid, orow);
 }
 
 // ---------------------------------------------------------------------------

@@ -61,8 +61,10 @@ struct BatchHeader {
 namespace {
 
 using gt::kThreads;
-constexpr int kSmemFloats = 32 * kThreads + kThreads;  // the largest tile workspace (LDA statistics, C = 32)
-static_assert(kSmemFloats >= gt::kBackprojectSmem && kSmemFloats >= gt::gram_smem(64) &&
+// the largest tile workspace: the back-projection's, or the LDA statistics' (C = 32)
+constexpr int kSmemFloats = gt::cmax(32 * kThreads + kThreads, gt::kBackprojectSmem);
+static_assert(kSmemFloats >= gt::kBackprojectSmem && kSmemFloats >= gt::kProjectSmem &&
+                  kSmemFloats >= gt::gram_smem(64) &&
                   kSmemFloats >= gt::update_smem(1) && kSmemFloats >= gt::kLdaWSmem,
               "batch workspace");
 
@@ -159,16 +161,16 @@ __device__ void run_phase(const BatchHeader* h, const InstDesc* inst, int phase,
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_batch_phase(const BatchHeader* __restrict__ h,
+__global__ void __launch_bounds__(kThreads, 2) k_batch_phase(const BatchHeader* __restrict__ h,
                                                           const InstDesc* __restrict__ inst, int phase) {
-  extern __shared__ float smem[];
+  extern __shared__ __align__(16) float smem[];
   run_phase(h, inst, phase, smem);
 }
 
-__global__ void __launch_bounds__(kThreads) k_batch_persistent(const BatchHeader* __restrict__ h,
+__global__ void __launch_bounds__(kThreads, 2) k_batch_persistent(const BatchHeader* __restrict__ h,
                                                                const InstDesc* __restrict__ inst,
                                                                unsigned long long* bar, int* dflag) {
-  extern __shared__ float smem[];
+  extern __shared__ __align__(16) float smem[];
   __shared__ int ok_s;
   const unsigned long long base = h->bar_base;
   for (int phase = 0; phase < kPhases; ++phase) {
@@ -296,7 +298,7 @@ static void partition(const BatchCtx& B, const Ctx& c, int64_t b, InstDesc& D) {
   D.b = b;
   D.nA = D.split ? b / 2 : (lda ? 0 : b);
   D.nrows_proj = lda ? b - D.nA : b;
-  D.row_tiles = (int)((D.nrows_proj + 31) / 32);
+  D.row_tiles = (int)((D.nrows_proj + gt::kProjRows - 1) / gt::kProjRows);
   int64_t chunk = B.tune.chunk_cap;
   // keep a few column chunks per row tile so that small-b instances still spread out
   while (chunk > 64 && (int64_t)D.row_tiles * ((c.d + chunk - 1) / chunk) < 8) chunk /= 2;

@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(kThreads) k_project(const T* __restrict__ X, c
                                                       int64_t chunk, int nchunk_x, float* __restrict__ PQ,
                                                       const Centring cz, const float* __restrict__ rsx,
                                                       const float* __restrict__ rsy) {
-  extern __shared__ float smem[];
+  extern __shared__ __align__(16) float smem[];
   gt::project_tile(X, Y, n, dx, dy, V, k, chunk, nchunk_x, PQ, cz, rsx, rsy, blockIdx.x, blockIdx.y, smem);
 }
 
@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(kThreads) k_backproject(
     int split, const float* __restrict__ PQ, int k, int nblk_x, int64_t rows_per_split, float inv_nA, float inv_nB,
     float* __restrict__ AV, float* __restrict__ BV, const Centring cz, const float* __restrict__ rsx,
     const float* __restrict__ rsy) {
-  extern __shared__ float smem[];
+  extern __shared__ __align__(16) float smem[];
   gt::backproject_tile(X, Y, b, dx, dy, nA, kind, split, PQ, k, nblk_x, rows_per_split, inv_nA, inv_nB, AV, BV, cz,
                        rsx, rsy, blockIdx.x, blockIdx.y, smem);
 }
@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(kThreads) k_gram(const float* __restrict__ V, 
                                                    const float* __restrict__ AV, const float* __restrict__ BV,
                                                    int64_t d, int k, float eps_B, int b_is_identity,
                                                    float* __restrict__ gram) {
-  extern __shared__ float smem[];
+  extern __shared__ __align__(16) float smem[];
   gt::gram_tile(V, S, AV, BV, d, k, eps_B, b_is_identity, gram, blockIdx.x, gridDim.x, smem);
 }
 
@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(kThreads) k_update(const float* __restrict__ V
                                                      float rho, float eps_B, int b_is_identity,
                                                      float* __restrict__ Vtmp, float* __restrict__ grad_out,
                                                      const UpdVariant var) {
-  extern __shared__ float smem[];
+  extern __shared__ __align__(16) float smem[];
   gt::update_tile(V, S, AV, BV, gram, d, k, eta, gamma, rho, eps_B, b_is_identity, Vtmp, grad_out, blockIdx.x,
                   gridDim.x, smem, var);
 }
@@ -94,16 +94,23 @@ __global__ void k_rayleigh(const float* __restrict__ PQ, int64_t n, int k, int k
 
 inline int grid_cap(const Ctx& c, int per_sm) { return c.num_sms * per_sm; }
 
+// The contraction tiles use more than the default 48 KB of dynamic shared memory.
+template <typename K>
+cudaError_t smem_optin(K kernel, int floats) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, floats * (int)sizeof(float));
+}
+
 template <typename T>
 int launch_project(Ctx& c, const T* X, const T* Y, int64_t n, cudaStream_t s, const Centring& cz,
                    const float* sx, const float* sy) {
-  const int64_t row_tiles = (n + 31) / 32;
+  const int64_t row_tiles = (n + gt::kProjRows - 1) / gt::kProjRows;
   // Column chunk: enough blocks to fill the GPU, at least 32 columns each.
   int64_t chunk = 1024;
   while (chunk > 64 && row_tiles * ((c.d + chunk - 1) / chunk) < 2LL * c.num_sms) chunk /= 2;
   const int nchunk_x = (int)((c.d_x + chunk - 1) / chunk);
   const int nchunk_y = c.has_y ? (int)((c.d_y + chunk - 1) / chunk) : 0;
   dim3 grid((unsigned)row_tiles, (unsigned)(nchunk_x + nchunk_y));
+  SGEP_CUDA_TRY(smem_optin(k_project<T>, gt::kProjectSmem));
   k_project<T><<<grid, kThreads, gt::kProjectSmem * sizeof(float), s>>>(X, Y, n, c.d_x, c.d_y, c.V, c.k, chunk, nchunk_x, c.PQ, cz, sx, sy);
   SGEP_CUDA_TRY(cudaGetLastError());
   ++c.launches;
@@ -129,6 +136,7 @@ int launch_backproject(Ctx& c, const T* X, const T* Y, int64_t b, cudaStream_t s
   dim3 grid((unsigned)nblk, (unsigned)splits);
   float* AV = c.acc;
   float* BV = c.acc + c.d * c.k;
+  SGEP_CUDA_TRY(smem_optin(k_backproject<T>, gt::kBackprojectSmem));
   k_backproject<T><<<grid, kThreads, gt::kBackprojectSmem * sizeof(float), s>>>(X, Y, b, c.d_x, c.d_y, nA, kind, split, c.PQ, c.k,
                                              nblk_x, rows_per_split, 1.f / (float)nA,
                                              1.f / (float)nB, AV, BV, cz, sx, sy);
@@ -212,12 +220,13 @@ __global__ void k_ica_combine(float* __restrict__ AV, const float* __restrict__ 
 template <typename T>
 int launch_project_with(Ctx& c, const T* X, int64_t n, const float* M, float* out, cudaStream_t s, const float* sx) {
   SGEP_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(float) * n * 2 * c.k, s));
-  const int64_t row_tiles = (n + 31) / 32;
+  const int64_t row_tiles = (n + gt::kProjRows - 1) / gt::kProjRows;
   int64_t chunk = 1024;
   while (chunk > 64 && row_tiles * ((c.d_x + chunk - 1) / chunk) < 2LL * c.num_sms) chunk /= 2;
   const int nchunk_x = (int)((c.d_x + chunk - 1) / chunk);
   const Centring none{nullptr, nullptr, 0, c.dflag};
   dim3 grid((unsigned)row_tiles, (unsigned)nchunk_x);
+  SGEP_CUDA_TRY(smem_optin(k_project<T>, gt::kProjectSmem));
   k_project<T><<<grid, kThreads, gt::kProjectSmem * sizeof(float), s>>>(X, nullptr, n, c.d_x, 0, M, c.k, chunk,
                                                                           nchunk_x, out, none, sx, nullptr);
   SGEP_CUDA_TRY(cudaGetLastError());
@@ -237,6 +246,7 @@ int launch_bp_rows(Ctx& c, const T* X, int64_t n, const float* P, float* out, fl
   splits = (int)((n + rows_per_split - 1) / rows_per_split);
   const Centring none{nullptr, nullptr, 0, c.dflag};
   dim3 grid((unsigned)nblk, (unsigned)splits);
+  SGEP_CUDA_TRY(smem_optin(k_backproject<T>, gt::kBackprojectSmem));
   k_backproject<T><<<grid, kThreads, gt::kBackprojectSmem * sizeof(float), s>>>(
       X, nullptr, n, c.d_x, 0, n, SGEP_PCA, 0, P, c.k, nblk, rows_per_split, scale, scale, out, nullptr, none, sx,
       nullptr);

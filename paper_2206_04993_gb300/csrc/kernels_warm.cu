@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(kThreads) k_sk_project(const T* __restrict__ X
                                                          int64_t dx, int64_t dy, const float* __restrict__ om, int m,
                                                          int64_t chunk, int nchunk_x, float* __restrict__ PQ,
                                                          int* dflag) {
-  extern __shared__ float smem[];
+  extern __shared__ __align__(16) float smem[];
   const gt::Centring none{nullptr, nullptr, 0, dflag};
   gt::project_tile(X, Y, n, dx, dy, om, m, chunk, nchunk_x, PQ, none, nullptr, nullptr, blockIdx.x, blockIdx.y,
                    smem);
@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(kThreads) k_sk_back(const T* __restrict__ X, c
                                                       int64_t dx, int64_t dy, const float* __restrict__ PQ, int m,
                                                       int nblk_x, int64_t rows_per_split, float inv_n,
                                                       float* __restrict__ out, int* dflag) {
-  extern __shared__ float smem[];
+  extern __shared__ __align__(16) float smem[];
   const gt::Centring none{nullptr, nullptr, 0, dflag};
   // kind PCA: every column block reads the first half of the PQ rows (T)
   gt::backproject_tile(X, Y, n, dx, dy, n, SGEP_PCA, 0, PQ, m, nblk_x, rows_per_split, inv_n, 0.f, out, nullptr, none,
@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(kThreads) k_mlp_forward(const float* __restric
                                                           const float* __restrict__ S, int64_t rows,
                                                           float* __restrict__ O, float* __restrict__ Z1,
                                                           float* __restrict__ Z2) {
-  extern __shared__ float smem[];
+  extern __shared__ __align__(16) float smem[];
   const SmemW w = load_weights(Pw, sh, smem);
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(kThreads) k_mlp_backward(const float* __restri
                                                            const float* __restrict__ stats, float inv_n,
                                                            float* __restrict__ dO, float* __restrict__ dH2,
                                                            float* __restrict__ dH1) {
-  extern __shared__ float smem[];
+  extern __shared__ __align__(16) float smem[];
   const SmemW w = load_weights(Pw, sh, smem);
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -596,7 +596,7 @@ int sketch_rows(const void* X, const void* Y, int dtype, int64_t n, int64_t dx, 
   int rc = SGEP_OK;
   cudaMemsetAsync(PQ, 0, (size_t)n * 2 * m * sizeof(float), s);
   cudaMemsetAsync(out, 0, (size_t)d * m * sizeof(float), s);
-  const int64_t row_tiles = (n + 31) / 32;
+  const int64_t row_tiles = (n + gt::kProjRows - 1) / gt::kProjRows;
   int64_t chunk = 1024;
   while (chunk > 64 && row_tiles * ((d + chunk - 1) / chunk) < 2LL * num_sms) chunk /= 2;
   const int nchunk_x = (int)((dx + chunk - 1) / chunk), nchunk_y = dy ? (int)((dy + chunk - 1) / chunk) : 0;
@@ -608,6 +608,8 @@ int sketch_rows(const void* X, const void* Y, int dtype, int64_t n, int64_t dx, 
   const size_t sp = gt::kProjectSmem * sizeof(float), sb = gt::kBackprojectSmem * sizeof(float);
   auto launch = [&](auto tag) {
     using T = std::remove_const_t<std::remove_pointer_t<decltype(tag)>>;
+    cudaFuncSetAttribute(k_sk_project<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp);
+    cudaFuncSetAttribute(k_sk_back<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
     k_sk_project<T><<<dim3((unsigned)row_tiles, (unsigned)(nchunk_x + nchunk_y)), kThreads, sp, s>>>(
         (const T*)X, (const T*)Y, n, dx, dy, om, m, chunk, nchunk_x, PQ, dflag);
     k_sk_combine<<<(unsigned)std::min<int64_t>((n * m + 255) / 256, 4LL * num_sms), 256, 0, s>>>(PQ, n, m);
