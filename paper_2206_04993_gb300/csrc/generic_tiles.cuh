@@ -119,6 +119,12 @@ __device__ __forceinline__ void cp_async4(float* dst, const float* src, bool val
 }
 __device__ __forceinline__ void cp_async_commit_all() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+// 16-byte variant (both addresses 16-byte aligned); zero-fills when !valid.
+__device__ __forceinline__ void cp_async16z(float* dst, const float* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 template <int N>
 __device__ __forceinline__ void cp_async_wait_pending() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
@@ -201,24 +207,46 @@ __device__ inline void project_tile_ring(const float* __restrict__ X, const floa
   const bool active = tid < ot * splits;
   const int o = tid % ot, sp = tid / ot;
   const int rq = o % 16, pq = o / 16;
-  // staging roles: rows xr + 8j at column xc; V rows vr + 4j at player vi
-  const int xc = tid % kProjCols, xr = tid / kProjCols;
-  const int vi = tid % 64, vr = tid / 64;
-  const float* zrow = Z + (row0 + xr) * ld;
+  // 16-byte copies when the row pitch and base allow (then a stage's columns are all valid
+  // or all past the end together), else 4-byte copies.
+  const bool x16 = (ld % 4 == 0) && aligned16(Z);
+  const bool v16 = (k % 4 == 0) && aligned16(V);
+  // staging roles: 16-byte rows xq + 32j, column quad xm (4-byte: rows xr + 8j, column xc);
+  // V rows vq + 16j, player quad vm (4-byte: rows vr + 4j, player vi)
+  const int xm = tid % 8, xq = tid / 8, xc = tid % kProjCols, xr = tid / kProjCols;
+  const int vm = tid % 16, vq = tid / 16, vi = tid % 64, vr = tid / 64;
+  const float* zrow = x16 ? Z + (row0 + xq) * ld + 4 * xm : Z + (row0 + xr) * ld + xc;
 
   auto issue = [&](int st) {
     if (st < nst) {
       float* xs = Xs + (st % NS) * kXStage;
       float* vs = Vs + (st % NS) * kVStage;
       const int64_t c0 = c_begin + (int64_t)st * kProjCols;
-      const int64_t col = c0 + xc;
-      const bool cv = col < c_end;
+      if (x16) {
+        const bool cv = c0 + 4 * xm < c_end;
 #pragma unroll
-      for (int j = 0; j < kProjRows / 8; ++j) {
-        const bool v = cv && row0 + xr + 8 * j < n;
-        cp_async4(xs + (xr + 8 * j) * kPRXS + xc, v ? zrow + 8 * j * ld + col : Z, v);
+        for (int j = 0; j < kProjRows / 32; ++j) {
+          const bool v = cv && row0 + xq + 32 * j < n;
+          cp_async16z(xs + (xq + 32 * j) * kPRXS + 4 * xm, v ? zrow + 32 * j * ld + c0 : Z, v);
+        }
+      } else {
+        const bool cv = c0 + xc < c_end;
+#pragma unroll
+        for (int j = 0; j < kProjRows / 8; ++j) {
+          const bool v = cv && row0 + xr + 8 * j < n;
+          cp_async4(xs + (xr + 8 * j) * kPRXS + xc, v ? zrow + 8 * j * ld + c0 : Z, v);
+        }
       }
-      if (vi < kp) {
+      if (v16) {
+        if (vm < nq) {
+#pragma unroll
+          for (int j = 0; j < kProjCols / 16; ++j) {
+            const int64_t c = c0 + vq + 16 * j;
+            const bool v = c < c_end;
+            cp_async16z(vs + (vq + 16 * j) * kWS + 4 * vm, v ? V + (voff + c) * k + 4 * vm : V, v);
+          }
+        }
+      } else if (vi < kp) {
 #pragma unroll
         for (int j = 0; j < kProjCols / 4; ++j) {
           const int64_t c = c0 + vr + 4 * j;
@@ -302,10 +330,14 @@ __device__ inline void backproject_tile_ring(const float* __restrict__ X, const 
   const bool active = tid < ot * splits;
   const int o = tid % ot, sp = tid / ot;
   const int cq = o % 16, pq = o / 16;
-  // staging roles: rows sr + 4j at column sc (data) or player sc (weights)
-  const int sc = tid % 64, sr = tid / 64;
-  const bool ccol = col0 + sc < ld;
-  const float* zcol = Z + col0 + sc;
+  // 16-byte copies when the row pitch and bases allow, else 4-byte copies
+  const bool z16 = (ld % 4 == 0) && aligned16(Z);
+  const bool w16 = (k % 4 == 0) && aligned16(PQ);
+  // staging roles: 16-byte rows sq + 16j at column (or player) quad sm; 4-byte rows sr + 4j
+  // at column (or player) sc
+  const int sm = tid % 16, sq = tid / 16, sc = tid % 64, sr = tid / 64;
+  const bool ccol = z16 ? col0 + 4 * sm < ld : col0 + sc < ld;
+  const float* zcol = z16 ? Z + col0 + 4 * sm : Z + col0 + sc;
 
   auto issue = [&](int st) {
     if (st < nst) {
@@ -313,13 +345,38 @@ __device__ inline void backproject_tile_ring(const float* __restrict__ X, const 
       float* zs = Zs + (st % NS) * kZStage;
       float* wa = WA + (st % NS) * kWStage;
       float* wb = WB + (st % NS) * kWStage;
+      if (z16) {
 #pragma unroll
-      for (int j = 0; j < kBpRows / 4; ++j) {
-        const int64_t row = r0 + sr + 4 * j;
-        const bool v = ccol && row < r_end;
-        cp_async4(zs + (sr + 4 * j) * kBpZS + sc, v ? zcol + row * ld : Z, v);
+        for (int j = 0; j < kBpRows / 16; ++j) {
+          const int64_t row = r0 + sq + 16 * j;
+          const bool v = ccol && row < r_end;
+          cp_async16z(zs + (sq + 16 * j) * kBpZS + 4 * sm, v ? zcol + row * ld : Z, v);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < kBpRows / 4; ++j) {
+          const int64_t row = r0 + sr + 4 * j;
+          const bool v = ccol && row < r_end;
+          cp_async4(zs + (sr + 4 * j) * kBpZS + sc, v ? zcol + row * ld : Z, v);
+        }
       }
-      if (sc < kp) {
+      if (w16) {
+        if (sm < nq) {
+#pragma unroll
+          for (int j = 0; j < kBpRows / 16; ++j) {
+            const int64_t row = r0 + sq + 16 * j;
+            const bool in = row < r_end;
+            if (wantA) {
+              const bool v = in && (!splitAB || row < nA);
+              cp_async16z(wa + (sq + 16 * j) * kWS + 4 * sm, v ? PQ + row * 2 * k + offA + 4 * sm : PQ, v);
+            }
+            if (wantB) {
+              const bool v = in && (!splitAB || row >= nA);
+              cp_async16z(wb + (sq + 16 * j) * kWS + 4 * sm, v ? PQ + row * 2 * k + own + 4 * sm : PQ, v);
+            }
+          }
+        }
+      } else if (sc < kp) {
 #pragma unroll
         for (int j = 0; j < kBpRows / 4; ++j) {
           const int64_t row = r0 + sr + 4 * j;
