@@ -458,6 +458,16 @@ struct TcUpdArgs {
   UpdVariant var;             // Adam on the players / Alg. 3 denominators, or plain Alg. 2
 };
 
+// acc[a][c] += x[a] y[c]: one 4 x 4 outer product.
+__device__ __forceinline__ void tc_fma4x4(float (&acc)[4][4], const float4 x, const float4 y) {
+  const float xa[4] = {x.x, x.y, x.z, x.w};
+  const float ya[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[a][c] = fmaf(xa[a], ya[c], acc[a][c]);
+}
+
 // Bounded grid barrier: returns false (and flags a timeout) when the wait gives up.
 __device__ __forceinline__ bool grid_barrier(unsigned long long* bar, unsigned long long target, int* flag,
                                              int* ok_s) {
@@ -477,11 +487,13 @@ template <bool kVar>
 __global__ void __launch_bounds__(256, 2) k_tc_update_fused(const TcUpdArgs u) {
   constexpr int R = 128;
   constexpr int KP = kTcKP;
-  __shared__ float T[KP * KP];
+  constexpr int SP = KP + 4;  // row stride of vs / ss: float4-aligned rows, 9 float4 (odd) per row
+  static_assert(KP == 32 && R == 128, "micro-tile mappings below assume 32 players and 128 rows");
+  __shared__ __align__(16) float T[KP * KP];
   __shared__ float cb[KP], cac[KP], inv_s[KP], inv_n[KP], nsq[KP], gdiag[KP];
   __shared__ float red[8][KP];
-  __shared__ float vs[R][KP + 1];
-  __shared__ float ss[R][KP + 1];
+  __shared__ __align__(16) float vs[R][SP];
+  __shared__ __align__(16) float ss[R][SP];
   __shared__ int ok_s;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int k = u.k, kk = k * k, slot = u.slot;
@@ -529,9 +541,9 @@ __global__ void __launch_bounds__(256, 2) k_tc_update_fused(const TcUpdArgs u) {
                                             : fmaxf(Gm[tid * k + tid], u.rho));
     }
     __syncthreads();
-    for (int p = tid; p < kk; p += 256) {
-      const int j = p / k, i = p % k;
-      T[j * KP + i] = j < i ? cb[i] * As[i * k + j] * inv_s[j] : 0.f;
+    for (int p = tid; p < KP * KP; p += 256) {  // zero outside k x k: read by the micro-tiles
+      const int j = p / KP, i = p % KP;
+      T[p] = (i < k && j < i) ? cb[i] * As[i * k + j] * inv_s[j] : 0.f;
     }
     if (tid < k) {
       float c = 0.f;
@@ -553,7 +565,7 @@ __global__ void __launch_bounds__(256, 2) k_tc_update_fused(const TcUpdArgs u) {
   float nr = 0.f;
   {
     constexpr int U = 16;
-    float v[U], sv[U], av[U], bv[U], pen[U];
+    float v[U], sv[U], av[U], bv[U];
 #pragma unroll
     for (int q = 0; q < U; ++q) {
       const int r = wid + 8 * q;
@@ -563,7 +575,6 @@ __global__ void __launch_bounds__(256, 2) k_tc_update_fused(const TcUpdArgs u) {
       sv[q] = ok ? u.S[g] : 0.f;
       av[q] = ok ? __ldcg(u.AV + g) : 0.f;
       bv[q] = ok ? __ldcg(u.BV + g) : 0.f;
-      pen[q] = 0.f;
     }
     float am[kVar ? U : 1], as2[kVar ? U : 1];  // Adam moments of the rows
     if constexpr (kVar) {
@@ -576,18 +587,44 @@ __global__ void __launch_bounds__(256, 2) k_tc_update_fused(const TcUpdArgs u) {
         as2[q] = ok ? u.var.s[g] : 0.f;
       }
     }
-    for (int j = 0; j < k; ++j) {
-      const float t = T[j * kTcKP + lane];
+    // penalty PEN = S T over the block's rows (T_ji = 0 unless j < i): the old S rows in ss,
+    // thread -> rows pr + 32a (a < 4) x players 4pc..4pc+3, result into vs
 #pragma unroll
-      for (int q = 0; q < U; ++q) pen[q] = fmaf(__shfl_sync(0xffffffffu, sv[q], j), t, pen[q]);
+    for (int q = 0; q < U; ++q) ss[wid + 8 * q][lane] = sv[q];
+    __syncthreads();
+    {
+      const int pr = tid & 31, pc = tid >> 5;
+      float pacc[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) pacc[a][c] = 0.f;
+      for (int j0 = 0; j0 < k; j0 += 4) {
+        float4 s4[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) s4[a] = *reinterpret_cast<const float4*>(&ss[pr + 32 * a][j0]);
+        const float4 t0 = *reinterpret_cast<const float4*>(&T[(j0 + 0) * KP + 4 * pc]);
+        const float4 t1 = *reinterpret_cast<const float4*>(&T[(j0 + 1) * KP + 4 * pc]);
+        const float4 t2 = *reinterpret_cast<const float4*>(&T[(j0 + 2) * KP + 4 * pc]);
+        const float4 t3 = *reinterpret_cast<const float4*>(&T[(j0 + 3) * KP + 4 * pc]);
+        tc_fma4x4(pacc, make_float4(s4[0].x, s4[1].x, s4[2].x, s4[3].x), t0);
+        tc_fma4x4(pacc, make_float4(s4[0].y, s4[1].y, s4[2].y, s4[3].y), t1);
+        tc_fma4x4(pacc, make_float4(s4[0].z, s4[1].z, s4[2].z, s4[3].z), t2);
+        tc_fma4x4(pacc, make_float4(s4[0].w, s4[1].w, s4[2].w, s4[3].w), t3);
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+        *reinterpret_cast<float4*>(&vs[pr + 32 * a][4 * pc]) =
+            make_float4(pacc[a][0], pacc[a][1], pacc[a][2], pacc[a][3]);
     }
+    __syncthreads();
 #pragma unroll
     for (int q = 0; q < U; ++q) {
       const int r = wid + 8 * q;
       const int64_t g = (c0 + r) * k + lane;
       const bool ok = on && c0 + r < u.d;
       const float bve = fmaf(u.eps_B, v[q], bv[q]);
-      const float gr = cb[lane] * av[q] - cac[lane] * bve - pen[q];
+      const float gr = cb[lane] * av[q] - cac[lane] * bve - vs[r][lane];
       float step = gr;
       if constexpr (kVar) {
         if (u.var.m) step = adam_increment(gr, am[q], as2[q], u.var.b1, u.var.b2, u.var.eps, u.var.bc1, u.var.bc2);
@@ -617,17 +654,31 @@ __global__ void __launch_bounds__(256, 2) k_tc_update_fused(const TcUpdArgs u) {
     atomicAdd(nsum + tid, s2);
   }
   {
-    // the block's partial of U = V'^T S': thread -> (row i of U, four consecutive columns)
-    const int i = tid >> 3, j0 = 4 * (tid & 7);
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 8
-    for (int r = 0; r < R; ++r) {
-      const float x = vs[r][i];
+    // the block's partial of U = V'^T S': thread -> rows 4iq..4iq+3 x columns 4jq..4jq+3 of
+    // U over the block rows rs, rs + 4, ...; the four row splits (lanes xor 8, 16) are added
+    const int jq = tid & 7, rs = (tid >> 3) & 3, iq = tid >> 5;
+    float uacc[4][4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] = fmaf(x, ss[r][j0 + q], acc[q]);
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) uacc[a][c] = 0.f;
+#pragma unroll 4
+    for (int r = rs; r < R; r += 4)
+      tc_fma4x4(uacc, *reinterpret_cast<const float4*>(&vs[r][4 * iq]),
+                *reinterpret_cast<const float4*>(&ss[r][4 * jq]));
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        uacc[a][c] += __shfl_xor_sync(0xffffffffu, uacc[a][c], 8);
+        uacc[a][c] += __shfl_xor_sync(0xffffffffu, uacc[a][c], 16);
+      }
+    if (rs == 0) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+        *reinterpret_cast<float4*>(part_t + (size_t)blockIdx.x * KP * KP + (4 * iq + a) * KP + 4 * jq) =
+            make_float4(uacc[a][0], uacc[a][1], uacc[a][2], uacc[a][3]);
     }
-    *reinterpret_cast<float4*>(part_t + (size_t)blockIdx.x * KP * KP + i * KP + j0) =
-        make_float4(acc[0], acc[1], acc[2], acc[3]);
   }
   stamp(1);
   if (!grid_barrier(u.bar, u.bar_target, u.dflag, &ok_s)) return;
