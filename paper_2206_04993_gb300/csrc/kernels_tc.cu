@@ -511,9 +511,15 @@ __global__ void __launch_bounds__(256, 2) k_tc_update_fused(const TcUpdArgs u) {
   const float* vv = vvs + slot * k;
   float* nsum = nrm + slot * k;    // column sums of v'^2 of this update (zero on entry)
   float* part_t = u.part;          // [nblk][KP * KP]
+  const bool on = lane < k;
+  const int64_t c0 = (int64_t)blockIdx.x * R;
+  constexpr int U = 16;
+  float v[U], sv[U], av[U], bv[U];
   {
-    // a and G staged in shared memory (vs and ss are free until phase 1): every load in
-    // flight before the first store
+    // a and G staged in shared memory (vs and ss are free until phase 1). Their loads go
+    // first, then phase 1's rows (16 per warp), whose latency overlaps the coefficients'
+    // setup (V, S and the Adam moments are not written by the products; AV and BV are
+    // complete at launch).
     float* As = &vs[0][0];
     float* Gm = &ss[0][0];
     float xa[4], xg[4];
@@ -525,6 +531,16 @@ __global__ void __launch_bounds__(256, 2) k_tc_update_fused(const TcUpdArgs u) {
     }
     const float xb = tid < k ? __ldcg(bt + tid) : 0.f;
     const float xv = tid < k ? __ldcg(vv + tid) : 0.f;
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const int r = wid + 8 * q;
+      const int64_t g = (c0 + r) * k + lane;
+      const bool ok = on && c0 + r < u.d;
+      v[q] = ok ? u.V[g] : 0.f;  // plain load: this launch rewrites V
+      sv[q] = ok ? u.S[g] : 0.f;
+      av[q] = ok ? __ldcg(u.AV + g) : 0.f;
+      bv[q] = ok ? __ldcg(u.BV + g) : 0.f;
+    }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int p = tid + 256 * q;
@@ -559,23 +575,10 @@ __global__ void __launch_bounds__(256, 2) k_tc_update_fused(const TcUpdArgs u) {
     }
     __syncthreads();
   }
-  // ---- phase 1: 16 rows per warp, all loads in flight at once -----------------
-  const bool on = lane < k;
-  const int64_t c0 = (int64_t)blockIdx.x * R;
+  stamp(3);
+  // ---- phase 1 (rows loaded above) ---------------------------------------------
   float nr = 0.f;
   {
-    constexpr int U = 16;
-    float v[U], sv[U], av[U], bv[U];
-#pragma unroll
-    for (int q = 0; q < U; ++q) {
-      const int r = wid + 8 * q;
-      const int64_t g = (c0 + r) * k + lane;
-      const bool ok = on && c0 + r < u.d;
-      v[q] = ok ? u.V[g] : 0.f;  // plain load: this launch rewrites V
-      sv[q] = ok ? u.S[g] : 0.f;
-      av[q] = ok ? __ldcg(u.AV + g) : 0.f;
-      bv[q] = ok ? __ldcg(u.BV + g) : 0.f;
-    }
     float am[kVar ? U : 1], as2[kVar ? U : 1];  // Adam moments of the rows
     if constexpr (kVar) {
 #pragma unroll
@@ -618,6 +621,7 @@ __global__ void __launch_bounds__(256, 2) k_tc_update_fused(const TcUpdArgs u) {
             make_float4(pacc[a][0], pacc[a][1], pacc[a][2], pacc[a][3]);
     }
     __syncthreads();
+    stamp(4);
 #pragma unroll
     for (int q = 0; q < U; ++q) {
       const int r = wid + 8 * q;
@@ -646,6 +650,7 @@ __global__ void __launch_bounds__(256, 2) k_tc_update_fused(const TcUpdArgs u) {
       nr = fmaf(vn, vn, nr);
     }
   }
+  stamp(6);
   red[wid][lane] = nr;
   __syncthreads();
   if (tid < k) {
@@ -653,6 +658,7 @@ __global__ void __launch_bounds__(256, 2) k_tc_update_fused(const TcUpdArgs u) {
     for (int w = 0; w < 8; ++w) s2 += red[w][tid];
     atomicAdd(nsum + tid, s2);
   }
+  stamp(7);
   {
     // the block's partial of U = V'^T S': thread -> rows 4iq..4iq+3 x columns 4jq..4jq+3 of
     // U over the block rows rs, rs + 4, ...; the four row splits (lanes xor 8, 16) are added
@@ -683,6 +689,17 @@ __global__ void __launch_bounds__(256, 2) k_tc_update_fused(const TcUpdArgs u) {
   stamp(1);
   if (!grid_barrier(u.bar, u.bar_target, u.dflag, &ok_s)) return;
   stamp(2);
+  // this block's entries [e0, e0 + ne) of U: the first entry of each warp has its partials
+  // (lanes over the first 256 blocks) in flight together with the norms
+  const int per = (KP * KP + nblk - 1) / nblk;
+  const int e0 = (int)blockIdx.x * per;
+  const int ne = max(0, min(per, KP * KP - e0));
+  float x0[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int blk = lane + 32 * q;
+    x0[q] = (wid < ne && blk < nblk) ? __ldcg(part_t + (size_t)blk * KP * KP + e0 + wid) : 0.f;
+  }
   if (blockIdx.x == 0) {  // every block has read a, b and z: clear a, b and next update's sums
     for (int p = tid; p < kk; p += 256) a[p] = 0.f;
     if (tid < k) {
@@ -711,29 +728,41 @@ __global__ void __launch_bounds__(256, 2) k_tc_update_fused(const TcUpdArgs u) {
   }
   if (bad) atomicOr(u.dflag, kFlagNonFinite);
   __syncthreads();
-  // transposed BF16 pairs: thread -> (operand row n, two consecutive rows of V)
-  for (int e = tid; e < 2 * KP * (R / 2); e += 256) {
-    const int n = e / (R / 2), rp = 2 * (e % (R / 2));
+  // transposed BF16 pairs: thread -> (four operand rows 4nq..4nq+3, two consecutive rows
+  // of V), one float4 of each V row (operand rows n < KP: hi parts of column n; n >= KP:
+  // lo parts of column n - KP)
+  for (int e = tid; e < (2 * KP / 4) * (R / 2); e += 256) {
+    const int nq = e / (R / 2), rp = 2 * (e % (R / 2));
     if (c0 + rp >= u.d) continue;  // d is even: rp + 1 < d as well
-    const float v0 = vs[rp][n % KP], v1 = vs[rp + 1][n % KP];
-    __nv_bfloat162 w;
-    if (n < KP) {
-      w = __floats2bfloat162_rn(v0, v1);
-    } else {
-      const float h0 = __bfloat162float(__float2bfloat16(v0)), h1 = __bfloat162float(__float2bfloat16(v1));
-      w = __floats2bfloat162_rn(v0 - h0, v1 - h1);
+    const float4 x4 = *reinterpret_cast<const float4*>(&vs[rp][4 * (nq % (KP / 4))]);
+    const float4 y4 = *reinterpret_cast<const float4*>(&vs[rp + 1][4 * (nq % (KP / 4))]);
+    const float xs4[4] = {x4.x, x4.y, x4.z, x4.w}, ys4[4] = {y4.x, y4.y, y4.z, y4.w};
+    const bool lo = nq >= KP / 4;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const float v0 = xs4[c], v1 = ys4[c];
+      __nv_bfloat162 w;
+      if (!lo) {
+        w = __floats2bfloat162_rn(v0, v1);
+      } else {
+        const float h0 = __bfloat162float(__float2bfloat16(v0)), h1 = __bfloat162float(__float2bfloat16(v1));
+        w = __floats2bfloat162_rn(v0 - h0, v1 - h1);
+      }
+      *reinterpret_cast<__nv_bfloat162*>(u.Vt + (int64_t)(4 * nq + c) * u.d + c0 + rp) = w;
     }
-    *reinterpret_cast<__nv_bfloat162*>(u.Vt + (int64_t)n * u.d + c0 + rp) = w;
   }
   // entries [j per, (j + 1) per) of U over all blocks -> the next step's G and |v|^2
   {
-    const int per = (KP * KP + nblk - 1) / nblk;
-    const int e0 = (int)blockIdx.x * per;
-    const int ne = max(0, min(per, KP * KP - e0));
     float* Gn = Gs + (1 - slot) * kk;
     for (int el = wid; el < ne; el += 8) {  // warp per entry, lanes over the blocks
       float s2 = 0.f;
-      for (int blk0 = lane; blk0 < nblk; blk0 += 256) {
+      int blk_start = lane;
+      if (el == wid) {  // partials of the first 256 blocks already loaded
+#pragma unroll
+        for (int q = 0; q < 8; ++q) s2 += x0[q];
+        blk_start = lane + 256;
+      }
+      for (int blk0 = blk_start; blk0 < nblk; blk0 += 256) {
         float x[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
@@ -1358,9 +1387,9 @@ void tc_update_trace_report(Ctx& c) {
   unsigned long long g0 = ~0ull;
   for (int b = 0; b < n; ++b) g0 = std::min(g0, t[(size_t)b * 8]);
   std::fprintf(stderr, "[sgep trace] fused update, %d blocks (us from first start, median/max):", n);
-  const char* names[4] = {"start", "phase1", "barrier", "end"};
-  const int ev[4] = {0, 1, 2, 5};
-  for (int ph = 0; ph < 4; ++ph) {
+  const char* names[8] = {"start", "coefficients", "penalty", "rows", "norms", "phase1", "barrier", "end"};
+  const int ev[8] = {0, 3, 4, 6, 7, 1, 2, 5};
+  for (int ph = 0; ph < 8; ++ph) {
     std::vector<double> v;
     for (int b = 0; b < n; ++b) v.push_back((t[(size_t)b * 8 + ev[ph]] - g0) / 1e3);
     std::sort(v.begin(), v.end());
