@@ -57,9 +57,14 @@ constexpr int kBpRingSmem = kBpRing * (kBpRows * kBpZS + 2 * kBpRows * kWS);
 // double-buffered.
 constexpr int kProjectSmem = cmax(cmax(kProjCols * kProjXS + 2 * kProjCols * kWS, kRedFloats), kProjRingSmem);
 constexpr int kBackprojectSmem = cmax(cmax(kBpRows * kBpZS + 4 * kBpRows * kWS, kRedFloats), kBpRingSmem);
-__host__ __device__ constexpr int gram_smem(int k) { return 3 * 32 * k; }
+// k x k terms: four staged 32-row chunks (V, AV, S, BV) of row stride ceil(k/4)*4 + 4, or the
+// split partials of one k x k matrix, whichever is larger.
+__host__ __device__ constexpr int gram_smem(int k) {
+  return 4 * 32 * (((k + 3) / 4) * 4 + 4) > kThreads * 16 ? 4 * 32 * (((k + 3) / 4) * 4 + 4) : kThreads * 16;
+}
+constexpr int kUpdRows = 4;  // rows per thread per iteration of the update tile
 __host__ __device__ constexpr int update_smem(int k) {
-  return k * k + 4 * k + (kThreads / k > 1 ? kThreads / k : 1) * k;
+  return k * k + 4 * k + kUpdRows * (kThreads / k > 1 ? kThreads / k : 1) * k;
 }
 __host__ __device__ constexpr int lda_stats_smem(int C) { return C * kThreads + kThreads; }
 constexpr int kLdaWSmem = kMaxClasses * 33 + 32 * (kMaxK + 1);
@@ -693,65 +698,99 @@ __device__ void backproject_tile(const T* __restrict__ X, const T* __restrict__ 
 // k x k terms: a_ij = sum_c V[c,i] AV[c,j];  G_ij = sum_c V[c,i] S[c,j];
 //              b_i = sum_c V[c,i] (B_t V)[c,i] with B_t V = BV + eps V (or (1+eps) V when B = I).
 // gram layout: [a (k*k) | G (k*k) | b (k) | norms (k)]; must be zeroed. Grid-stride
-// over 32-row chunks of V: tile `bx` of `nb`.
+// over 32-row chunks of V: tile `bx` of `nb`. Each chunk's rows of V, AV, S and BV are
+// staged (players padded to a multiple of 4 with zeros); a thread owns a 4 x 4 block
+// (players 4iq.., 4jq..) of both a and G over the rows of its split, so one float4 of V,
+// of AV and of S feed 32 FMAs. The splits' partials are added in shared memory, then one
+// atomic per entry.
 __device__ inline void gram_tile(const float* __restrict__ V, const float* __restrict__ S,
                                  const float* __restrict__ AV, const float* __restrict__ BV, int64_t d, int k,
                                  float eps_B, int b_is_identity, float* __restrict__ gram, int bx, int nb,
                                  float* smem) {
   constexpr int CR = 32;
-  float* Vs = smem;             // CR x k
-  float* As = Vs + CR * k;      // CR x k
-  float* Ss = As + CR * k;      // CR x k
+  const int kp = (k + 3) & ~3, nq = kp >> 2;
+  const int gs = kp + 4;         // staged row stride
+  float* Vs = smem;              // CR x gs
+  float* As = Vs + CR * gs;
+  float* Ss = As + CR * gs;
+  float* Bs = Ss + CR * gs;
   const int tid = threadIdx.x;
   const int kk = k * k;
-  float ga[kMaxK * kMaxK / kThreads], gg[kMaxK * kMaxK / kThreads];
+  const int tiles = nq * nq;
+  const int splits = min(kThreads / tiles, CR);
+  const int t = tid % tiles, sp = tid / tiles;
+  const bool active = sp < splits;
+  const int iq = t / nq, jq = t % nq;
+  const int si = tid % 64, sr = tid / 64;  // staging: player si of rows sr + 4u
+  float acc_a[4][4], acc_g[4][4];
 #pragma unroll
-  for (int q = 0; q < kMaxK * kMaxK / kThreads; ++q) ga[q] = gg[q] = 0.f;
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) acc_a[x][y] = acc_g[x][y] = 0.f;
   float gb = 0.f;
+  __syncthreads();  // the workspace may still be read by this block's previous tile
   for (int64_t c0 = (int64_t)bx * CR; c0 < d; c0 += (int64_t)nb * CR) {
     const int nr = (int)min((int64_t)CR, d - c0);
-    for (int e = tid; e < CR * k; e += kThreads) {
-      const int rr = e / k;
-      const bool ok = rr < nr;
-      const int64_t idx = c0 * k + e;
-      Vs[e] = ok ? V[idx] : 0.f;
-      As[e] = ok ? AV[idx] : 0.f;
-      Ss[e] = ok ? S[idx] : 0.f;
+    if (si < kp) {
+      float xv[CR / 4], xa[CR / 4], xs[CR / 4], xb[CR / 4];
+#pragma unroll
+      for (int u = 0; u < CR / 4; ++u) {
+        const int rr = sr + 4 * u;
+        const bool ok = si < k && rr < nr;
+        const int64_t idx = (c0 + rr) * k + si;
+        xv[u] = ok ? V[idx] : 0.f;
+        xa[u] = ok ? AV[idx] : 0.f;
+        xs[u] = ok ? S[idx] : 0.f;
+        xb[u] = (ok && !b_is_identity) ? BV[idx] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < CR / 4; ++u) {
+        const int o = (sr + 4 * u) * gs + si;
+        Vs[o] = xv[u];
+        As[o] = xa[u];
+        Ss[o] = xs[u];
+        Bs[o] = xb[u];
+      }
     }
     __syncthreads();
-#pragma unroll
-    for (int q = 0; q < kMaxK * kMaxK / kThreads; ++q) {
-      const int p = tid + q * kThreads;
-      if (p < kk) {
-        const int i = p / k, j = p % k;
-        float sa = 0.f, sg = 0.f;
-        for (int rr = 0; rr < nr; ++rr) {
-          const float v = Vs[rr * k + i];
-          sa = fmaf(v, As[rr * k + j], sa);
-          sg = fmaf(v, Ss[rr * k + j], sg);
-        }
-        ga[q] += sa;
-        gg[q] += sg;
+    if (active) {
+      for (int rr = sp; rr < nr; rr += splits) {
+        const float4 v4 = lds4(Vs + rr * gs + 4 * iq);
+        fma4x4(acc_a, v4, lds4(As + rr * gs + 4 * jq));
+        fma4x4(acc_g, v4, lds4(Ss + rr * gs + 4 * jq));
       }
     }
     if (tid < k) {
       float sb = 0.f;
       for (int rr = 0; rr < nr; ++rr) {
-        const float v = Vs[rr * k + tid];
-        const float bv = b_is_identity ? (1.f + eps_B) * v : BV[(c0 + rr) * k + tid] + eps_B * v;
+        const float v = Vs[rr * gs + tid];
+        const float bv = b_is_identity ? (1.f + eps_B) * v : Bs[rr * gs + tid] + eps_B * v;
         sb = fmaf(v, bv, sb);
       }
       gb += sb;
     }
     __syncthreads();
   }
+  // add the splits' partials of a, then of G (red aliases the staging buffers)
+  float* red = smem;  // [splits][kp][kp]
 #pragma unroll
-  for (int q = 0; q < kMaxK * kMaxK / kThreads; ++q) {
-    const int p = tid + q * kThreads;
-    if (p < kk) {
-      atomicAdd(&gram[p], ga[q]);
-      atomicAdd(&gram[kk + p], gg[q]);
+  for (int m = 0; m < 2; ++m) {
+    if (active) {
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        const float* src = m == 0 ? acc_a[x] : acc_g[x];
+        *reinterpret_cast<float4*>(red + (sp * kp + 4 * iq + x) * kp + 4 * jq) =
+            make_float4(src[0], src[1], src[2], src[3]);
+      }
     }
+    __syncthreads();
+    for (int p = tid; p < kk; p += kThreads) {
+      const int i = p / k, j = p % k;
+      float sum = 0.f;
+      for (int s2 = 0; s2 < splits; ++s2) sum += red[(s2 * kp + i) * kp + j];
+      atomicAdd(&gram[m * kk + p], sum);
+    }
+    __syncthreads();
   }
   if (tid < k) atomicAdd(&gram[2 * kk + tid], gb);
 }
@@ -770,7 +809,7 @@ __device__ inline void update_tile(const float* __restrict__ V, float* __restric
   float* nrm = cac + k;          // k
   float* sden = nrm + k;         // k: Alg. 3 denominators
   const int rows = max(1, kThreads / k);
-  float* Ss = sden + k;          // rows x k
+  float* Ss = sden + k;          // kUpdRows * rows x k
   if (var.z) {
     for (int j = threadIdx.x; j < k; j += blockDim.x) sden[j] = smooth_den(var.z[j], var.log_rho, var.log_nu);
     __syncthreads();
@@ -782,31 +821,50 @@ __device__ inline void update_tile(const float* __restrict__ V, float* __restric
   const int rl = tid / k, i = tid % k;
   const bool active = rl < rows;
   float my_norm = 0.f;
-  for (int64_t c0 = (int64_t)bx * rows; c0 < d; c0 += (int64_t)nb * rows) {
-    const int64_t c = c0 + rl;
-    const bool ok = active && c < d;
-    const int64_t idx = c * k + i;
-    const float s_old = ok ? S[idx] : 0.f;
-    if (active) Ss[rl * k + i] = s_old;
+  // kUpdRows rows per thread per iteration (rows rl + rows u), every load in flight at once
+  const int64_t span = (int64_t)rows * kUpdRows;
+  for (int64_t c0 = (int64_t)bx * span; c0 < d; c0 += (int64_t)nb * span) {
+    float xs[kUpdRows], xv[kUpdRows], xa[kUpdRows], xb[kUpdRows];
+#pragma unroll
+    for (int u = 0; u < kUpdRows; ++u) {
+      const int64_t c = c0 + rl + (int64_t)rows * u;
+      const bool ok = active && c < d;
+      const int64_t idx = c * k + i;
+      xs[u] = ok ? S[idx] : 0.f;
+      xv[u] = ok ? V[idx] : 0.f;
+      xa[u] = ok ? AV[idx] : 0.f;
+      xb[u] = (ok && !b_is_identity) ? BV[idx] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < kUpdRows; ++u)
+      if (active) Ss[(rl + rows * u) * k + i] = xs[u];
     __syncthreads();
-    if (ok) {
-      const float v = V[idx];
-      const float bv = b_is_identity ? (1.f + eps_B) * v : BV[idx] + eps_B * v;
-      float pen = 0.f;
-      for (int j = 0; j < i; ++j) pen = fmaf(Ss[rl * k + j], T[j * k + i], pen);
-      const float gr = cb[i] * AV[idx] - cac[i] * bv - pen;
-      float step = gr;
-      if (var.m) {  // Adam on the players
-        float m = var.m[idx], s2 = var.s[idx];
-        step = adam_increment(gr, m, s2, var.b1, var.b2, var.eps, var.bc1, var.bc2);
-        var.m[idx] = m;
-        var.s[idx] = s2;
+#pragma unroll
+    for (int u = 0; u < kUpdRows; ++u) {
+      const int64_t c = c0 + rl + (int64_t)rows * u;
+      const bool ok = active && c < d;
+      const int64_t idx = c * k + i;
+      const float s_old = xs[u];
+      const int srow = (rl + rows * u) * k;
+      if (ok) {
+        const float v = xv[u];
+        const float bv = b_is_identity ? (1.f + eps_B) * v : xb[u] + eps_B * v;
+        float pen = 0.f;
+        for (int j = 0; j < i; ++j) pen = fmaf(Ss[srow + j], T[j * k + i], pen);
+        const float gr = cb[i] * xa[u] - cac[i] * bv - pen;
+        float step = gr;
+        if (var.m) {  // Adam on the players
+          float m = var.m[idx], s2 = var.s[idx];
+          step = adam_increment(gr, m, s2, var.b1, var.b2, var.eps, var.bc1, var.bc2);
+          var.m[idx] = m;
+          var.s[idx] = s2;
+        }
+        const float vn = fmaf(eta, step, v);
+        Vtmp[idx] = vn;
+        S[idx] = fmaf(gamma, bv - s_old, s_old);
+        if (grad_out) grad_out[idx] = gr;
+        my_norm = fmaf(vn, vn, my_norm);
       }
-      const float vn = fmaf(eta, step, v);
-      Vtmp[idx] = vn;
-      S[idx] = fmaf(gamma, bv - s_old, s_old);
-      if (grad_out) grad_out[idx] = gr;
-      my_norm = fmaf(vn, vn, my_norm);
     }
     __syncthreads();
   }

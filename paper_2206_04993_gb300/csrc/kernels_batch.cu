@@ -65,7 +65,8 @@ using gt::kThreads;
 constexpr int kSmemFloats = gt::cmax(32 * kThreads + kThreads, gt::kBackprojectSmem);
 static_assert(kSmemFloats >= gt::kBackprojectSmem && kSmemFloats >= gt::kProjectSmem &&
                   kSmemFloats >= gt::gram_smem(64) &&
-                  kSmemFloats >= gt::update_smem(1) && kSmemFloats >= gt::kLdaWSmem,
+                  kSmemFloats >= gt::update_smem(1) && kSmemFloats >= gt::update_smem(gt::kMaxK) &&
+                  kSmemFloats >= gt::kLdaWSmem,
               "batch workspace");
 
 __device__ int find_instance(const InstDesc* inst, int n, int phase, int item) {
@@ -315,9 +316,9 @@ static void partition(const BatchCtx& B, const Ctx& c, int64_t b, InstDesc& D) {
   D.stats_items = lda ? (int)((c.d + kThreads - 1) / kThreads) : 0;
   D.ldaw_items = lda ? (int)std::max<int64_t>(1, std::min<int64_t>((c.d + 31) / 32, 16)) : 0;
   D.ldaav_items = lda ? (int)std::max<int64_t>(1, std::min<int64_t>((c.d * c.k + kThreads - 1) / kThreads, 32)) : 0;
-  D.gram_items = (int)std::max<int64_t>(1, std::min<int64_t>((c.d + 31) / 32, 16));
-  const int rows = std::max(1, kThreads / c.k);
-  D.upd_items = (int)std::max<int64_t>(1, std::min<int64_t>((c.d + rows - 1) / rows, 32));
+  D.gram_items = (int)std::max<int64_t>(1, std::min<int64_t>((c.d + 31) / 32, 32));
+  const int64_t span = (int64_t)std::max(1, kThreads / c.k) * gt::kUpdRows;
+  D.upd_items = (int)std::max<int64_t>(1, std::min<int64_t>((c.d + span - 1) / span, 32));
   D.norm_items = (int)std::max<int64_t>(1, std::min<int64_t>((c.d * c.k + kThreads - 1) / kThreads, 32));
   D.items[0] = D.zero_items + (lda ? 1 : 0);
   D.items[1] = D.stats_items;

@@ -318,7 +318,8 @@ int generic_update(Ctx& c, float eta, float gamma, cudaStream_t s) {
                                         c.b_is_identity ? 1 : 0, c.gram);
   SGEP_CUDA_TRY(cudaGetLastError());
   const int rows = std::max(1, kThreads / k);
-  const int ublocks = (int)std::min<int64_t>((c.d + rows - 1) / rows, grid_cap(c, 4));
+  const int64_t span = (int64_t)rows * gt::kUpdRows;
+  const int ublocks = (int)std::min<int64_t>((c.d + span - 1) / span, grid_cap(c, 4));
   const size_t usm = sizeof(float) * gt::update_smem(k);
   const UpdVariant var = next_variant(c);
   k_update<<<ublocks, kThreads, usm, s>>>(c.V, c.S, AV, BV, c.gram, c.d, k, eta, gamma, c.cfg.rho,
