@@ -79,6 +79,20 @@ def test_single_step_matches_oracle(kind, dx, dy, k, b, path):
         assert e <= STEP_TOL, (name, e, err)
 
 
+@pytest.mark.parametrize("kind,dx,dy,k,b", [("cca", 2048, 2048, 8, 8192), ("cca", 2046, 2050, 7, 8192),
+                                             ("pls", 2048, 1024, 12, 8192)])
+def test_generic_ring_many_stages_matches_oracle(kind, dx, dy, k, b):
+    """Many row tiles make the projection take 1024-column chunks (32 stages of the cp.async
+    ring, which wraps its slots eight times) and the back-projection ~50-stage row splits;
+    row pitches that are and are not a multiple of 4 take the 16-byte and 4-byte copies."""
+    X, Y = _data(kind, dx, dy, b, seed=dx + k)
+    V0, S0 = _state(dx + dy, k, seed=k, kind=kind)
+    with _solver(kind, dx, dy, k, S.SGEP_PATH_GENERIC, eta0=0.3, gamma0=0.4, rho=1e-3, max_b=b) as s:
+        err = step_errors(s, V0, S0, X, Y, kind, 0.3, 0.4, 1e-3)
+    for name, e in err.items():
+        assert e <= STEP_TOL, (name, e, err)
+
+
 @pytest.mark.parametrize("path", PATHS, ids=["generic", "cluster"])
 def test_single_step_shared_batch_and_ridge(path):
     X, Y = _data("cca", 48, 40, 200, seed=3)
