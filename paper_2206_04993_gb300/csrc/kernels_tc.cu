@@ -520,14 +520,27 @@ __global__ void __launch_bounds__(256, 2) k_tc_update_fused(const TcUpdArgs u) {
     // first, then phase 1's rows (16 per warp), whose latency overlaps the coefficients'
     // setup (V, S and the Adam moments are not written by the products; AV and BV are
     // complete at launch).
-    float* As = &vs[0][0];
-    float* Gm = &ss[0][0];
+    // Every block reads the same a and G, so their loads are as few and as wide as possible
+    // (one float4 of each per thread when aligned: these hot lines are request-bound in L2).
+    // Both are staged transposed (At[j k + i] = a_ij), so the reads below that walk a row of
+    // a or G across the lanes (lane = i) hit consecutive banks.
+    float* At = &vs[0][0];
+    float* Gt = &ss[0][0];
+    const bool vec = (kk % 4 == 0) && ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(G)) & 15) == 0;
     float xa[4], xg[4];
+    if (vec) {
+      const bool in = 4 * tid < kk;
+      const float4 a4 = in ? __ldcg(reinterpret_cast<const float4*>(a) + tid) : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 g4 = in ? __ldcg(reinterpret_cast<const float4*>(G) + tid) : make_float4(0.f, 0.f, 0.f, 0.f);
+      xa[0] = a4.x, xa[1] = a4.y, xa[2] = a4.z, xa[3] = a4.w;
+      xg[0] = g4.x, xg[1] = g4.y, xg[2] = g4.z, xg[3] = g4.w;
+    } else {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int p = tid + 256 * q;
-      xa[q] = p < kk ? __ldcg(a + p) : 0.f;
-      xg[q] = p < kk ? __ldcg(G + p) : 0.f;
+      for (int q = 0; q < 4; ++q) {
+        const int p = tid + 256 * q;
+        xa[q] = p < kk ? __ldcg(a + p) : 0.f;
+        xg[q] = p < kk ? __ldcg(G + p) : 0.f;
+      }
     }
     const float xb = tid < k ? __ldcg(bt + tid) : 0.f;
     const float xv = tid < k ? __ldcg(vv + tid) : 0.f;
@@ -543,33 +556,35 @@ __global__ void __launch_bounds__(256, 2) k_tc_update_fused(const TcUpdArgs u) {
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int p = tid + 256 * q;
+      const int p = vec ? 4 * tid + q : tid + 256 * q;  // element p = i k + j of a and G
       if (p < kk) {
-        As[p] = xa[q];
-        Gm[p] = xg[q];
+        const int t = (p % k) * k + p / k;
+        At[t] = xa[q];
+        Gt[t] = xg[q];
       }
     }
     if (tid < k) cb[tid] = fmaf(u.eps_B, xv, xb);
     __syncthreads();
     if (tid < k) {
-      gdiag[tid] = Gm[tid * k + tid];  // <v_i, [Bv]_i> of step t (Alg. 3's z step)
+      gdiag[tid] = Gt[tid * k + tid];  // <v_i, [Bv]_i> of step t (Alg. 3's z step)
       inv_s[tid] = 1.f / ((kVar && u.var.z) ? smooth_den(u.var.z[tid], u.var.log_rho, u.var.log_nu)
-                                            : fmaxf(Gm[tid * k + tid], u.rho));
+                                            : fmaxf(Gt[tid * k + tid], u.rho));
     }
     __syncthreads();
     for (int p = tid; p < KP * KP; p += 256) {  // zero outside k x k: read by the micro-tiles
       const int j = p / KP, i = p % KP;
-      T[p] = (i < k && j < i) ? cb[i] * As[i * k + j] * inv_s[j] : 0.f;
+      T[p] = (i < k && j < i) ? cb[i] * At[j * k + i] * inv_s[j] : 0.f;
     }
     if (tid < k) {
       float c = 0.f;
-      for (int j = 0; j < tid; ++j) c = fmaf(As[tid * k + j] * Gm[tid * k + j], inv_s[j], c);
-      cac[tid] = As[tid * k + tid] - c;
+      for (int j = 0; j < tid; ++j) c = fmaf(At[j * k + tid] * Gt[j * k + tid], inv_s[j], c);
+      cac[tid] = At[tid * k + tid] - c;
     }
-    if (blockIdx.x == 0 && u.dbg) {  // the terms as used (debug)
+    if (blockIdx.x == 0 && u.dbg) {  // the terms as used (debug), untransposed
       for (int p = tid; p < kk; p += 256) {
-        u.dbg[p] = As[p];
-        u.dbg[kk + p] = Gm[p];
+        const int t = (p % k) * k + p / k;
+        u.dbg[p] = At[t];
+        u.dbg[kk + p] = Gt[t];
       }
       if (tid < k) u.dbg[2 * kk + tid] = xb;
     }
