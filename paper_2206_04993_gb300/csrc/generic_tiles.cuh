@@ -66,7 +66,8 @@ constexpr int kUpdRows = 4;  // rows per thread per iteration of the update tile
 __host__ __device__ constexpr int update_smem(int k) {
   return k * k + 4 * k + kUpdRows * (kThreads / k > 1 ? kThreads / k : 1) * k;
 }
-__host__ __device__ constexpr int lda_stats_smem(int C) { return C * kThreads + kThreads; }
+constexpr int kStatsRows = 16;  // rows per cp.async block of the LDA statistics (FP32 rows)
+__host__ __device__ constexpr int lda_stats_smem(int C) { return C * kThreads + kThreads + 2 * kStatsRows * kThreads; }
 constexpr int kLdaWSmem = kMaxClasses * 33 + 32 * (kMaxK + 1);
 constexpr int kLdaAvSmem = kMaxClasses * kMaxK;
 constexpr int kLdaCountsSmem = kMaxClasses + 2;  // histogram + a double
@@ -933,6 +934,7 @@ __device__ void lda_stats_tile(const T* __restrict__ X, const float* __restrict_
                                float* __restrict__ M, int bx, float* smem) {
   float* acc = smem;                                             // [C][kThreads]
   int* labs = reinterpret_cast<int*>(smem + C * kThreads);       // [kThreads]
+  float* xs = smem + C * kThreads + kThreads;                    // [2][kStatsRows][kThreads]
   const int tid = threadIdx.x;
   const int64_t col = (int64_t)bx * kThreads + tid;
   for (int c = 0; c < C; ++c) acc[c * kThreads + tid] = 0.f;
@@ -943,7 +945,40 @@ __device__ void lda_stats_tile(const T* __restrict__ X, const float* __restrict_
     labs[tid] = (unsigned)lab < (unsigned)C ? lab : -1;  // bad labels are flagged by the counts tile
     __syncthreads();
     const int nr = (int)min((int64_t)kThreads, b - r0);
-    if (col < d) {
+    if (col >= d) continue;
+    if constexpr (std::is_same<T, float>::value) {
+      if (!rs) {
+        // Plain FP32 rows: each thread stages its own column in blocks of kStatsRows rows by
+        // cp.async (double-buffered), so the loads of a block are in flight together and
+        // ahead of the additions (no barrier: a thread reads only what it copied).
+        const float* xcol = X + col;
+        auto issue = [&](int s0, int buf) {
+#pragma unroll
+          for (int q = 0; q < kStatsRows; ++q) {
+            const bool ok = s0 + q < nr;
+            cp_async4(xs + (buf * kStatsRows + q) * kThreads + tid, ok ? xcol + (r0 + s0 + q) * d : xcol, ok);
+          }
+          cp_async_commit_all();
+        };
+        issue(0, 0);
+        int buf = 0;
+        for (int s0 = 0; s0 < nr; s0 += kStatsRows, buf ^= 1) {
+          if (s0 + kStatsRows < nr) {
+            issue(s0 + kStatsRows, buf ^ 1);
+            cp_async_wait_pending<1>();
+          } else {
+            cp_async_wait_all();
+          }
+#pragma unroll
+          for (int q = 0; q < kStatsRows; ++q) {
+            const int lab2 = (s0 + q < nr) ? labs[s0 + q] : -1;
+            if (lab2 >= 0) acc[lab2 * kThreads + tid] += xs[(buf * kStatsRows + q) * kThreads + tid];
+          }
+        }
+        continue;
+      }
+    }
+    {
       for (int q0 = 0; q0 < nr; q0 += 8) {
         float x[8];
 #pragma unroll

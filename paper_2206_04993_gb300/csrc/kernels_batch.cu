@@ -62,7 +62,7 @@ namespace {
 
 using gt::kThreads;
 // the largest tile workspace: the back-projection's, or the LDA statistics' (C = 32)
-constexpr int kSmemFloats = gt::cmax(32 * kThreads + kThreads, gt::kBackprojectSmem);
+constexpr int kSmemFloats = gt::cmax(gt::lda_stats_smem(kMaxClasses), gt::kBackprojectSmem);
 static_assert(kSmemFloats >= gt::kBackprojectSmem && kSmemFloats >= gt::kProjectSmem &&
                   kSmemFloats >= gt::gram_smem(64) &&
                   kSmemFloats >= gt::update_smem(1) && kSmemFloats >= gt::update_smem(gt::kMaxK) &&

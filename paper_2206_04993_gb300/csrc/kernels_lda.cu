@@ -87,7 +87,12 @@ static int stats(Ctx& c, const void* X, const int32_t* labels, int64_t b, cudaSt
   k_lda_counts<<<1, kThreads, 0, s>>>(labels, b, C, c.lda_cnt, c.lda_pi, c.dflag);
   SGEP_CUDA_TRY(cudaGetLastError());
   const unsigned grid = (unsigned)((c.d + kThreads - 1) / kThreads);
-  const size_t smem = (size_t)gt::lda_stats_smem(C) * sizeof(float);
+  const size_t smem = (size_t)gt::lda_stats_smem(C) * sizeof(float);  // above 48 KB for C >= 16
+  SGEP_CUDA_TRY(cudaFuncSetAttribute(k_lda_stats<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  SGEP_CUDA_TRY(
+      cudaFuncSetAttribute(k_lda_stats<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  SGEP_CUDA_TRY(
+      cudaFuncSetAttribute(k_lda_stats<__nv_fp8_e4m3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   if (c.cfg.dtype == SGEP_BF16)
     k_lda_stats<__nv_bfloat16><<<grid, kThreads, smem, s>>>((const __nv_bfloat16*)X, sx, labels, b, c.d, C,
                                                             c.lda_sum, c.lda_cnt, c.lda_mean, c.lda_M);
