@@ -29,9 +29,10 @@ constexpr int kMaxK = 64;
 // float4 of weights per 16 FMAs. The k players form ceil(k/4) player quads; the threads
 // left after one thread per (data quad, player quad) split the contraction dimension, and
 // their partial sums are added in shared memory before one atomic per output. The next
-// stage's loads are issued before the current stage is computed: the data rows (any element
+// stage's loads are written before the current stage is computed: the data rows (any element
 // type, centred or scaled) into registers, the FP32 weights by cp.async into the other half
-// of a double buffer (zero-filled where masked).
+// of a double buffer (zero-filled where masked). The compiler may still issue a register load
+// next to its use, so plain FP32 rows take the cp.async ring below instead.
 constexpr int kPad = 4;
 constexpr int kWS = kMaxK + kPad;  // staged row stride of V, P and Q (floats)
 constexpr int kProjRows = 64;      // rows of one projection tile
