@@ -110,6 +110,9 @@ def test_clipping_floor_scales_penalty(rng):
     reward = np.sum(V * BV, 0) * AV - np.sum(V * AV, 0) * BV
     pen1 = reward - p1["grad"]
     pen2 = reward - p2["grad"]
+    # finite and present: without the floor the denominators would be square roots of -1
+    assert np.all(np.isfinite(pen1)) and np.all(np.isfinite(pen2))
+    assert np.abs(pen1[:, 1:]).max() > 1e-3 * np.abs(reward).max()
     np.testing.assert_allclose(pen1[:, 0], 0.0, atol=1e-13)   # player 1 has no parents
     np.testing.assert_allclose(pen1[:, 1:], 2.0 * pen2[:, 1:], rtol=1e-10, atol=1e-12)
 
