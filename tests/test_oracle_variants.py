@@ -108,6 +108,30 @@ def test_adam_without_momentum_repeats_the_normalised_step(rng):
     np.testing.assert_allclose(V2, Vp / np.linalg.norm(Vp, axis=0), atol=1e-13)
 
 
+def test_adam_trajectory_equals_a_library_adam(rng):
+    """Six chained Adam steps equal torch.optim.Adam (the textbook recursion, run on the CPU in
+    FP64) given the same update directions (negated: torch descends) and the same retraction:
+    momentum decay, bias correction over t and the epsilon's place all have to match."""
+    torch = pytest.importorskip("torch")
+    X, Y, V, S = _problem(rng)
+    Amv, Bmv = eg.cca_ops(X, Y)
+    eta, gamma, rho, b1, b2, eps = 0.05, 0.4, 1e-4, 0.8, 0.95, 1e-3
+    p = torch.nn.Parameter(torch.tensor(V, dtype=torch.float64))
+    opt = torch.optim.Adam([p], lr=eta, betas=(b1, b2), eps=eps)
+    ad = _adam(*V.shape, b1=b1, b2=b2, eps=eps)
+    Vo, So = V.copy(), S.copy()
+    for _ in range(6):
+        _, _, parts = eg.eg_step(Vo, So, Amv, Bmv, eta, gamma, rho, return_parts=True)
+        p.grad = torch.tensor(-parts["grad"], dtype=torch.float64)
+        opt.step()
+        with torch.no_grad():
+            p /= p.norm(dim=0, keepdim=True)
+        Vo, So, st = eg.eg_step_variant(Vo, So, Amv, Bmv, eta, gamma, rho, adam=ad)
+        ad = st["adam"]
+        np.testing.assert_allclose(Vo, p.detach().numpy(), atol=1e-12)
+    assert ad["t"] == 6
+
+
 def test_adam_keeps_the_solution(rng):
     """App. C fixed point: with exact A, B and [Bv] = B v the update direction is zero (up to
     rounding, which Adam scales by at most 1/eps), so Adam moves neither the players nor its
