@@ -78,6 +78,38 @@ def test_init_rejects_shape_and_schedule_mismatch():
     assert L.sgep_init(ctypes.byref(cfg), ctypes.byref(h)) == S.SGEP_EINVAL
 
 
+@pytest.mark.parametrize("fields,why", [
+    ({"optimizer": 7}, "optimizer"),
+    ({"optimizer": S.SGEP_OPT_ADAM, "adam_b1": 1.0}, "Adam"),
+    ({"optimizer": S.SGEP_OPT_ADAM, "adam_b2": -0.1}, "Adam"),
+    ({"optimizer": S.SGEP_OPT_ADAM, "adam_eps": float("inf")}, "Adam"),
+    ({"variant": 5}, "variant"),
+    ({"variant": S.SGEP_ALG3, "nu": float("inf")}, "nu"),
+    ({"center": 2}, "center"),
+])
+def test_init_rejects_bad_variant_config_before_touching_the_gpu(fields, why):
+    """Adam (App. H.2.2), Alg. 3 (App. E.2) and running-mean centring settings are checked
+    before any device work, each with its own message."""
+    cfg = S.sgep_config_default(d_x=8, d_y=8, k=2)
+    for name, value in fields.items():
+        setattr(cfg, name, value)
+    h = ctypes.c_void_p()
+    assert S.lib().sgep_init(ctypes.byref(cfg), ctypes.byref(h)) == S.SGEP_EINVAL and h.value is None
+    assert why in S.sgep_last_error(), S.sgep_last_error()
+
+
+def test_init_rejects_variant_and_kind_combinations():
+    L = S.lib()
+    h = ctypes.c_void_p()
+    cfg = S.sgep_config_default(d_x=8, d_y=8, k=2, variant=S.SGEP_ALG3)
+    cfg.nu = cfg.rho  # Alg. 3 interpolates between rho and nu > rho
+    assert L.sgep_init(ctypes.byref(cfg), ctypes.byref(h)) == S.SGEP_EINVAL
+    cfg = S.sgep_config_default(kind=S.SGEP_ICA, d_x=8, d_y=4, k=2)  # ICA has one view
+    assert L.sgep_init(ctypes.byref(cfg), ctypes.byref(h)) == S.SGEP_EINVAL
+    cfg = S.sgep_config_default(kind=S.SGEP_LDA, d_x=8, d_y=0, k=2, n_classes=3, center=1)
+    assert L.sgep_init(ctypes.byref(cfg), ctypes.byref(h)) == S.SGEP_EINVAL  # LDA centres by class
+
+
 def test_init_without_gpu_fails_cleanly():
     import torch
     if torch.cuda.is_available():
