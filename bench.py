@@ -289,6 +289,18 @@ def oracle_rate(cfg, seconds: float):
     return steps * b / el, steps, el
 
 
+def fma_roofline(b, d, k, ms, n_sms, sm_mhz, split=True):
+    """FP32 FMA-rate roofline of the SIMT contractions: the projection does k FMAs per
+    element, the back-projection k with split A/B batches (every row feeds one estimate) or 2k
+    without; the peak is n_sms x 128 FP32 FMA per clock at the SM clock."""
+    fma = b * d * k * (2 if split else 3)
+    peak = n_sms * 128 * sm_mhz * 1e6 / 1e12
+    achieved = fma / (ms / 1e3) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFMA/s", "frac": achieved / peak,
+            "fma_per_step": fma, "kernel": "generic projection + back-projection (whole step)",
+            "peak_source": f"{n_sms} SMs x 128 FP32 FMA/clock x {sm_mhz:.0f} MHz"}
+
+
 def measure_throughput(workload, steps, warmup, dev, rank=0, path=0):
     """Samples/s and roofline of one workload with its rows resident in HBM."""
     import torch
@@ -329,6 +341,14 @@ def measure_throughput(workload, steps, warmup, dev, rank=0, path=0):
                         "frac": alg / (ms / 1e3) / 1e9 / peak, "traffic": None,
                         "kernel": "whole step", "peak_source": peak_kind, "alg_bytes_per_launch": alg},
            "clocks": clk.summary()}
+    if dtype == "f32" and solver.path == sgep.SGEP_PATH_GENERIC:  # SIMT contractions: FMA-bound
+        try:
+            mhz = out["clocks"].get("sm_max_mhz") or out["clocks"].get("sm_mhz")
+            sms = torch.cuda.get_device_properties(dev).multi_processor_count
+            if mhz:
+                out["fma_roofline"] = fma_roofline(b, d, k, ms, sms, float(mhz))
+        except Exception:  # an extra figure: never costs the measurement
+            pass
     solver.close()
     del X, Y
     torch.cuda.empty_cache()
