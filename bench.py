@@ -1,10 +1,12 @@
 """Benchmark of the gamma-EigenGame step (Alg. 2) on GB300.
 
-Default workload: plain CCA in FP32, d_x = d_y = 512 (d = 1024), k = 16 players,
-minibatch b = 1024, rows from the planted model with 32 latent directions
-(canonical correlations 0.95..0.3). A pool of 1,000,000 rows (4 GB) is generated on
+Default workload: activation-like CCA, d_x = d_y = 16384 (d = 32768), k = 32 players,
+minibatch b = 4096 rows in BF16 (268 MB per minibatch), power-law noise spectrum with 64
+planted shared directions. A pool of 32,768 rows (8 minibatches, 2.1 GB) is generated on
 the device before timing; timed steps stream consecutive minibatches through it, so the
-inputs exceed L2 and every step reads fresh rows from HBM.
+inputs exceed L2 and every step reads fresh rows from HBM. The other workloads (the
+1024-dim FP32 CCA with its time-to-1e-3 runs, the FP32 form of the large problem, the
+batching form, the learned warm start) are reported under `forms`.
 
 One JSON line is printed (rank 0). `value` is samples/s of the whole job with inputs
 resident in HBM; `e2e` is the same metric through the C ABI with the minibatch copied
@@ -41,20 +43,21 @@ WORKLOADS = {
     "cca_d32768_k32_b4096_bf16": ("config_c3", "bf16", 32_768),
     "cca_d32768_k32_b4096_f32": ("config_c3", "f32", 16_384),
 }
-DEFAULT_WORKLOAD = "cca_d1024_k16_b1024_f32"
+DEFAULT_WORKLOAD = "cca_d32768_k32_b4096_bf16"
+TTE_WORKLOAD = "cca_d1024_k16_b1024_f32"
 
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=2000)
+    p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=20)
     p.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     p.add_argument("--impl", default="native", choices=["native", "reference"])
     p.add_argument("--path", type=int, default=0, help="0 auto, 1 generic, 2 cluster, 3 tc")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--pool-rows", type=int, default=0, help="override the resident row pool")
     p.add_argument("--no-tte", action="store_true", help="skip the time-to-1e-3 measurements")
     p.add_argument("--no-forms", action="store_true", help="skip the BF16 tensor-core and batching workloads")
@@ -89,13 +92,32 @@ def dist_env():
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 
+def gpu_selector(dev) -> str:
+    """The nvidia-smi `-i` argument of the GPU behind torch device `dev`: its UUID (CUDA
+    ordinals are relative to CUDA_VISIBLE_DEVICES, nvidia-smi indices are not)."""
+    import torch
+    idx = torch.device(dev).index or 0
+    try:
+        u = str(torch.cuda.get_device_properties(idx).uuid)
+        if u:
+            return u if u.startswith(("GPU-", "MIG-")) else "GPU-" + u
+    except Exception:
+        pass
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [x.strip() for x in vis.split(",") if x.strip()]
+        if idx < len(ids):
+            return ids[idx]
+    return str(idx)
+
+
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
-        self.idx = gpu_index
+    def __init__(self, dev):
+        self.idx = gpu_selector(dev)
         self.proc = None
         self.f = None
 
@@ -138,7 +160,7 @@ class ClockSampler:
         reasons = sorted({names[j] for r in rows for j in range(4) if r[5 + j].lower() == "active"})
         return {"sm_mhz": float(np.median(sm)) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(rows), "gpu": self.idx}
 
 
 def measured_peaks():
@@ -269,18 +291,19 @@ def time_to_error(make_solver, X, Y, b, truth, target=1e-3, every=500, max_steps
 
 def oracle_rate(cfg, seconds: float):
     """Samples/s of the oracle's Alg. 2 step (FP64, numpy, streamed operators) on
-    minibatches of the workload, over about `seconds` of work."""
+    minibatches of the workload, over about `seconds` of work (at least two steps)."""
     from oracle import eg
     model = cfg["model"]
     b, k = cfg["b"], cfg["k"]
     d = model.d_x + model.d_y
     V = synth.random_unit_columns(d, k, seed=0)
     S = V.copy()
-    batches = [synth.draw_rows(model, b, batch=i) for i in range(4)]
+    nbat = 4 if b * d <= 1 << 24 else 2  # two FP64 minibatches (2.1 GB) at the 32768-dim size
+    batches = [synth.draw_rows(model, b, batch=i) for i in range(nbat)]
     steps = 0
     t0 = time.perf_counter()
     while True:
-        X, Y = batches[steps % 4]
+        X, Y = batches[steps % nbat]
         V, S = eg.eg_step(V, S, *eg.cca_ops(X, Y), cfg["eta0"], cfg["gamma0"], cfg["rho"])
         steps += 1
         el = time.perf_counter() - t0
@@ -289,16 +312,30 @@ def oracle_rate(cfg, seconds: float):
     return steps * b / el, steps, el
 
 
-def fma_roofline(b, d, k, ms, n_sms, sm_mhz, split=True):
+def line_config(workload: str, pool_rows: int, world: int) -> dict:
+    """The `config` block of the JSON line; both arms print the same one."""
+    cfg = getattr(synth, WORKLOADS[workload][0])()
+    model = cfg["model"]
+    return {"workload": workload, "d_x": model.d_x, "d_y": model.d_y, "k": cfg["k"], "b": cfg["b"],
+            "dtype": WORKLOADS[workload][1], "pool_rows": pool_rows,
+            "l2": "inputs larger than L2 (pool streamed)", "parallelism": f"replicas{world}"}
+
+
+def fma_roofline(b, d, k, ms, n_sms, sm_mhz, sm_max_mhz=None, split=True):
     """FP32 FMA-rate roofline of the SIMT contractions: the projection does k FMAs per
     element, the back-projection k with split A/B batches (every row feeds one estimate) or 2k
-    without; the peak is n_sms x 128 FP32 FMA per clock at the SM clock."""
+    without; the peak is n_sms x 128 FP32 FMA per clock at the SM clock sampled during the
+    timed region (the rated maximum is reported beside it)."""
     fma = b * d * k * (2 if split else 3)
     peak = n_sms * 128 * sm_mhz * 1e6 / 1e12
     achieved = fma / (ms / 1e3) / 1e12
-    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFMA/s", "frac": achieved / peak,
-            "fma_per_step": fma, "kernel": "generic projection + back-projection (whole step)",
-            "peak_source": f"{n_sms} SMs x 128 FP32 FMA/clock x {sm_mhz:.0f} MHz"}
+    out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFMA/s", "frac": achieved / peak,
+           "fma_per_step": fma, "kernel": "generic projection + back-projection (whole step)",
+           "peak_source": f"{n_sms} SMs x 128 FP32 FMA/clock x {sm_mhz:.0f} MHz (median sampled SM clock)"}
+    if sm_max_mhz:
+        pmax = n_sms * 128 * sm_max_mhz * 1e6 / 1e12
+        out["at_rated_max_clock"] = {"peak": pmax, "frac": achieved / pmax, "sm_mhz": sm_max_mhz}
+    return out
 
 
 def measure_throughput(workload, steps, warmup, dev, rank=0, path=0):
@@ -324,7 +361,7 @@ def measure_throughput(workload, steps, warmup, dev, rank=0, path=0):
     torch.cuda.synchronize()
     l0 = solver.launches
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(torch.cuda.current_device()) as clk:
+    with ClockSampler(dev) as clk:
         e0.record()
         for i in range(steps):
             j = (warmup + i) % nb
@@ -343,10 +380,10 @@ def measure_throughput(workload, steps, warmup, dev, rank=0, path=0):
            "clocks": clk.summary()}
     if dtype == "f32" and solver.path == sgep.SGEP_PATH_GENERIC:  # SIMT contractions: FMA-bound
         try:
-            mhz = out["clocks"].get("sm_max_mhz") or out["clocks"].get("sm_mhz")
+            mhz = out["clocks"].get("sm_mhz") or out["clocks"].get("sm_max_mhz")
             sms = torch.cuda.get_device_properties(dev).multi_processor_count
             if mhz:
-                out["fma_roofline"] = fma_roofline(b, d, k, ms, sms, float(mhz))
+                out["fma_roofline"] = fma_roofline(b, d, k, ms, sms, float(mhz), out["clocks"].get("sm_max_mhz"))
         except Exception:  # an extra figure: never costs the measurement
             pass
     solver.close()
@@ -582,6 +619,47 @@ def measure_warm(dev, seed=0, n_train=128, n_eval=16, max_steps=8000, check_ever
     return out
 
 
+def measure_tte(dev, rank, args):
+    """Time to 1e-3 generalized subspace error on the 1024-dim FP32 workload (1,000,000-row
+    resident pool), plain FP32 rows against the same rows in BF16, three initial V each."""
+    import torch
+    from paper_2206_04993_gb300 import Solver, sgep
+    name, _, pool_rows = WORKLOADS[TTE_WORKLOAD]
+    cfg = getattr(synth, name)(seed=rank)
+    model = cfg["model"]
+    b, k = cfg["b"], cfg["k"]
+    dx, dy = model.d_x, model.d_y
+    X, Y = make_pool(cfg, pool_rows, "f32", dev, seed=rank)
+    truth = pool_truth(X, Y, k)
+
+    def mk(dt):
+        return lambda: Solver(kind=sgep.SGEP_CCA, d_x=dx, d_y=dy, k=k,
+                              dtype=sgep.SGEP_BF16 if dt == "bf16" else sgep.SGEP_F32,
+                              eta0=cfg["eta0"], gamma0=cfg["gamma0"], rho=cfg["rho"],
+                              schedule=cfg["schedule"], t_c=cfg["t_c"], T=cfg["T"],
+                              eta_T=cfg["eta_T"], max_b=b, path=args.path, seed=rank)
+
+    def median_runs(fn):
+        runs = [fn(seed) for seed in (1, 2, 3)]
+        secs = sorted(r["seconds"] if r["reached"] else float("inf") for r in runs)
+        steps = sorted(r["steps"] if r["reached"] else 10 ** 12 for r in runs)
+        return {"median_seconds": secs[1], "median_steps": steps[1] if steps[1] < 10 ** 12 else None,
+                "reached": sum(r["reached"] for r in runs), "runs": [
+                    {kk: r[kk] for kk in ("reached", "steps", "seconds", "final_error")} for r in runs],
+                "curve_seed1": runs[0]["curve"]}
+    tte = {"workload": TTE_WORKLOAD,
+           "truth": "scipy eigh of the pool's FP64 covariances (the paper's ground truth, Sec. 5)",
+           "seeds": "initial V from seeds 1, 2, 3; median reported; device time of the steps only",
+           "plain_f32": median_runs(lambda sd: time_to_error(mk("f32"), X, Y, b, truth, every=1000,
+                                                             max_steps=args.tte_max_steps, seed=sd))}
+    Xb, Yb = X.to(torch.bfloat16), Y.to(torch.bfloat16)
+    tte["bf16"] = median_runs(lambda sd: time_to_error(mk("bf16"), Xb, Yb, b, truth, every=1000,
+                                                       max_steps=args.tte_max_steps, seed=sd))
+    del X, Y, Xb, Yb
+    torch.cuda.empty_cache()
+    return tte
+
+
 def cpu_cores():
     for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         if os.environ.get(var):
@@ -593,16 +671,19 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    cfg = getattr(synth, WORKLOADS[args.workload][0])()
-    # a bounded sample: about 0.05 s of oracle work per requested step, 3 s to 100 s in total
-    rate, steps, el = oracle_rate(cfg, min(100.0, max(3.0, 0.05 * args.steps)))
-    sample = f"{steps} oracle steps of b={cfg['b']} rows ({el:.1f} s), FP64 numpy"
+    name, _, pool_rows = WORKLOADS[args.workload]
+    if args.pool_rows:
+        pool_rows = args.pool_rows
+    cfg = getattr(synth, name)()
+    # a bounded sample: about 0.5 s of oracle work per requested step, 5 s to 60 s in total
+    rate, steps, el = oracle_rate(cfg, min(60.0, max(5.0, 0.5 * args.steps)))
+    sample = f"{steps} oracle steps of b={cfg['b']} rows ({el:.1f} s), FP64 numpy, streamed operators"
     line = {
         "impl": "reference", "metric": METRIC, "value": rate, "unit": "samples/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * el / steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic planted CCA",
-        "config": {"workload": args.workload},
+        "config": line_config(args.workload, pool_rows, world),
         "cpu_baseline": {"value": rate, "unit": "samples/s", "cores": cpu_cores(), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": rate, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -658,7 +739,7 @@ def run_native(args):
         torch.distributed.barrier()
     launches0 = solver.launches
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(torch.cuda.current_device()) as clk:
+    with ClockSampler(dev) as clk:
         torch.cuda.synchronize()
         ev0.record(stream)
         pos = run_steps(pos, args.steps)
@@ -716,45 +797,23 @@ def run_native(args):
         cpu = {"value": rate, "unit": "samples/s", "cores": cpu_cores(), "kind": "oracle",
                "sample": f"{steps} FP64 oracle steps of b={b} ({el:.1f} s) on this workload"}
 
-    tte = None
-    if rank == 0 and not args.no_tte and args.workload == DEFAULT_WORKLOAD:
-        truth = pool_truth(X, Y, k)
-
-        def mk(dt):
-            return lambda: Solver(kind=sgep.SGEP_CCA, d_x=dx, d_y=dy, k=k,
-                                  dtype=sgep.SGEP_BF16 if dt == "bf16" else sgep.SGEP_F32,
-                                  eta0=cfg["eta0"], gamma0=cfg["gamma0"], rho=cfg["rho"],
-                                  schedule=cfg["schedule"], t_c=cfg["t_c"], T=cfg["T"],
-                                  eta_T=cfg["eta_T"], max_b=b, path=args.path, seed=rank)
-        def median_runs(fn):
-            runs = [fn(seed) for seed in (1, 2, 3)]
-            secs = sorted(r["seconds"] if r["reached"] else float("inf") for r in runs)
-            steps = sorted(r["steps"] if r["reached"] else 10 ** 12 for r in runs)
-            return {"median_seconds": secs[1], "median_steps": steps[1] if steps[1] < 10 ** 12 else None,
-                    "reached": sum(r["reached"] for r in runs), "runs": [
-                        {kk: r[kk] for kk in ("reached", "steps", "seconds", "final_error")} for r in runs],
-                    "curve_seed1": runs[0]["curve"]}
-        tte = {"truth": "scipy eigh of the pool's FP64 covariances (the paper's ground truth, Sec. 5)",
-               "seeds": "initial V from seeds 1, 2, 3; median reported; device time of the steps only",
-               "plain_f32": median_runs(lambda sd: time_to_error(mk("f32"), X, Y, b, truth, every=1000,
-                                                                 max_steps=args.tte_max_steps, seed=sd))}
-        Xb, Yb = X.to(torch.bfloat16), Y.to(torch.bfloat16)
-        tte["bf16"] = median_runs(lambda sd: time_to_error(mk("bf16"), Xb, Yb, b, truth, every=1000,
-                                                           max_steps=args.tte_max_steps, seed=sd))
-        del Xb, Yb
-
     forms = None
-    if rank == 0 and not args.no_forms and args.workload == DEFAULT_WORKLOAD:
+    if rank == 0 and not args.no_forms:
         del X, Y
         torch.cuda.empty_cache()
-        forms = {"cca_d32768_k32_b4096_bf16": measure_throughput("cca_d32768_k32_b4096_bf16", 60, 5, dev, rank),
-                 # the plain FP32 form of the same problem (generic SIMT path; no FP32 tensor-core path)
-                 "cca_d32768_k32_b4096_f32": measure_throughput("cca_d32768_k32_b4096_f32", 8, 2, dev, rank),
-                 "batch64_cca_lda_b512_f32": measure_batch("f32", 40, 3, dev, seed=rank),
-                 "batch64_cca_lda_b512_bf16": measure_batch("bf16", 40, 3, dev, seed=rank),
-                 "warm_start_cca_family": measure_warm(dev, seed=rank)}
-        forms["bf16_vs_f32_step_speedup_d32768"] = (forms["cca_d32768_k32_b4096_f32"]["ms_per_step"] /
-                                                    forms["cca_d32768_k32_b4096_bf16"]["ms_per_step"])
+        forms = {}
+        if args.workload != TTE_WORKLOAD:
+            forms[TTE_WORKLOAD] = measure_throughput(TTE_WORKLOAD, 2000, 20, dev, rank)
+        if not args.no_tte:
+            forms[TTE_WORKLOAD + "_time_to_1e-3"] = measure_tte(dev, rank, args)
+        if args.workload != "cca_d32768_k32_b4096_f32":
+            # the plain FP32 form of the same problem
+            forms["cca_d32768_k32_b4096_f32"] = measure_throughput("cca_d32768_k32_b4096_f32", 8, 3, dev, rank)
+        if args.workload == "cca_d32768_k32_b4096_bf16":
+            forms["bf16_vs_f32_step_speedup_d32768"] = forms["cca_d32768_k32_b4096_f32"]["ms_per_step"] / ms_step
+        forms["batch64_cca_lda_b512_f32"] = measure_batch("f32", 40, 3, dev, seed=rank)
+        forms["batch64_cca_lda_b512_bf16"] = measure_batch("bf16", 40, 3, dev, seed=rank)
+        forms["warm_start_cca_family"] = measure_warm(dev, seed=rank)
 
     if rank == 0:
         line = {
@@ -762,11 +821,9 @@ def run_native(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": dtype, "data": "synthetic planted CCA generated on device",
-            "config": {"workload": args.workload, "d_x": dx, "d_y": dy, "k": k, "b": b,
-                       "pool_rows": pool_rows, "l2": "inputs larger than L2 (pool streamed)",
-                       "parallelism": f"replicas{world}", "path": solver.path},
+            "config": line_config(args.workload, pool_rows, world), "path": solver.path,
             "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "clocks": clk.summary(), "time_to_1e-3": tte, "forms": forms,
+            "clocks": clk.summary(), "forms": forms,
         }
         print(json.dumps(line), flush=True)
     solver.close()

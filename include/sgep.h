@@ -132,6 +132,13 @@ typedef struct {
                        /* (App. H.2.2 "mean estimates are learned"; the pencils of Sec. 1     */
                        /* assume zero-mean data). PCA, CCA, PLS on the generic path. A step   */
                        /* adds its rows to the running sums first, then centres them.         */
+  int32_t  machines;   /* M of Alg. 2 (default 1): the b rows of a step form M consecutive      */
+                       /* shards of b / M rows (the last takes the remainder); each shard is a  */
+                       /* machine's minibatch with its own A/B split, its update direction and  */
+                       /* auxiliary increment B_tm v_i - [Bv]_i are averaged over the machines   */
+                       /* before the player and auxiliary steps. M > 1: CCA, PCA, PLS on the     */
+                       /* generic path, Alg. 2's plain step (no Adam, Alg. 3 or centring).       */
+  int32_t  reserved0;  /* must be 0 */
 } sgep_config;
 
 /* Fill `cfg` with defaults: CCA, F32, k = 1, eta0 = 0.1, gamma0 = 1, rho = 1e-6,
@@ -224,6 +231,20 @@ int sgep_get_eigenvalues(sgep_t h, const void* X, const void* Y, const float* ro
 int sgep_rayleigh_ritz(sgep_t h, const void* X, const void* Y, const float* row_scale_x,
                        const float* row_scale_y, const int32_t* labels, int64_t n,
                        double* lambda_out, void* stream);
+
+/* Periodic Rayleigh-Ritz correction (precision form): after every step whose count
+ * t (sgep_step_count) is a multiple of `every`, sgep_step and sgep_step_many apply
+ * sgep_rayleigh_ritz on the evaluation rows given here (same meaning and layout as
+ * its arguments; device pointers owned by the caller, which must keep them valid and
+ * unchanged while the schedule is set). The correction is the Ritz step of App. A
+ * (Prop. "Similar matrices") on the span of the players, taken every `every` steps of
+ * Alg. 2; sgep_step_many splits its launches at those steps. every = 0 removes the
+ * schedule (the pointers may then be NULL). The corrections run on the step's stream
+ * and synchronise it. Errors: SGEP_EINVAL (every < 0, NULL rows or labels when
+ * needed, n < 1, bad scales), SGEP_ENOTSUP (ICA). A correction that finds V^T B V not
+ * positive definite makes the step report SGEP_ENONFINITE (V and [Bv] unchanged). */
+int sgep_set_rr_every(sgep_t h, int64_t every, const void* X, const void* Y, const float* row_scale_x,
+                      const float* row_scale_y, const int32_t* labels, int64_t n);
 
 /* ---- batching form ------------------------------------------------------
  * Many independent problems (uneven kind, d_x, d_y, k, element type) advanced

@@ -12,6 +12,8 @@ Test infrastructure only (see the package header).
 * `eg_step_variant` adds the two variants of the paper: Adam on the players with the
   warm-up / harmonic schedule (App. H.2.2) and the smooth denominators of Alg. 3
   (App. E.2, extra scalars z_i).
+* `eg_step_machines` is Alg. 2 with M > 1 machines: per-machine update directions and
+  auxiliary increments from each machine's own minibatch estimates, averaged.
 * `alg1_step` is the deterministic variant (Alg. 1) with exact A and B.
 * `utility` is Eq. util_new; `schedule_eta` is the warm-up plus harmonic decay
   of App. H.2.2.
@@ -256,6 +258,28 @@ def eg_step(V: np.ndarray, S: np.ndarray, Amv, Bmv, eta: float, gamma: float,
     if return_parts:
         return V_next, S_next, {"AV": AV, "BV": BV, "grad": grad}
     return V_next, S_next
+
+
+def eg_step_machines(V: np.ndarray, S: np.ndarray, machine_ops, eta: float, gamma: float, rho: float):
+    """One iteration of Alg. 2 with M = len(machine_ops) machines.
+
+    Machine m holds its own minibatch estimates (A_tm, B_tm) (the operators of its shard) and
+    forms, from the shared state of step t, the update direction grad_im of every player
+    (rewards minus penalties, Eq. update) and the auxiliary increment B_tm v_i - [Bv]_i; both
+    are averaged over the machines, then the player step with the retraction and the
+    auxiliary step follow, as Alg. 2 writes them. Returns (V_next, S_next).
+    """
+    V = np.asarray(V, dtype=np.float64)
+    S = np.asarray(S, dtype=np.float64)
+    M = len(machine_ops)
+    grad = np.zeros_like(V)
+    inc = np.zeros_like(S)
+    for Amv, Bmv in machine_ops:
+        _, _, parts = eg_step(V, S, Amv, Bmv, 0.0, 0.0, rho, return_parts=True)
+        grad += parts["grad"] / M
+        inc += (parts["BV"] - S) / M
+    Vp = V + eta * grad
+    return Vp / np.linalg.norm(Vp, axis=0, keepdims=True), S + gamma * inc
 
 
 def smooth_denominator(z: np.ndarray, rho: float, nu: float) -> np.ndarray:

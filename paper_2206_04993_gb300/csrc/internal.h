@@ -82,11 +82,6 @@ struct Ctx {
   __nv_bfloat16* tc_Qt = nullptr;
   float* tc_coef = nullptr;        // k*k + 2k update coefficients
   int tc_generic_step = 0;         // the last step's shape needed the generic products
-  void* tc_fused_buf = nullptr;    // counters of the one-read products kernel
-  size_t tc_fused_bytes = 0;
-  unsigned long long* tc_trace = nullptr;  // SGEP_TRACE=1: per-row-block event times of the one-read kernel
-  int tc_trace_grid = 0, tc_trace_nrb = 0;
-  float* tc_fused_rep = nullptr;   // replicas of the row projections (one-read kernel)
   float* tc_dbg = nullptr;         // a | G | b used by the last tensor-core update (debug)
   unsigned long long* tc_bar = nullptr;  // grid-barrier arrivals of the fused update
   float* tc_part = nullptr;              // its per-block partial sums
@@ -95,19 +90,19 @@ struct Ctx {
   int tc_upd_fused = 0;            // the fused update fits on the device (all blocks resident)
   int tc_chain = 0;                // the last update prepared this step's V operand and d-side terms
   int tc_bar_reset = 0;            // the barrier count must be cleared before the next launch
-  int tc_fused_dirty = 0;          // the replicas must be cleared before the next launch
   size_t tc_smem_p = 0, tc_smem_b = 0;
   // one-read streamed products (kernels_tc_stream.cu)
   int tc_st_ok = 0;                // the streamed kernel is set up for this handle
   unsigned* tc_st_cnt = nullptr;   // [max_b / 128] contributions, then [max_b / 128] operand-ready flags
-  unsigned tc_st_epoch = 0;        // launches since the counters were last cleared
+  unsigned tc_st_epoch = 0;        // streamed steps since the counters were last cleared
   int tc_st_reset = 0;             // clear the counters (and the row sums) before the next launch
   int tc_pq_dirty = 0;             // P and Q hold values another kernel left behind
   unsigned long long* tc_st_trace = nullptr;  // SGEP_TRACE=1: per-CTA, per-chunk event times
   int tc_st_nchunk = 0;            // chunks of the most recent streamed launch
   int tc_st_grid = 0;              // its CTAs (streaming + builder helpers)
   int tc_st_lag = 5, tc_st_helpers = 24;  // tuning knobs (SGEP_TC_LAG, SGEP_TC_HELPERS)
-  int tc_st_fuse = 1;              // the streamed launch also applies the update (SGEP_TC_STREAM_UPDATE)
+  float* tc_st_terms = nullptr;    // [3] row-side term slots a | b, then [3] slots |v'|^2 | U
+  unsigned tc_st_launch = 0;       // streamed launches since the counters were last cleared
   int tc_st_updated = 0;           // the most recent streamed launch applied the step's update
   int64_t tc_st_last_b = 0;        // minibatch size the counters were last used with
   int tc_acc_stale = 0;            // acc does not hold the last step's products (not kept)
@@ -120,8 +115,17 @@ struct Ctx {
   float* lda_pi = nullptr;    // C priors n_c / n
   float* lda_W = nullptr;     // C x k: (mu_c - mu)^T V
   double* rr_buf = nullptr;   // Rayleigh-Ritz: k x k sums, C, eigenvalues, norms (FP64)
+  int64_t rr_every = 0;       // periodic Rayleigh-Ritz: every this many steps (0: none)
+  const void* rr_X = nullptr; // its evaluation rows (caller-owned device memory)
+  const void* rr_Y = nullptr;
+  const float* rr_sx = nullptr;
+  const float* rr_sy = nullptr;
+  const int32_t* rr_labels = nullptr;
+  int64_t rr_n = 0;
 
   int64_t t = 0;       // iterations applied (Alg. 2's t)
+  float* mach_buf = nullptr;  // machines > 1: 3 x d x k (V' sum, [Bv]' sum, [Bv] copy)
+  int test_stall = 0;   // SGEP_TEST_STALL=1 at init: the fused update's grid barrier never completes
   int64_t launches = 0; // kernels launched
   int debug_valid = 0; // sgep_debug_update has data
 };
@@ -157,6 +161,10 @@ int generic_products(Ctx& c, const void* X, const void* Y, int64_t b, cudaStream
                      const float* sx = nullptr, const float* sy = nullptr);
 // Update from acc: grams, update, retraction. eta/gamma of this step.
 int generic_update(Ctx& c, float eta, float gamma, cudaStream_t s);
+// One step of Alg. 2 with cfg.machines shards of the b rows: per-shard products, update
+// directions and auxiliary increments, averaged over the shards before the steps.
+int generic_machines_step(Ctx& c, const void* X, const void* Y, int64_t b, cudaStream_t s, const float* sx,
+                          const float* sy, float eta, float gamma);
 // Row projections of n rows into PQ (n <= max_b), zeroing PQ first.
 // sx, sy: per-row scales of FP8 rows (null otherwise); center/labels: LDA centring.
 int generic_project(Ctx& c, const void* X, const void* Y, int64_t n, cudaStream_t s,
@@ -235,19 +243,17 @@ struct TcTerms {
 size_t tc_terms_floats(int k);
 TcTerms tc_terms(const Ctx& c, int slot);
 
-// One-read fused products (kernels_tc_fused.cu).
-bool tc_fused_supported(const Ctx& c, int64_t b);
-int tc_fused_setup(Ctx& c);
-int tc_fused_products(Ctx& c, const CUtensorMap& mX, const CUtensorMap& mY, const CUtensorMap& mX64,
-                      const CUtensorMap& mY64, const CUtensorMap& mVt, int64_t b, cudaStream_t s);
-// One-read streamed products (kernels_tc_stream.cu): acc, and the row-side terms a and b.
+// Streamed tensor-core steps (kernels_tc_stream.cu): products, row-side terms and update.
 bool tc_stream_supported(const Ctx& c, int64_t b);
 int tc_stream_setup(Ctx& c);
 void tc_stream_free(Ctx& c);
-int tc_stream_products(Ctx& c, const CUtensorMap& mX, const CUtensorMap& mY, const CUtensorMap& mX64,
-                       const CUtensorMap& mY64, const CUtensorMap& mVt, const CUtensorMap& mPt,
-                       const CUtensorMap& mQt, float* a_terms, float* b_terms, int64_t b, float eta,
-                       float gamma, cudaStream_t s);
+// nsteps (<= tc_stream_max_steps()) consecutive steps of Alg. 2 in one launch: products,
+// row-side terms and the update of each; X and Y hold nsteps minibatches of b rows.
+int tc_stream_steps(Ctx& c, const void* X, const void* Y, int64_t b, int nsteps, cudaStream_t s);
+int tc_stream_max_steps();
+// V split into BF16 pairs and the d-side terms of slot (c.t & 1), unless the chain of
+// tensor-core steps left them current.
+int tc_prepare_chain(Ctx& c, cudaStream_t s);
 void tc_stream_trace_report(Ctx& c);
 // Update from acc with the k x k terms the tensor-core products accumulated.
 int tc_update(Ctx& c, float eta, float gamma, cudaStream_t s);
@@ -263,8 +269,6 @@ int cluster_step(Ctx& c, const void* X, const void* Y, int64_t b, float eta, flo
 int cluster_flush(Ctx& c, cudaStream_t s);
 // Copy the pending products into acc layout (d x k AV, d x k BV) for debugging.
 int cluster_products(Ctx& c, float* AV, float* BV, cudaStream_t s);
-// SGEP_TRACE=1: print per-row-block event times of the most recent one-read launch to stderr.
-void tc_fused_trace_report(Ctx& c);
 void tc_update_trace_report(Ctx& c);
 // SGEP_TRACE=1: print per-phase times of the most recent cluster launch to stderr.
 void cluster_trace_report(Ctx& c);

@@ -333,6 +333,77 @@ int generic_update(Ctx& c, float eta, float gamma, cudaStream_t s) {
   return SGEP_OK;
 }
 
+// Alg. 2 with M machines: acc_v += inv_m (v_i + eta grad_im) and acc_s += inv_m ([Bv]_i +
+// gamma (B_tm v_i - [Bv]_i)) over the machines m, elementwise (both steps are affine in the
+// machine's quantities, so this is the step with the averaged direction and increment).
+__global__ void k_machine_accumulate(const float* __restrict__ vstep, const float* __restrict__ sstep,
+                                     float* __restrict__ acc_v, float* __restrict__ acc_s, int64_t n, float inv_m) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    acc_v[e] = fmaf(inv_m, vstep[e], acc_v[e]);
+    acc_s[e] = fmaf(inv_m, sstep[e], acc_s[e]);
+  }
+}
+
+// Squared column norms of a d x k matrix, added into out[k] (zero on entry).
+__global__ void k_col_norms(const float* __restrict__ A, int64_t d, int k, float* out) {
+  const int i = threadIdx.x % k, lanes = blockDim.x / k, lr = threadIdx.x / k;
+  if (lr >= lanes) return;
+  float s2 = 0.f;
+  for (int64_t r = (int64_t)blockIdx.x * lanes + lr; r < d; r += (int64_t)gridDim.x * lanes) {
+    const float v = A[r * k + i];
+    s2 = fmaf(v, v, s2);
+  }
+  atomicAdd(out + i, s2);
+}
+
+int generic_machines_step(Ctx& c, const void* X, const void* Y, int64_t b, cudaStream_t s, const float* sx,
+                          const float* sy, float eta, float gamma) {
+  const int M = c.cfg.machines, k = c.k, kk = k * k;
+  const int64_t dk = c.d * k;
+  float* accv = c.mach_buf;
+  float* accs = accv + dk;
+  float* Sm = accs + dk;  // the machine's [Bv] step (k_update steps its S argument in place)
+  const size_t esz = elem_size(c);
+  SGEP_CUDA_TRY(cudaMemsetAsync(accv, 0, 2 * (size_t)dk * sizeof(float), s));
+  const int rows = std::max(1, kThreads / k);
+  const int64_t span = (int64_t)rows * gt::kUpdRows;
+  const int ublocks = (int)std::min<int64_t>((c.d + span - 1) / span, grid_cap(c, 4));
+  const int gblocks = (int)std::min<int64_t>((c.d + 31) / 32, grid_cap(c, 2));
+  const int eblocks = (int)std::min<int64_t>((dk + 255) / 256, grid_cap(c, 4));
+  for (int m = 0; m < M; ++m) {
+    const int64_t r0 = b * m / M, r1 = b * (m + 1) / M;
+    const char* xs = (const char*)X + (size_t)r0 * c.d_x * esz;
+    const char* ys = c.has_y ? (const char*)Y + (size_t)r0 * c.d_y * esz : nullptr;
+    int rc = generic_products(c, xs, ys, r1 - r0, s, sx ? sx + r0 : nullptr, sy ? sy + r0 : nullptr);
+    if (rc) return rc;
+    SGEP_CUDA_TRY(cudaMemsetAsync(c.gram, 0, sizeof(float) * (2 * kk + 2 * k), s));
+    k_gram<<<gblocks, kThreads, sizeof(float) * gt::gram_smem(k), s>>>(c.V, c.S, c.acc, c.acc + dk, c.d, k,
+                                                                       c.cfg.eps_B, c.b_is_identity ? 1 : 0, c.gram);
+    SGEP_CUDA_TRY(cudaGetLastError());
+    SGEP_CUDA_TRY(cudaMemcpyAsync(Sm, c.S, (size_t)dk * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    k_update<<<ublocks, kThreads, sizeof(float) * gt::update_smem(k), s>>>(
+        c.V, Sm, c.acc, c.acc + dk, c.gram, c.d, k, eta, gamma, c.cfg.rho, c.cfg.eps_B, c.b_is_identity ? 1 : 0,
+        c.Vtmp, nullptr, UpdVariant());
+    SGEP_CUDA_TRY(cudaGetLastError());
+    k_machine_accumulate<<<eblocks, 256, 0, s>>>(c.Vtmp, Sm, accv, accs, dk, 1.f / (float)M);
+    SGEP_CUDA_TRY(cudaGetLastError());
+    c.launches += 4;
+  }
+  // [Bv] <- the averaged step; V <- retraction of the averaged player step
+  SGEP_CUDA_TRY(cudaMemcpyAsync(c.S, accs, (size_t)dk * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  float* norms = c.gram + 2 * kk + k;
+  SGEP_CUDA_TRY(cudaMemsetAsync(norms, 0, (size_t)k * sizeof(float), s));
+  const int lanes = std::max(1, 256 / k);
+  k_col_norms<<<(unsigned)std::min<int64_t>((c.d + lanes - 1) / lanes, grid_cap(c, 2)), lanes * k, 0, s>>>(
+      accv, c.d, k, norms);
+  SGEP_CUDA_TRY(cudaGetLastError());
+  k_normalize<<<eblocks, 256, 0, s>>>(accv, c.gram, c.V, c.d, k, c.dflag, UpdVariant(), 0.f);
+  SGEP_CUDA_TRY(cudaGetLastError());
+  c.launches += 2;
+  c.debug_valid = 0;  // the update directions of the shards are not kept
+  return SGEP_OK;
+}
+
 int generic_normalize(Ctx& c, cudaStream_t s) {
   const int nblocks = (int)std::min<int64_t>((c.d * c.k + 255) / 256, grid_cap(c, 4));
   k_normalize<<<nblocks, 256, 0, s>>>(c.Vtmp, c.gram, c.V, c.d, c.k, c.dflag, UpdVariant(), 0.f);

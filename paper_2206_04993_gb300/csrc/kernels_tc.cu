@@ -453,6 +453,7 @@ struct TcUpdArgs {
   float rho, eta, gamma, eps_B;
   unsigned long long* bar;  // grid-barrier arrivals (monotone)
   unsigned long long bar_target;  // arrivals that complete this launch's barrier
+  unsigned long long bar_ns;      // how long a block waits at the barrier before giving up
   int* dflag;
   unsigned long long* trace;  // [grid][8] globaltimer stamps of the phases, or null
   UpdVariant var;             // Adam on the players / Alg. 3 denominators, or plain Alg. 2
@@ -470,12 +471,12 @@ __device__ __forceinline__ void tc_fma4x4(float (&acc)[4][4], const float4 x, co
 
 // Bounded grid barrier: returns false (and flags a timeout) when the wait gives up.
 __device__ __forceinline__ bool grid_barrier(unsigned long long* bar, unsigned long long target, int* flag,
-                                             int* ok_s) {
+                                             int* ok_s, unsigned long long ns) {
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
     atomicAdd(bar, 1ull);
-    *ok_s = tc::spin_until_geq64(bar, target) ? 1 : 0;
+    *ok_s = tc::spin_until_geq64(bar, target, ns) ? 1 : 0;
     if (!*ok_s) atomicOr(flag, kFlagTimeout);
   }
   __syncthreads();
@@ -702,7 +703,7 @@ __global__ void __launch_bounds__(256, 2) k_tc_update_fused(const TcUpdArgs u) {
     }
   }
   stamp(1);
-  if (!grid_barrier(u.bar, u.bar_target, u.dflag, &ok_s)) return;
+  if (!grid_barrier(u.bar, u.bar_target, u.dflag, &ok_s, u.bar_ns)) return;
   stamp(2);
   // this block's entries [e0, e0 + ne) of U: the first entry of each warp has its partials
   // (lanes over the first 256 blocks) in flight together with the norms
@@ -1106,11 +1107,6 @@ int tc_alloc(Ctx& c) {
   SGEP_CUDA_TRY(cudaFuncSetAttribute(k_tc_backproject, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb));
   c.tc_smem_p = sp;
   c.tc_smem_b = sb;
-  // The one-read products kernel is opt-in (SGEP_TC_FUSED=1): on GB300 its cross-CTA
-  // reductions share the memory system with the minibatch stream and it is slower than the
-  // two-pass products.
-  const char* fused = getenv("SGEP_TC_FUSED");
-  if (fused && fused[0] == '1') return tc_fused_setup(c);
   // The streamed one-read kernel is the default where the shape allows it
   // (SGEP_TC_STREAM=0 keeps the two-pass products).
   return tc_stream_setup(c);
@@ -1132,18 +1128,25 @@ void tc_free(Ctx& c) {
   c.tc_part = nullptr;
   cudaFree(c.tc_upd_trace);
   c.tc_upd_trace = nullptr;
-  cudaFree(c.tc_fused_buf);
-  cudaFree(c.tc_fused_rep);
-  c.tc_fused_rep = nullptr;
-  cudaFree(c.tc_trace);
-  c.tc_trace = nullptr;
-  c.tc_fused_buf = nullptr;
   c.tc_Vt = nullptr;
   c.tc_PQ = nullptr;
   c.tc_Pt = c.tc_Qt = nullptr;
 }
 
+int tc_prepare_chain(Ctx& c, cudaStream_t s) {
+  if (c.tc_chain) return SGEP_OK;
+  const TcTerms tt = tc_terms(c, (int)(c.t & 1));
+  SGEP_CUDA_TRY(cudaMemsetAsync(c.gram, 0, tc_terms_floats(c.k) * sizeof(float), s));
+  k_tc_prep_v<<<(unsigned)((c.d + 63) / 64), 256, 0, s>>>(c.V, c.S, c.d, c.k, c.tc_Vt, tt.G, tt.vv);
+  SGEP_CUDA_TRY(cudaGetLastError());
+  ++c.launches;
+  c.tc_chain = 1;
+  return SGEP_OK;
+}
+
 int tc_products(Ctx& c, const void* X, const void* Y, int64_t b, cudaStream_t s, float eta, float gamma) {
+  (void)eta;
+  (void)gamma;
   const int split = c.cfg.split_AB ? 1 : 0;
   const int64_t nA = split ? b / 2 : b;
   c.tc_st_updated = 0;
@@ -1158,40 +1161,24 @@ int tc_products(Ctx& c, const void* X, const void* Y, int64_t b, cudaStream_t s,
   const int k = c.k;
   const int slot = (int)(c.t & 1);
   const TcTerms tt = tc_terms(c, slot);
-  // 1. V split into BF16 pairs and the d-side terms -- unless the previous step's fused
-  //    update produced them (and cleared the terms this step accumulates)
-  if (!c.tc_chain) {
-    SGEP_CUDA_TRY(cudaMemsetAsync(c.gram, 0, tc_terms_floats(k) * sizeof(float), s));
-    k_tc_prep_v<<<(unsigned)((c.d + 63) / 64), 256, 0, s>>>(c.V, c.S, c.d, k, c.tc_Vt, tt.G, tt.vv);
-    SGEP_CUDA_TRY(cudaGetLastError());
-    ++c.launches;
+  // 1. V split into BF16 pairs and the d-side terms -- unless the previous step's update
+  //    produced them (and cleared the terms this step accumulates)
+  int rc = tc_prepare_chain(c, s);
+  if (rc) return rc;
+  if (tc_stream_supported(c, b)) {
+    // one read of the minibatch from HBM: products, row-side terms and update in one launch
+    rc = tc_stream_steps(c, X, Y, b, 1, s);
+    if (!rc) c.tc_st_updated = 1;
+    return rc;
   }
   CUtensorMap mX1, mY1, mVt, mX2, mY2, mPt, mQt;
-  int rc = make_map_bf16(&mX1, X, b, c.d_x, c.d_x, 128, 64);
+  rc = make_map_bf16(&mX1, X, b, c.d_x, c.d_x, 128, 64);
   if (!rc) rc = make_map_bf16(&mY1, Y, b, c.d_y, c.d_y, 128, 64);
   if (!rc) rc = make_map_bf16(&mVt, c.tc_Vt, 2 * kTcKP, c.d, c.d, 64, 64);
   if (!rc) rc = make_map_bf16(&mX2, X, b, c.d_x, c.d_x, 64, 64);
   if (!rc) rc = make_map_bf16(&mY2, Y, b, c.d_y, c.d_y, 64, 64);
   if (rc) return rc;
-  if (tc_stream_supported(c, b)) {
-    // one read of the minibatch from HBM: products and row-side terms in one persistent launch
-    rc = make_map_bf16(&mPt, c.tc_Pt, 2 * kTcKP, b, c.cfg.max_b, 64, 64);
-    if (!rc) rc = make_map_bf16(&mQt, c.tc_Qt, 2 * kTcKP, b, c.cfg.max_b, 64, 64);
-    if (!rc) rc = tc_stream_products(c, mX1, mY1, mX2, mY2, mVt, mPt, mQt, tt.a, tt.b, b, eta, gamma, s);
-    return rc;
-  }
   c.tc_pq_dirty = 1;  // the kernels below leave P and Q non-zero
-  if (c.tc_fused_buf && tc_fused_supported(c, b)) {
-    // one read of the minibatch: products in one persistent launch, then the row-side terms
-    rc = tc_fused_products(c, mX1, mY1, mX2, mY2, mVt, b, s);
-    if (rc) return rc;
-    k_tc_prep_w<<<(unsigned)((b + 15) / 16), 256, 0, s>>>(P, Q, b, c.cfg.max_b, nA, k, 1.f / (float)nA,
-                                                           1.f / (float)(split ? b - nA : b), nullptr, nullptr,
-                                                           tt.a, tt.b);
-    SGEP_CUDA_TRY(cudaGetLastError());
-    c.launches += 1;
-    return SGEP_OK;
-  }
   rc = make_map_bf16(&mPt, c.tc_Pt, 2 * kTcKP, b, c.cfg.max_b, 64, 64);
   if (!rc) rc = make_map_bf16(&mQt, c.tc_Qt, 2 * kTcKP, b, c.cfg.max_b, 64, 64);
   if (rc) return rc;
@@ -1278,6 +1265,11 @@ int tc_update(Ctx& c, float eta, float gamma, cudaStream_t s) {
     u.eps_B = c.cfg.eps_B;
     u.bar = c.tc_bar;
     u.bar_target = c.tc_bar_base + grid;
+    u.bar_ns = 2000000000ull;
+    if (c.test_stall) {  // test hook: a barrier count nothing reaches, a short limit
+      u.bar_target += 1;
+      u.bar_ns = 20000000ull;
+    }
     u.trace = c.tc_upd_trace;
     u.dflag = c.dflag;
     u.var = next_variant(c);

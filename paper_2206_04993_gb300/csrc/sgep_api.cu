@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -98,6 +99,7 @@ static void free_ctx(sgep_ctx* c) {
   cudaFree(c->adam_m);
   cudaFree(c->z);
   cudaFree(c->ica_buf);
+  cudaFree(c->mach_buf);
   cudaFree(c->cen_sum);
   cudaFree(c->cen_mean);
   delete c;
@@ -109,8 +111,7 @@ static int check_flag(Ctx& c) {
   if (flag) {
     SGEP_CUDA_TRY(cudaMemset(c.dflag, 0, sizeof(int)));
     if (flag & kFlagTimeout) {
-      c.tc_fused_dirty = 1;  // an aborted one-read launch may leave partial sums behind
-      c.tc_bar_reset = 1;    // ... and an aborted update a short barrier count
+      c.tc_bar_reset = 1;    // an aborted update may leave a short barrier count
       c.tc_st_reset = 1;     // ... and an aborted streamed launch short counters and row sums
       c.tc_chain = 0;
       return fail(SGEP_ETIMEOUT, "a bounded device-side wait gave up");
@@ -157,7 +158,7 @@ UpdVariant next_variant(Ctx& c) {
 
 using namespace sgep;
 
-static_assert(sizeof(sgep_config) == 128, "sgep_config layout changed: update the bindings");
+static_assert(sizeof(sgep_config) == 136, "sgep_config layout changed: update the bindings");
 
 extern "C" {
 
@@ -188,6 +189,7 @@ int sgep_config_default(sgep_config* cfg) {
   cfg->adam_eps = 1e-8f;
   cfg->variant = SGEP_ALG2;
   cfg->nu = 0.f;
+  cfg->machines = 1;
   return SGEP_OK;
 }
 
@@ -229,6 +231,11 @@ int sgep_init(const sgep_config* cfg, sgep_t* out) {
   if (g.center != 0 && g.center != 1) return fail(SGEP_EINVAL, "center must be 0 or 1");
   if (g.center && g.kind != SGEP_PCA && g.kind != SGEP_CCA && g.kind != SGEP_PLS)
     return fail(SGEP_EINVAL, "running-mean centring is for PCA, CCA and PLS (LDA centres by class means)");
+  if (g.machines < 1 || g.reserved0 != 0) return fail(SGEP_EINVAL, "machines must be >= 1 (reserved0 = 0)");
+  if (g.machines > 1 &&
+      ((g.kind != SGEP_CCA && g.kind != SGEP_PCA && g.kind != SGEP_PLS) || variants || g.center ||
+       (g.path != SGEP_PATH_AUTO && g.path != SGEP_PATH_GENERIC)))
+    return fail(SGEP_ENOTSUP, "machines > 1: CCA, PCA or PLS with Alg. 2's plain step on the generic path");
 
   sgep_ctx* c = new (std::nothrow) sgep_ctx();
   if (!c) return fail(SGEP_ENOMEM, "host allocation failed");
@@ -239,6 +246,12 @@ int sgep_init(const sgep_config* cfg, sgep_t* out) {
   c->k = g.k;
   c->b_is_identity = (g.kind == SGEP_PCA || g.kind == SGEP_PLS);
   c->has_y = !one_view;
+  {
+    // test hook for the bounded waits: the fused tensor-core update's grid barrier waits for
+    // one arrival too many (nothing sends it) and gives up after 20 ms
+    const char* st = std::getenv("SGEP_TEST_STALL");
+    c->test_stall = (st && st[0] == '1') ? 1 : 0;
+  }
   cudaError_t e = cudaGetDevice(&c->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
   if (e != cudaSuccess) {
@@ -297,7 +310,8 @@ int sgep_init(const sgep_config* cfg, sgep_t* out) {
   // Path selection.
   const char* why = nullptr;
   const bool cl_ok = cluster_supported(*c, &why);
-  const bool generic_only = g.kind == SGEP_LDA || g.kind == SGEP_ICA || g.dtype == SGEP_FP8E4M3 || g.center;
+  const bool generic_only =
+      g.kind == SGEP_LDA || g.kind == SGEP_ICA || g.dtype == SGEP_FP8E4M3 || g.center || g.machines > 1;
   if (generic_only && g.path != SGEP_PATH_AUTO && g.path != SGEP_PATH_GENERIC) {
     free_ctx(c);
     return fail(SGEP_ENOTSUP, "LDA, ICA, FP8 rows and running-mean centring run on the generic path only");
@@ -313,6 +327,13 @@ int sgep_init(const sgep_config* cfg, sgep_t* out) {
     }
   }
   if (generic_only) c->path = SGEP_PATH_GENERIC;
+  if (g.machines > 1) {  // per-machine averaging: V' and [Bv]' accumulators and a copy of [Bv]
+    e = cudaMalloc((void**)&c->mach_buf, 3 * dk * sizeof(float));
+    if (e != cudaSuccess) {
+      free_ctx(c);
+      return cuda_fail(e, "cudaMalloc (machines)");
+    }
+  }
   if (g.kind == SGEP_ICA) {
     int rc = ica_alloc(*c);
     if (rc) {
@@ -406,9 +427,19 @@ static int step_checks(Ctx& c, const void* X, const void* Y, const float* sx, co
   if (c.cfg.kind == SGEP_LDA && !labels) return fail(SGEP_EINVAL, "LDA needs labels");
   const bool split = (c.cfg.kind == SGEP_CCA || c.cfg.kind == SGEP_LDA || c.cfg.kind == SGEP_ICA) && c.cfg.split_AB;
   const int64_t bmin = split ? (c.cfg.kind == SGEP_ICA ? 4 : 2) : 1;
-  if (b < bmin) return fail(SGEP_EINVAL, "b too small (split batches need b >= 2, ICA quarters b >= 4)");
+  if (b < bmin * c.cfg.machines)
+    return fail(SGEP_EINVAL, "b too small (split batches need b >= 2, ICA quarters b >= 4, per machine)");
   if (b > c.cfg.max_b) return fail(SGEP_EINVAL, "b exceeds max_b");
   return SGEP_OK;
+}
+
+// The periodic Rayleigh-Ritz correction, when step count c.t is due for one.
+static int rr_if_due(Ctx& c, cudaStream_t s) {
+  if (c.rr_every <= 0 || c.t % c.rr_every != 0) return SGEP_OK;
+  int rc = rr_correct(c, c.rr_X, c.rr_Y, c.rr_sx, c.rr_sy, c.rr_labels, c.rr_n, nullptr, s);
+  c.tc_chain = 0;  // V and [Bv] changed outside the step
+  if (rc) return rc;
+  return check_flag(c);
 }
 
 static int do_step(Ctx& c, const void* X, const void* Y, const float* sx, const float* sy, const int32_t* labels,
@@ -426,16 +457,21 @@ static int do_step(Ctx& c, const void* X, const void* Y, const float* sx, const 
       if (!rc) rc = c.tc_generic_step ? generic_update(c, eta, gamma, s) : tc_update(c, eta, gamma, s);
     } else {
       rc = c.cen_sum ? centring_update(c, X, Y, b, s, sx, sy) : SGEP_OK;  // the step's rows first
-      if (!rc) {
-        if (c.cfg.kind == SGEP_LDA) rc = lda_products(c, X, labels, b, s, sx);
-        else if (c.cfg.kind == SGEP_ICA) rc = ica_products(c, X, b, s, sx, c.cfg.split_AB != 0);
-        else rc = generic_products(c, X, Y, b, s, sx, sy);
+      if (!rc && c.cfg.machines > 1) {
+        rc = generic_machines_step(c, X, Y, b, s, sx, sy, eta, gamma);
+      } else {
+        if (!rc) {
+          if (c.cfg.kind == SGEP_LDA) rc = lda_products(c, X, labels, b, s, sx);
+          else if (c.cfg.kind == SGEP_ICA) rc = ica_products(c, X, b, s, sx, c.cfg.split_AB != 0);
+          else rc = generic_products(c, X, Y, b, s, sx, sy);
+        }
+        if (!rc) rc = generic_update(c, eta, gamma, s);
       }
-      if (!rc) rc = generic_update(c, eta, gamma, s);
     }
-    if (!rc) c.debug_valid = c.cfg.debug;
+    if (!rc) c.debug_valid = c.cfg.machines > 1 ? 0 : c.cfg.debug;  // shards keep no directions
   }
   if (!rc) c.t = t;
+  if (!rc && c.path != SGEP_PATH_CLUSTER) rc = rr_if_due(c, s);
   return rc;
 }
 
@@ -454,6 +490,27 @@ int sgep_step_many(sgep_t h, const void* X, const void* Y, const float* row_scal
   int rc = step_checks(*h, X, Y, row_scale_x, row_scale_y, labels, b);
   if (rc) return rc;
   const size_t esz = elem_size(*h);
+  Ctx& c = *h;
+  if (c.path == SGEP_PATH_TC && tc_stream_supported(c, b) && !((uintptr_t)X & 15) && !((uintptr_t)Y & 15)) {
+    // consecutive minibatches of the streamed tensor-core path: several steps per launch
+    for (int64_t s0 = 0; s0 < nsteps;) {
+      int64_t lim = std::min<int64_t>(nsteps - s0, tc_stream_max_steps());
+      if (c.rr_every > 0) lim = std::min<int64_t>(lim, c.rr_every - c.t % c.rr_every);  // stop at a correction
+      const int n = (int)lim;
+      const char* xs = (const char*)X + (size_t)s0 * b * c.d_x * esz;
+      const char* ys = (const char*)Y + (size_t)s0 * b * c.d_y * esz;
+      rc = tc_prepare_chain(c, (cudaStream_t)stream);
+      if (!rc) rc = tc_stream_steps(c, xs, ys, b, n, (cudaStream_t)stream);
+      if (rc) return rc;
+      c.t += n;
+      c.tc_generic_step = 0;
+      c.debug_valid = c.cfg.debug;
+      s0 += n;
+      rc = rr_if_due(c, (cudaStream_t)stream);
+      if (rc) return rc;
+    }
+    return SGEP_OK;
+  }
   for (int64_t s = 0; s < nsteps; ++s) {
     const char* xs = (const char*)X + (size_t)s * b * h->d_x * esz;
     const char* ys = Y ? (const char*)Y + (size_t)s * b * h->d_y * esz : nullptr;
@@ -470,7 +527,6 @@ int sgep_sync(sgep_t h, void* stream) {
   if (!h) return fail(SGEP_EINVAL, "handle is NULL");
   int rc = complete(*h, (cudaStream_t)stream);
   if (h->trace) cluster_trace_report(*h);
-  if (h->tc_trace) tc_fused_trace_report(*h);
   if (h->tc_upd_trace) tc_update_trace_report(*h);
   if (h->tc_st_trace) tc_stream_trace_report(*h);
   return rc;
@@ -648,6 +704,36 @@ int sgep_rayleigh_ritz(sgep_t h, const void* X, const void* Y, const float* row_
   c.debug_valid = 0;
   if (rc) return rc;
   return check_flag(c);
+}
+
+int sgep_set_rr_every(sgep_t h, int64_t every, const void* X, const void* Y, const float* row_scale_x,
+                      const float* row_scale_y, const int32_t* labels, int64_t n) {
+  if (!h) return fail(SGEP_EINVAL, "handle is NULL");
+  Ctx& c = *h;
+  if (every < 0) return fail(SGEP_EINVAL, "every must be >= 0");
+  if (every == 0) {
+    c.rr_every = 0;
+    c.rr_X = c.rr_Y = nullptr;
+    c.rr_sx = c.rr_sy = nullptr;
+    c.rr_labels = nullptr;
+    c.rr_n = 0;
+    return SGEP_OK;
+  }
+  if (c.cfg.kind == SGEP_ICA) return fail(SGEP_ENOTSUP, "the Rayleigh-Ritz correction does not take ICA");
+  if (c.path == SGEP_PATH_CLUSTER)
+    return fail(SGEP_ENOTSUP, "the cluster path keeps its update pending: call sgep_rayleigh_ritz between steps");
+  if (!X || (c.has_y && !Y)) return fail(SGEP_EINVAL, "NULL argument");
+  if (c.cfg.kind == SGEP_LDA && !labels) return fail(SGEP_EINVAL, "LDA needs labels");
+  if (n < 1) return fail(SGEP_EINVAL, "n must be >= 1");
+  if (int e = scale_checks(c, row_scale_x, row_scale_y)) return e;
+  c.rr_every = every;
+  c.rr_X = X;
+  c.rr_Y = Y;
+  c.rr_sx = row_scale_x;
+  c.rr_sy = row_scale_y;
+  c.rr_labels = labels;
+  c.rr_n = n;
+  return SGEP_OK;
 }
 
 int sgep_get_state(sgep_t h, void* buf, size_t* nbytes) {

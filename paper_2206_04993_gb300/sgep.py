@@ -40,6 +40,7 @@ class sgep_config(ctypes.Structure):
         ("debug", ctypes.c_int32), ("optimizer", ctypes.c_int32), ("adam_b1", ctypes.c_float),
         ("adam_b2", ctypes.c_float), ("adam_eps", ctypes.c_float), ("variant", ctypes.c_int32),
         ("nu", ctypes.c_float), ("center", ctypes.c_int32),
+        ("machines", ctypes.c_int32), ("reserved0", ctypes.c_int32),
     ]
 
 
@@ -63,6 +64,7 @@ _SIGS = {
     "sgep_set_VS": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P]),
     "sgep_get_eigenvalues": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.c_int64, _P, _P]),
     "sgep_rayleigh_ritz": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, ctypes.c_int64, _P, _P]),
+    "sgep_set_rr_every": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P, _P, _P, ctypes.c_int64]),
     "sgep_batch_create": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P)]),
     "sgep_batch_destroy": (ctypes.c_int, [_P]),
     "sgep_batch_step": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P]),
@@ -202,6 +204,11 @@ def sgep_set_V(h, V, on_device: bool, stream=None) -> None:
 
 def sgep_set_VS(h, V, S, on_device: bool, stream=None) -> None:
     check(lib().sgep_set_VS(h, _ptr(V), _ptr(S), int(on_device), _stream(stream)), "sgep_set_VS")
+
+
+def sgep_set_rr_every(h, every, X=None, Y=None, n=0, labels=None, sx=None, sy=None) -> None:
+    check(lib().sgep_set_rr_every(h, int(every), _ptr(X), _ptr(Y), _ptr(sx), _ptr(sy), _ptr(labels), int(n)),
+          "sgep_set_rr_every")
 
 
 def sgep_rayleigh_ritz(h, X, Y, n, out=None, labels=None, stream=None, sx=None, sy=None) -> None:

@@ -77,6 +77,13 @@ class Solver:
         _s.sgep_rayleigh_ritz(self.h, X, Y, X.shape[0], out, labels, self._cur_stream(), sx, sy)
         return out
 
+    def set_rr_every(self, every, X=None, Y=None, labels=None, sx=None, sy=None):
+        """Rayleigh-Ritz correction on the evaluation rows (X, Y) after every `every` steps
+        (0 removes it); the rows must stay alive and unchanged while it is set."""
+        n = 0 if X is None else X.shape[0]
+        self._rr_rows = (X, Y, labels, sx, sy) if every else None  # keep them alive
+        _s.sgep_set_rr_every(self.h, every, X, Y, n, labels, sx, sy)
+
     def products(self):
         AV = np.empty((self.d, self.k), dtype=np.float32)
         BV = np.empty((self.d, self.k), dtype=np.float32)

@@ -8,6 +8,13 @@ from oracle import eg
 
 # Per-step parity bar for the FP32 path (relative to the magnitude of the terms).
 STEP_TOL = 1e-5
+# The per-column checks (keys ending in "_col" and "_elem") bound what a whole-matrix
+# Frobenius ratio dilutes: an error confined to one player column or to a few rows (a ragged
+# tail tile). One column's rounding error relative to its own norm, and the largest element
+# error relative to the column's largest entry, may exceed the whole-matrix ratio by a small
+# factor (a column of small norm; the maximum of d errors against the maximum of d values),
+# so those keys are held to COL_FACTOR times the step bar.
+COL_FACTOR = 4.0
 
 
 def bf16_round(a: np.ndarray) -> np.ndarray:
@@ -39,6 +46,26 @@ def rel(a, b) -> float:
     return float(np.linalg.norm(np.asarray(a, np.float64) - b) / (nb if nb > 0 else 1.0))
 
 
+def col_errors(a, b):
+    """(max over columns of |a_i - b_i| / |b_i|, max over columns of max_c |a_ci - b_ci| /
+    max_c |b_ci|) for d x k matrices whose columns are players."""
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    diff = np.abs(a - b)
+    nb = np.linalg.norm(b, axis=0)
+    mb = np.max(np.abs(b), axis=0)
+    col = np.linalg.norm(a - b, axis=0) / np.where(nb > 0, nb, 1.0)
+    elem = np.max(diff, axis=0) / np.where(mb > 0, mb, 1.0)
+    return float(np.max(col)), float(np.max(elem))
+
+
+def assert_within(err: dict, tol: float):
+    """Every whole-matrix ratio within tol, every per-column ratio within COL_FACTOR tol."""
+    for name, e in err.items():
+        lim = tol * (COL_FACTOR if name.endswith(("_col", "_elem")) else 1.0)
+        assert e <= lim, (name, e, lim, err)
+
+
 def step_errors(solver, V0, S0, X, Y, kind, eta, gamma, rho, split=True, eps_B=0.0, dtype="f32"):
     """Run one library step from (V0, S0) on (X, Y) and one oracle step on the same values.
     Returns a dict of relative errors for A_t V, B_t V, grad, V', S'."""
@@ -62,6 +89,10 @@ def step_errors(solver, V0, S0, X, Y, kind, eta, gamma, rho, split=True, eps_B=0
     out = {"AV": rel(AVg, AV), "V": rel(Vg, V1), "S": rel(Sg, S1)}
     if kind == "cca":
         out["BV"] = rel(BVg, BV - eps_B * V0.astype(np.float64))
+        out["BV_col"], out["BV_elem"] = col_errors(BVg, BV - eps_B * V0.astype(np.float64))
+    out["AV_col"], out["AV_elem"] = col_errors(AVg, AV)
+    out["V_col"], out["V_elem"] = col_errors(Vg, V1)
+    out["S_col"], out["S_elem"] = col_errors(Sg, S1)
     if solver.cfg.debug:
         gg, a, G, b = solver.update_terms()
         a_ref = V0.astype(np.float64).T @ AV

@@ -31,9 +31,10 @@ def test_config_defaults_and_layout():
     assert cfg.kind == S.SGEP_CCA and cfg.dtype == S.SGEP_F32
     assert cfg.k == 1 and cfg.split_AB == 1 and cfg.max_b == 4096
     assert abs(cfg.rho - 1e-6) < 1e-12 and cfg.schedule == S.SGEP_SCHED_CONST
+    assert cfg.machines == 1 and cfg.reserved0 == 0
     # the header's struct: 2 int32, 2 int64, 2 int32, 4 float, 2 int32, 2 int64, float,
-    # int32, uint64, int64, int32, 7 int32 (natural alignment)
-    assert ctypes.sizeof(S.sgep_config) == 128
+    # int32, uint64, int64, int32, 9 int32 (natural alignment)
+    assert ctypes.sizeof(S.sgep_config) == 136
 
 
 def test_strerror_and_null_arguments():

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import synth
-from gpu_util import STEP_TOL, step_errors
+from gpu_util import STEP_TOL, assert_within, step_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -75,8 +75,7 @@ def test_single_step_matches_oracle(kind, dx, dy, k, b, path):
     V0, S0 = _state(d, k, seed=b, kind=kind)
     with _solver(kind, dx, dy, k, path, eta0=0.3, gamma0=0.4, rho=1e-3) as s:
         err = step_errors(s, V0, S0, X, Y, kind, 0.3, 0.4, 1e-3)
-    for name, e in err.items():
-        assert e <= STEP_TOL, (name, e, err)
+    assert_within(err, STEP_TOL)
 
 
 @pytest.mark.parametrize("kind,dx,dy,k,b", [("cca", 2048, 2048, 8, 8192), ("cca", 2046, 2050, 7, 8192),
@@ -89,8 +88,7 @@ def test_generic_ring_many_stages_matches_oracle(kind, dx, dy, k, b):
     V0, S0 = _state(dx + dy, k, seed=k, kind=kind)
     with _solver(kind, dx, dy, k, S.SGEP_PATH_GENERIC, eta0=0.3, gamma0=0.4, rho=1e-3, max_b=b) as s:
         err = step_errors(s, V0, S0, X, Y, kind, 0.3, 0.4, 1e-3)
-    for name, e in err.items():
-        assert e <= STEP_TOL, (name, e, err)
+    assert_within(err, STEP_TOL)
 
 
 @pytest.mark.parametrize("path", PATHS, ids=["generic", "cluster"])
@@ -99,8 +97,7 @@ def test_single_step_shared_batch_and_ridge(path):
     V0, S0 = _state(88, 6, seed=5, kind="cca")
     with _solver("cca", 48, 40, 6, path, eta0=0.2, gamma0=1.0, rho=1e-6, split_AB=0, eps_B=0.05) as s:
         err = step_errors(s, V0, S0, X, Y, "cca", 0.2, 1.0, 1e-6, split=False, eps_B=0.05)
-    for name, e in err.items():
-        assert e <= STEP_TOL, (name, e, err)
+    assert_within(err, STEP_TOL)
 
 
 @pytest.mark.parametrize("path", PATHS, ids=["generic", "cluster"])
@@ -111,8 +108,7 @@ def test_single_step_bf16_aligned_shapes(path, dx, dy, k, b):
     V0, S0 = _state(dx + dy, k, seed=4, kind="cca")
     with _solver("cca", dx, dy, k, path, dtype="bf16", eta0=0.3, gamma0=0.5, rho=1e-4) as s:
         err = step_errors(s, V0, S0, X, Y, "cca", 0.3, 0.5, 1e-4, dtype="bf16")
-    for name, e in err.items():
-        assert e <= STEP_TOL, (name, e, err)
+    assert_within(err, STEP_TOL)
 
 
 @pytest.mark.parametrize("path", PATHS, ids=["generic", "cluster"])
@@ -123,8 +119,7 @@ def test_single_step_bf16_inputs(path):
     V0, S0 = _state(176, 8, seed=2, kind="cca")
     with _solver("cca", 96, 80, 8, path, dtype="bf16", eta0=0.3, gamma0=0.5, rho=1e-4) as s:
         err = step_errors(s, V0, S0, X, Y, "cca", 0.3, 0.5, 1e-4, dtype="bf16")
-    for name, e in err.items():
-        assert e <= STEP_TOL, (name, e, err)
+    assert_within(err, STEP_TOL)
 
 
 @pytest.mark.parametrize("path", PATHS, ids=["generic", "cluster"])
@@ -135,8 +130,7 @@ def test_clipping_active(path):
     S0 = -0.5 * V0
     with _solver("cca", 20, 20, 5, path, eta0=0.05, gamma0=0.3, rho=0.2) as s:
         err = step_errors(s, V0, S0, X, Y, "cca", 0.05, 0.3, 0.2)
-    for name, e in err.items():
-        assert e <= STEP_TOL, (name, e, err)
+    assert_within(err, STEP_TOL)
 
 
 @pytest.mark.parametrize("path", PATHS, ids=["generic", "cluster"])
