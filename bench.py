@@ -2,7 +2,7 @@
 
 Default workload: activation-like CCA, d_x = d_y = 16384 (d = 32768), k = 32 players,
 minibatch b = 4096 rows in BF16 (268 MB per minibatch), power-law noise spectrum with 64
-planted shared directions. A pool of 32,768 rows (8 minibatches, 2.1 GB) is generated on
+planted shared directions. A pool of 65,536 rows (16 minibatches, 4.3 GB) is generated on
 the device before timing; timed steps stream consecutive minibatches through it, so the
 inputs exceed L2 and every step reads fresh rows from HBM. The other workloads (the
 1024-dim FP32 CCA with its time-to-1e-3 runs, the FP32 form of the large problem, the
@@ -39,8 +39,8 @@ WORKLOADS = {
     # name: (synth config function, dtype, pool rows)
     "cca_d1024_k16_b1024_f32": ("config_c2", "f32", 1_000_000),
     "cca_d64_k4_b256_f32": ("config_c1", "f32", 10_000),
-    # activation-like CCA, d_x = d_y = 16384, k = 32, b = 4096, BF16 rows (8 minibatches = 2.1 GB)
-    "cca_d32768_k32_b4096_bf16": ("config_c3", "bf16", 32_768),
+    # activation-like CCA, d_x = d_y = 16384, k = 32, b = 4096, BF16 rows (16 minibatches = 4.3 GB)
+    "cca_d32768_k32_b4096_bf16": ("config_c3", "bf16", 65_536),
     "cca_d32768_k32_b4096_f32": ("config_c3", "f32", 16_384),
 }
 DEFAULT_WORKLOAD = "cca_d32768_k32_b4096_bf16"
@@ -65,10 +65,10 @@ def parse():
     return p.parse_args()
 
 
-# DRAM bytes (read + write) per launch of the dominant kernel from one ncu capture of the
-# current kernel (profiles/cluster_step_cca_d1024_k16_b1024_f32.md); set to None whenever
-# the kernel changes until it is captured again.
-TRAFFIC_BYTES = {"cca_d1024_k16_b1024_f32": 4_707_328}
+# DRAM bytes (read + write) per step of the dominant kernel from one ncu capture of the
+# current kernel (profiles/); an entry is removed whenever the kernel changes until it is
+# captured again.
+TRAFFIC_BYTES = {}
 
 
 def world_max(value: float, world: int, device=None) -> float:
@@ -753,18 +753,25 @@ def run_native(args):
     ms_step = ms / args.steps
     value = world * b * args.steps / (ms / 1e3)
 
-    # roofline of the step (the minibatch is read once; V and [Bv] are read and written once)
+    # roofline of the step (the minibatch is read once; V and [Bv] are read and written once).
+    # On the streamed tensor-core path and the cluster path the timed steps are exactly the
+    # launches of one kernel (the streamed kernel runs every step of a step_many call, the
+    # cluster kernel one step per launch), so the step time is that kernel's time per step.
     peak, peak_kind = measured_peaks()
     alg_bytes = b * d * esz + 16 * d * k
     achieved = alg_bytes / (ms_step / 1e3) / 1e9
-    one_kernel = solver.path == sgep.SGEP_PATH_CLUSTER
+    kernels = {sgep.SGEP_PATH_CLUSTER: "k_cluster_step (one step per launch)",
+               sgep.SGEP_PATH_TC: "k_tc_stream (products, row-side terms and update of every step of a "
+                                  "step_many call in one launch)"}
+    one_kernel = solver.path in kernels and launches <= -(-args.steps // max(1, min(nb, 64)))
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak,
                 "traffic": TRAFFIC_BYTES.get(args.workload) if one_kernel else None,
-                "kernel": "k_cluster_step (the whole step, one launch)" if one_kernel
-                else f"whole step, path {solver.path}",
-                "peak_source": peak_kind, "alg_bytes_per_launch": alg_bytes,
-                "timing": "CUDA events over the timed launches on their stream"}
+                "kernel": kernels[solver.path] if one_kernel else f"whole step, path {solver.path}",
+                "peak_source": peak_kind, "alg_bytes_per_step": alg_bytes,
+                "alg_bytes_formula": "b d (element bytes) + 16 d k",
+                "timing": "CUDA events over the timed launches on their stream (the step's only kernel)"
+                if one_kernel else "CUDA events over the timed launches on their stream"}
 
     # e2e: through the C ABI with host buffers every step
     e2e = None

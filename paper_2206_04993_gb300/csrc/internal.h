@@ -103,6 +103,7 @@ struct Ctx {
   int tc_st_lag = 5, tc_st_helpers = 24;  // tuning knobs (SGEP_TC_LAG, SGEP_TC_HELPERS)
   float* tc_st_terms = nullptr;    // [3] row-side term slots a | b, then [3] slots |v'|^2 | U
   unsigned tc_st_launch = 0;       // streamed launches since the counters were last cleared
+  unsigned tc_st_grams = 0;        // helper Gram contributions since then
   int tc_st_updated = 0;           // the most recent streamed launch applied the step's update
   int64_t tc_st_last_b = 0;        // minibatch size the counters were last used with
   int tc_acc_stale = 0;            // acc does not hold the last step's products (not kept)

@@ -80,11 +80,13 @@ constexpr int kEStg = 128 * 32 * 4;  // epilogue staging: one 128 x 32 FP32 proj
 constexpr int kNumBars = 2 * kPS + 2 * kAcc + 2 * kBS + 5 + 2 + 4 + 1;
 constexpr size_t kSmem = (size_t)kVtB + kPS * kPBox + kBS * kBStage + kEStg + kNumBars * 8 + 64 + 1024;
 static_assert(2 * kStgRows * 32 * 4 <= kVtB, "builder staging fits in the V^T region");
+static_assert(2 * kStgRows * 32 * 4 + (3 * 32 * 32 + 4 * 32) * 4 <= kVtB,
+              "builder staging and the coefficient scratch fit in the V^T region");
 static_assert(kSmem <= 232448, "shared memory budget");
-constexpr int kRTc = kR / 128;  // row tiles per chunk
 constexpr int kKP = 32;         // players padded to 32
 constexpr int kTerms = kKP * kKP + kKP;  // one slot of row-side terms a (k x k) | b (k), or |v'|^2 | U
 constexpr int kMaxSteps = 64;   // steps of one launch
+constexpr int kCoef = kKP * kKP + 3 * kKP;  // one slot of update coefficients: T | b | a_ii - c_i | 1/n
 // update scratch: V' and [Bv] rows [256][kRS] (16-byte aligned rows) in the back-projection stages
 constexpr int kRS = 36;
 static_assert(2 * 256 * kRS * 4 <= kBS * kBStage, "update rows fit in the back-projection stages");
@@ -95,6 +97,7 @@ struct StreamArgs {
   int64_t d;
   int k, nchunk, splits;
   int G;                    // streaming CTAs; CTAs G .. gridDim.x - 1 are builder helpers
+  int H;                    // helper CTAs
   int lag;                  // chunks the projection may run ahead of the CTA's back-projection
   int nsteps;               // consecutive minibatches of this launch (rows s*b .. s*b + b - 1)
   int serial;               // the next step's projection also waits for the CTA's own update
@@ -111,8 +114,12 @@ struct StreamArgs {
   unsigned* terms_done;     // row-side items added by the builders (monotone)
   unsigned* bar;            // grid-barrier arrivals (one barrier per launch, monotone)
   unsigned bar_target;
-  unsigned* upd_cnt;        // updates finished, all CTAs (monotone)
-  unsigned* upd_done;       // [G] updates finished by CTA j (monotone)
+  unsigned* grams_done;     // helper CTAs (those owning a slice) that added a step's |v'|^2 and U (monotone)
+  unsigned grams_base;      // its value at the launch
+  unsigned* upd_done;       // [G] updates finished by CTA j: the V^T operand is written (monotone)
+  unsigned* rows_done;      // [G] ... and the rows of V and [Bv] (monotone)
+  unsigned* coef_ready;     // steps whose update coefficients are written (monotone)
+  float* cbuf;              // [2][kCoef] update coefficients of step e in slot e & 1
   float* abbuf;             // [3][kTerms] row-side terms a | b of step e in slot e % 3
   float* ubuf;              // [3][kTerms] |v'_i|^2 | U of the V' left by step e - 1, slot e % 3
   float* V;                 // d x k, read and rewritten
@@ -127,7 +134,8 @@ struct StreamArgs {
   float* dbg;               // a | G | b as used by the last step (debug), or null
   float* grad_out;          // update directions of the last step (debug), or null
   int* dflag;
-  unsigned long long* trace;  // [G + H][nchunk + 1][kEv] globaltimer stamps of the last step, or null
+  unsigned long long* trace;  // [G + H][nchunk + 2][kEv] globaltimer stamps of the last step, or null
+  unsigned long long* trace2;  // [G][16] row-work stamps of the step before the last, or null
 };
 
 // Trace events per chunk (last step of the launch); row nchunk of a CTA holds start,
@@ -162,18 +170,92 @@ __device__ __forceinline__ bool wait_shared_geq(volatile int* p, int target, uin
   }
 }
 
-// 16 consecutive FP32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-      "%14, %15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+// The k x k coefficients of step e's update, computed once per step by the 128 builder threads
+// (bt) of the helper CTA that added the step's last row-side item: with the deferred norms
+// n_i (step s > 0: n_i^2 and U from ubuf[e % 3]; step 0: n_i = 1, G and |v_i|^2 from G0, vv0),
+// a_ij = a'_ij / (n_i n_j), b_i = b'_i / n_i^2 (+ eps_B |v_i|^2), G = diag(1/n) U, s_j =
+// max(G_jj, rho), T_ji = b_i a_ij / s_j (j < i, else 0), c_i = sum_{j<i} a_ij G_ij / s_j.
+// Writes T | b | a_ii - c_i | 1/n into cbuf[e & 1] (and a | G | b to dbg at the launch's last
+// step), then releases coef_ready. sm: 3 * 32 * 32 + 4 * 32 floats. False on a timeout.
+__device__ __forceinline__ bool build_coefficients(const StreamArgs& a, int s, unsigned e, int bt, float* sm,
+                                                volatile int* ok) {
+  const int k = a.k, kk = k * k;
+  float* Am = sm;                // [32][32]
+  float* Gm = Am + kKP * kKP;    // [32][32]
+  float* T = Gm + kKP * kKP;     // [32][32]
+  float* cb = T + kKP * kKP;
+  float* cac = cb + kKP;
+  float* inv_s = cac + kKP;
+  float* inv_n = inv_s + kKP;
+  const float* ab = a.abbuf + (size_t)(e % 3) * kTerms;
+  const float* ub = a.ubuf + (size_t)(e % 3) * kTerms;
+  if (bt == 0)
+    *ok = (s == 0 || spin_until_geq(a.grams_done, a.grams_base + (unsigned)(s * min(a.H, a.G)))) ? 1 : 0;
+  named_barrier(2, 128);
+  if (!*ok) return false;
+  // every load in flight at once (kk <= 8 * 128)
+  float la[8], lg[8];
 #pragma unroll
-  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+  for (int u = 0; u < 8; ++u) {
+    const int p = bt + 128 * u;
+    const int i = p / k, jj = p - i * k;
+    la[u] = p < kk ? __ldcg(ab + p) : 0.f;
+    lg[u] = p < kk ? (s == 0 ? __ldcg(a.G0 + p) : __ldcg(ub + kKP + i * kKP + jj)) : 0.f;
+  }
+  const float nsq = (s > 0 && bt < k) ? __ldcg(ub + bt) : 1.f;
+  const float bq = bt < k ? __ldcg(ab + kk + bt) : 0.f;
+  const float vv = (s == 0 && bt < k) ? __ldcg(a.vv0 + bt) : 1.f;
+  if (bt < kKP) inv_n[bt] = bt < k ? (s == 0 ? 1.f : 1.f / sqrtf(nsq)) : 0.f;
+  named_barrier(2, 128);
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int p = bt + 128 * u;
+    const int i = p / k, jj = p - i * k;
+    if (p < kk) {
+      Am[i * kKP + jj] = la[u] * inv_n[i] * inv_n[jj];
+      Gm[i * kKP + jj] = s == 0 ? lg[u] : lg[u] * inv_n[i];
+    }
+  }
+  if (bt < kKP) cb[bt] = bt < k ? fmaf(a.eps_B, vv, bq * inv_n[bt] * inv_n[bt]) : 0.f;
+  named_barrier(2, 128);
+  if (bt < kKP) inv_s[bt] = bt < k ? 1.f / fmaxf(Gm[bt * kKP + bt], a.rho) : 0.f;
+  named_barrier(2, 128);
+  for (int p = bt; p < kKP * kKP; p += 128) {
+    const int jj = p / kKP, i = p % kKP;
+    T[p] = (jj < i && i < k) ? cb[i] * Am[i * kKP + jj] * inv_s[jj] : 0.f;
+  }
+  {
+    // c_i: warp w takes players 8w .. 8w + 7, the lanes run over j
+    const int w = bt >> 5, lane = bt & 31;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = 8 * w + u;
+      float c = (lane < i && i < k) ? Am[i * kKP + lane] * Gm[i * kKP + lane] * inv_s[lane] : 0.f;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+      if (lane == 0) cac[i] = i < k ? Am[i * kKP + i] - c : 0.f;
+    }
+  }
+  named_barrier(2, 128);
+  float* cf = a.cbuf + (size_t)(e & 1) * kCoef;
+  for (int p = bt; p < kKP * kKP; p += 128) cf[p] = T[p];
+  if (bt < kKP) {
+    cf[kKP * kKP + bt] = cb[bt];
+    cf[kKP * kKP + kKP + bt] = cac[bt];
+    cf[kKP * kKP + 2 * kKP + bt] = inv_n[bt];
+  }
+  if (s == a.nsteps - 1 && a.dbg) {  // a | G | b as used (b without eps_B)
+    for (int p = bt; p < kk; p += 128) {
+      const int i = p / k, jj = p - i * k;
+      a.dbg[p] = Am[i * kKP + jj];
+      a.dbg[kk + p] = Gm[i * kKP + jj];
+    }
+    if (bt < k) a.dbg[2 * kk + bt] = __ldcg(ab + kk + bt) * inv_n[bt] * inv_n[bt];
+  }
+  __threadfence();
+  named_barrier(2, 128);
+  if (bt == 0) red_release_add(a.coef_ready, 1u);
+  return true;
 }
 
 // 8 consecutive FP32 columns of this thread's TMEM lane (no wait).
@@ -197,18 +279,16 @@ __device__ __forceinline__ void tmem_wait_ld32(uint32_t (&a)[8], uint32_t (&b)[8
 
 // The update of Alg. 2 for the CTA's 256 rows of V (rows goff .. goff + 255), by warps 4-11
 // (ut = tid - 128: row ut of the slice; TMEM lane ut & 127 of accumulator half ut >> 7).
-// V in memory holds v'_i = n_i v_i (step s > 0: the previous step's retraction deferred, with
-// n_i^2 and U = V'^T [Bv] reduced in ubuf[e % 3]; step 0: n_i = 1 and G from G0). Reads:
-// A_t V' and B_t V' (TMEM), a' and b' (abbuf[e % 3], from the rows' projections with V');
-// scaled by 1/n they are the step's A_t V, B_t V, a_ij = v_i^T A_t v_j, b_i = v_i^T B_t v_i, and
-// G = diag(1/n) U. Eq. (update) in matrix form: grad = A_t V diag(b) - B_t V diag(a - c) - [Bv] T
-// with T_ji = b_i a_ij / s_j (j < i), c_i = sum_{j<i} a_ij G_ij / s_j, s_j = max(G_jj, rho); then
-// v'' = v + eta grad, [Bv]'' = [Bv] + gamma (B_t v - [Bv]). A non-final step first writes the
-// BF16 pairs of v'' (the next step's operand; the retraction deferred) and releases them, then
-// writes v'' and [Bv]'' and adds |v''_i|^2 and V''^T [Bv]'' into ubuf[(e + 1) % 3]; the final step
-// normalises behind a grid barrier and leaves G, |v_i|^2 for the next launch. br_free is
-// arrived on when the back-projection stages (the update's scratch) may be reused. Returns
-// false on a timeout (recorded).
+// V in memory holds v'_i = n_i v_i (step s > 0: the previous step's retraction deferred; step 0:
+// n_i = 1). A_t V' and B_t V' (TMEM) scaled by 1/n are the step's A_t V and B_t V; the k x k
+// coefficients of Eq. (update) in matrix form, grad = A_t V diag(b) - B_t V diag(a - c) - [Bv] T
+// (T_ji = b_i a_ij / s_j for j < i, c_i = sum_{j<i} a_ij G_ij / s_j, s_j = max(G_jj, rho)), come
+// from cbuf (build_coefficients); then v'' = v + eta grad, [Bv]'' = [Bv] + gamma (B_t v - [Bv]).
+// A non-final step writes the BF16 pairs of v'' (the next step's operand; the retraction
+// deferred) and releases them, then the rows of v'' and [Bv]'' (the helpers form their Grams);
+// the final step adds |v''_i|^2 and V''^T [Bv]'' into ubuf[(e + 1) % 3], normalises behind a
+// grid barrier and leaves G, |v_i|^2 for the next launch. br_free is arrived on when the
+// back-projection stages (the update's scratch) may be reused. False on a timeout (recorded).
 __device__ __forceinline__ bool run_update(const StreamArgs& a, int s, unsigned e, int j, int64_t goff,
                                            uint32_t tmem_bp, uint8_t* BR, float* ESTG, uint64_t* bp_done,
                                            uint64_t* bp_free, uint64_t* br_free, volatile int* ok,
@@ -220,17 +300,18 @@ __device__ __forceinline__ bool run_update(const StreamArgs& a, int s, unsigned 
   float* vs = reinterpret_cast<float*>(BR);  // [256][36] V' rows, then v''
   float* ss = vs + 256 * kRS;                // [256][36] [Bv] rows, then [Bv]''
   float* T = ESTG;                           // [32][32] T_ji at j * 32 + i
-  float* Am = T + kKP * kKP;                 // [32][32] a_ij at i * 32 + j
-  float* Gm = Am + kKP * kKP;                // [32][32] G_ij
-  float* cb = Gm + kKP * kKP;                // b_i (+ eps_B |v_i|^2)
+  float* cb = T + kKP * kKP;                 // b_i (+ eps_B |v_i|^2)
   float* cac = cb + kKP;                     // a_ii - c_i
-  float* inv_s = cac + kKP;
-  float* inv_n = inv_s + kKP;                // 1 / n_i
+  float* inv_n = cac + kKP;                  // 1 / n_i
   float* red8 = inv_n + kKP;                 // [8][32]
-  const float* ab = a.abbuf + (size_t)(e % 3) * kTerms;
-  const float* ub = a.ubuf + (size_t)(e % 3) * kTerms;
   float* ubn = a.ubuf + (size_t)((e + 1) % 3) * kTerms;
   const bool tr = a.trace && ut == 0 && s >= a.nsteps - 2;
+  // quarter stamps of thread 0's row work (step before the last), in row nchunk + 1 events 0..3
+  // and the spare trace area after the per-CTA rows
+  const bool qtr = a.trace && ut == 0 && s == a.nsteps - 2;
+  auto qstamp = [&](int ev) {  // ev 0..15
+    if (qtr) a.trace2[(size_t)j * 16 + ev] = globaltimer();
+  };
   auto ustamp = [&](int ev) {  // ev 0..7
     if (tr) a.trace[((size_t)j * (a.nchunk + 2) + a.nchunk + (last ? 0 : 1)) * kEv + 4 + ev] = globaltimer();
   };
@@ -244,10 +325,10 @@ __device__ __forceinline__ bool run_update(const StreamArgs& a, int s, unsigned 
     const float4* gv = reinterpret_cast<const float4*>(a.V + goff * k);
     const float4* gs = reinterpret_cast<const float4*>(a.S + goff * k);
     const int n4 = 64 * k;
-    for (int base = 0; base < n4; base += 256 * 8) {
-      float4 xv[8], xs[8];
+    for (int base = 0; base < n4; base += 256 * 4) {
+      float4 xv[4], xs[4];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < 4; ++u) {
         const int el = base + ut + 256 * u;
         if (el < n4) {
           xv[u] = __ldcg(gv + el);
@@ -255,7 +336,7 @@ __device__ __forceinline__ bool run_update(const StreamArgs& a, int s, unsigned 
         }
       }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < 4; ++u) {
         const int el = base + ut + 256 * u;
         if (el < n4) {
           const int row = (4 * el) / k, i = 4 * el - row * k;
@@ -276,73 +357,30 @@ __device__ __forceinline__ bool run_update(const StreamArgs& a, int s, unsigned 
     vs[row * kRS + i] = 0.f;
     ss[row * kRS + i] = 0.f;
   }
-  // 2. every row-side term of the step is in (and with it every CTA's previous update)
-  if (ut == 0) {
-    const unsigned tt = (e + 1) * (unsigned)(a.b / 64);
-    *ok = spin_until_geq(a.terms_done, tt) && (s == 0 || spin_until_geq(a.upd_cnt, e * (unsigned)a.G)) &&
-                  !*abort_flag
-              ? 1
-              : 0;
-  }
+  // 2. the step's coefficients (computed once, by the builder that added its last row-side item)
+  if (ut == 0) *ok = spin_until_geq(a.coef_ready, e + 1) && !*abort_flag ? 1 : 0;
   named_barrier(3, 256);
   if (!*ok) return false;
   ustamp(1);
   {
-    // every load of the step's k x k inputs in flight at once (kk <= 4 * 256)
-    float la[4], lg[4];
+    const float* cf = a.cbuf + (size_t)(e & 1) * kCoef;
+    float t[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int p = ut + 256 * u;
-      const int i = p / k, jj = p - i * k;
-      la[u] = p < kk ? __ldcg(ab + p) : 0.f;
-      lg[u] = p < kk ? (s == 0 ? __ldcg(a.G0 + p) : __ldcg(ub + kKP + i * kKP + jj)) : 0.f;
-    }
-    const float nsq = (s > 0 && ut < k) ? __ldcg(ub + ut) : 1.f;
-    const float bq = ut < k ? __ldcg(ab + kk + ut) : 0.f;
-    const float vv = (s == 0 && ut < k) ? __ldcg(a.vv0 + ut) : 1.f;
-    if (ut < kKP) inv_n[ut] = ut < k ? (s == 0 ? 1.f : 1.f / sqrtf(nsq)) : 0.f;
-    named_barrier(3, 256);
+    for (int u = 0; u < 4; ++u) t[u] = __ldcg(cf + ut + 256 * u);
+    const float c0 = ut < kKP ? __ldcg(cf + kKP * kKP + ut) : 0.f;
+    const float c1 = ut < kKP ? __ldcg(cf + kKP * kKP + kKP + ut) : 0.f;
+    const float c2 = ut < kKP ? __ldcg(cf + kKP * kKP + 2 * kKP + ut) : 0.f;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int p = ut + 256 * u;
-      const int i = p / k, jj = p - i * k;
-      if (p < kk) {
-        Am[i * kKP + jj] = la[u] * inv_n[i] * inv_n[jj];
-        Gm[i * kKP + jj] = s == 0 ? lg[u] : lg[u] * inv_n[i];
-      }
+    for (int u = 0; u < 4; ++u) T[ut + 256 * u] = t[u];
+    if (ut < kKP) {
+      cb[ut] = c0;
+      cac[ut] = c1;
+      inv_n[ut] = c2;
     }
-    if (ut < kKP) cb[ut] = ut < k ? fmaf(a.eps_B, vv, bq * inv_n[ut] * inv_n[ut]) : 0.f;
   }
   named_barrier(3, 256);
   ustamp(2);
-  if (ut < kKP) inv_s[ut] = ut < k ? 1.f / fmaxf(Gm[ut * kKP + ut], a.rho) : 0.f;
-  named_barrier(3, 256);
-  for (int p = ut; p < kKP * kKP; p += 256) {
-    const int jj = p / kKP, i = p % kKP;
-    T[p] = (jj < i && i < k) ? cb[i] * Am[i * kKP + jj] * inv_s[jj] : 0.f;
-  }
-  {
-    // c_i = sum_{j<i} a_ij G_ij / s_j: warp w takes players 4w .. 4w + 3, the lanes run over j
-    const int w8 = warp - 4;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int i = 4 * w8 + u;
-      float c = (lane < i && i < k) ? Am[i * kKP + lane] * Gm[i * kKP + lane] * inv_s[lane] : 0.f;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-      if (lane == 0) cac[i] = i < k ? Am[i * kKP + i] - c : 0.f;
-    }
-  }
-  named_barrier(3, 256);
   ustamp(3);
-  if (last && j == 0 && a.dbg) {  // a | G | b as used (b without eps_B)
-    for (int p = ut; p < kk; p += 256) {
-      const int i = p / k, jj = p - i * k;
-      a.dbg[p] = Am[i * kKP + jj];
-      a.dbg[kk + p] = Gm[i * kKP + jj];
-    }
-    if (ut < k) a.dbg[2 * kk + ut] = __ldcg(ab + kk + ut) * inv_n[ut] * inv_n[ut];
-  }
   // 3. one row per thread, players in quarters of 8 (A_t V' and B_t V' from tensor memory)
   const float eta = a.eta[s];
   {
@@ -350,35 +388,45 @@ __device__ __forceinline__ bool run_update(const StreamArgs& a, int s, unsigned 
     const int64_t c = goff + row;
     float4* v4 = reinterpret_cast<float4*>(vs + row * kRS);
     float4* s4 = reinterpret_cast<float4*>(ss + row * kRS);
-    float sr[kKP];  // [Bv] of step t (zero beyond k)
-#pragma unroll
-    for (int i4 = 0; i4 < kKP / 4; ++i4) {
-      const float4 t = s4[i4];
-      sr[4 * i4] = t.x, sr[4 * i4 + 1] = t.y, sr[4 * i4 + 2] = t.z, sr[4 * i4 + 3] = t.w;
-    }
     const uint32_t ta0 = tmem_bp + (uint32_t)(64 * h) + ((uint32_t)(32 * q) << 16);
+    uint32_t x[8], lo[8], y[8], ylo[8];
+    tmem_ld8_nowait(ta0, x);  // quarter 0 of A_t V' (hi, lo) and B_t V' in flight during the penalty
+    tmem_ld8_nowait(ta0 + 32, lo);
+    tmem_ld8_nowait(ta0 + 128, y);
+    tmem_ld8_nowait(ta0 + 128 + 32, ylo);
+    qstamp(0);
+    // penalty_i = sum_{j<i} [Bv]_j T_ji for every player (T_ji = 0 unless j < i < k): [Bv]_j from
+    // shared memory, the zero triangle skipped at compile time
+    float gr[kKP];
+#pragma unroll
+    for (int i = 0; i < kKP; ++i) gr[i] = 0.f;
+#pragma unroll
+    for (int jj = 0; jj < kKP - 1; ++jj) {
+      const float sj = ss[row * kRS + jj];
+#pragma unroll
+      for (int i4 = (jj + 1) / 4; i4 < kKP / 4; ++i4) {
+        const float4 t = *reinterpret_cast<const float4*>(T + jj * kKP + 4 * i4);
+        gr[4 * i4] = fmaf(sj, t.x, gr[4 * i4]);
+        gr[4 * i4 + 1] = fmaf(sj, t.y, gr[4 * i4 + 1]);
+        gr[4 * i4 + 2] = fmaf(sj, t.z, gr[4 * i4 + 2]);
+        gr[4 * i4 + 3] = fmaf(sj, t.w, gr[4 * i4 + 3]);
+      }
+    }
+    qstamp(1);
     float chk = 0.f;
 #pragma unroll
     for (int qq = 0; qq < kKP / 8; ++qq) {
       const int i0 = 8 * qq;
-      uint32_t x[8], lo[8], y[8], ylo[8];
-      tmem_ld8_nowait(ta0 + i0, x);  // A_t V' (hi, lo)
-      tmem_ld8_nowait(ta0 + 32 + i0, lo);
-      tmem_ld8_nowait(ta0 + 128 + i0, y);  // B_t V' (hi, lo)
-      tmem_ld8_nowait(ta0 + 128 + 32 + i0, ylo);
-      // penalty sum_{j<i} [Bv]_j T_ji of the quarter (T_ji = 0 unless j < i < k)
-      float gr[8] = {};
-#pragma unroll
-      for (int jj = 0; jj < i0 + 7; ++jj) {
-        const float4 t0 = *reinterpret_cast<const float4*>(T + jj * kKP + i0);
-        const float4 t1 = *reinterpret_cast<const float4*>(T + jj * kKP + i0 + 4);
-        const float sj = sr[jj];
-        gr[0] = fmaf(sj, t0.x, gr[0]), gr[1] = fmaf(sj, t0.y, gr[1]), gr[2] = fmaf(sj, t0.z, gr[2]);
-        gr[3] = fmaf(sj, t0.w, gr[3]), gr[4] = fmaf(sj, t1.x, gr[4]), gr[5] = fmaf(sj, t1.y, gr[5]);
-        gr[6] = fmaf(sj, t1.z, gr[6]), gr[7] = fmaf(sj, t1.w, gr[7]);
+      if (qq > 0) {
+        tmem_ld8_nowait(ta0 + i0, x);
+        tmem_ld8_nowait(ta0 + 32 + i0, lo);
+        tmem_ld8_nowait(ta0 + 128 + i0, y);
+        tmem_ld8_nowait(ta0 + 128 + 32 + i0, ylo);
       }
       const float4 va = v4[2 * qq], vb = v4[2 * qq + 1];
+      const float4 sa = s4[2 * qq], sb = s4[2 * qq + 1];
       const float vq[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
+      const float sq[8] = {sa.x, sa.y, sa.z, sa.w, sb.x, sb.y, sb.z, sb.w};
       tmem_wait_ld32(x, lo, y, ylo);
       float vn[8], sn[8];
 #pragma unroll
@@ -388,22 +436,21 @@ __device__ __forceinline__ bool run_update(const StreamArgs& a, int s, unsigned 
         const float av = (__uint_as_float(x[u]) + __uint_as_float(lo[u])) * a.inv_nA * inv_n[i];
         const float bvr = (__uint_as_float(y[u]) + __uint_as_float(ylo[u])) * a.inv_nB * inv_n[i];
         const float bv = fmaf(a.eps_B, v, bvr);
-        const float g = cb[i] * av - gr[u] - cac[i] * bv;
+        const float g = cb[i] * av - gr[i] - cac[i] * bv;
         vn[u] = i < k ? fmaf(eta, g, v) : 0.f;
-        sn[u] = i < k ? fmaf(a.gamma, bv - sr[i], sr[i]) : 0.f;
+        sn[u] = i < k ? fmaf(a.gamma, bv - sq[u], sq[u]) : 0.f;
         chk += vn[u] + sn[u];
-        if (last && i < k) {
-          if (a.grad_out) a.grad_out[c * k + i] = g;
-          if (a.AV) {
-            a.AV[c * k + i] = av;
-            a.BV[c * k + i] = bvr;
-          }
+        if (last && i < k && a.AV) {  // debug readback: update direction, A_t V, B_t V
+          a.grad_out[c * k + i] = g;
+          a.AV[c * k + i] = av;
+          a.BV[c * k + i] = bvr;
         }
       }
       v4[2 * qq] = make_float4(vn[0], vn[1], vn[2], vn[3]);
       v4[2 * qq + 1] = make_float4(vn[4], vn[5], vn[6], vn[7]);
       s4[2 * qq] = make_float4(sn[0], sn[1], sn[2], sn[3]);
       s4[2 * qq + 1] = make_float4(sn[4], sn[5], sn[6], sn[7]);
+      qstamp(2 + qq);
     }
     if (!isfinite(chk)) atomicOr(a.dflag, kFlagNonFinite);
   }
@@ -478,10 +525,21 @@ __device__ __forceinline__ bool run_update(const StreamArgs& a, int s, unsigned 
     }
   };
   auto write_rows = [&]() {  // rows of V (v'' or v''/n) and [Bv]''
-    for (int el = ut; el < 256 * k; el += 256) {
-      const int row = el / k, i = el - row * k;
-      a.V[goff * k + el] = vs[row * kRS + i];
-      a.S[goff * k + el] = ss[row * kRS + i];
+    if ((k & 3) == 0) {
+      const int k4 = k / 4;
+      float4* gv = reinterpret_cast<float4*>(a.V + goff * k);
+      float4* gs = reinterpret_cast<float4*>(a.S + goff * k);
+      for (int el = ut; el < 256 * k4; el += 256) {
+        const int row = el / k4, i = 4 * (el - row * k4);
+        gv[el] = *reinterpret_cast<const float4*>(vs + row * kRS + i);
+        gs[el] = *reinterpret_cast<const float4*>(ss + row * kRS + i);
+      }
+    } else {
+      for (int el = ut; el < 256 * k; el += 256) {
+        const int row = el / k, i = el - row * k;
+        a.V[goff * k + el] = vs[row * kRS + i];
+        a.S[goff * k + el] = ss[row * kRS + i];
+      }
     }
   };
   auto clear_slots = [&]() {  // CTA 0: slots read by the previous step in every CTA, for step e + 2
@@ -495,21 +553,20 @@ __device__ __forceinline__ bool run_update(const StreamArgs& a, int s, unsigned 
     }
   };
   if (!last) {
-    // 4. the next step's operand first (what its projections wait for), released
+    // 4. the next step's operand first (what its projections wait for), released; then the
+    //    rows of V'' and [Bv]'' (the helpers read them for the Grams of the next update)
     write_operand();
     fence_proxy_async_global();  // the operand is read by TMA (async proxy) in other CTAs
     __threadfence();
     named_barrier(3, 256);
     if (ut == 0) red_release_add(a.upd_done + j, 1u);
     ustamp(5);
-    // 5. off the critical path: rows of V'' and [Bv]'', the Grams the next update needs
     write_rows();
-    add_grams();
     clear_slots();
     __threadfence();
     named_barrier(3, 256);
     if (ut == 0) {
-      red_release_add(a.upd_cnt, 1u);
+      red_release_add(a.rows_done + j, 1u);
       mbar_arrive(br_free);
     }
     ustamp(7);
@@ -549,7 +606,7 @@ __device__ __forceinline__ bool run_update(const StreamArgs& a, int s, unsigned 
   named_barrier(3, 256);
   if (ut == 0) {
     red_release_add(a.upd_done + j, 1u);
-    red_release_add(a.upd_cnt, 1u);
+    red_release_add(a.rows_done + j, 1u);
     mbar_arrive(br_free);
   }
   ustamp(7);
@@ -590,6 +647,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   volatile int* epi_ok = abort_flag + 2;
   volatile int* bld_ok = abort_flag + 3;
   volatile int* upd_ok = abort_flag + 4;
+  volatile int* bld_last = abort_flag + 6;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int G = a.G, j = (int)blockIdx.x;
@@ -646,7 +704,122 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (tid == 0) stamp(0);
 
   if (helper) {
-    if (warp >= 8) {
+    if (warp < 8 && j - G < G) {  // helpers that own at least one slice (the others never release)
+      // ---- Grams of the next update: |v_i|^2 and U = V^T [Bv] over the rows the streaming
+      //      CTAs' updates just wrote (step s reads the players of step s, still unnormalised),
+      //      slices hid, hid + H, ... accumulated in registers, then added into ubuf[e % 3] ----
+      const int gt = tid;  // 0..255
+      const int k = a.k;
+      const int hid = j - G;
+      float* vs = reinterpret_cast<float*>(BR);  // [256][kRS]
+      float* ss = vs + 256 * kRS;
+      float* red8 = ESTG;                        // [8][32]
+      volatile int* g_ok = abort_flag + 5;
+      const int i0 = 4 * warp, l0 = 4 * (lane & 7), rq = lane >> 3;
+      auto hstamp = [&](int s, int ev) {  // the last step's Gram phase of this helper
+        if (a.trace2 && gt == 0 && s == nsteps - 1) a.trace2[(size_t)j * 16 + ev] = globaltimer();
+      };
+      for (int s = 1; s < nsteps; ++s) {
+        const unsigned e = a.e0 + (unsigned)s;
+        float u[4][4] = {};
+        float s2 = 0.f;
+        bool alive = true;
+        hstamp(s, 0);
+        for (int sl = hid; sl < G; sl += H) {
+          if (gt == 0) *g_ok = !*abort_flag && spin_until_geq(a.rows_done + sl, e) ? 1 : 0;
+          named_barrier(4, 256);
+          if (!*g_ok) {
+            if (gt == 0) fail();
+            alive = false;
+            break;
+          }
+          if (sl == hid) hstamp(s, 1);
+          const int64_t goff = (int64_t)sl * 256;
+          if ((k & 3) == 0) {  // all of the slice's float4 loads in flight (8 of V and 8 of S per thread at k = 32)
+            const float4* gv = reinterpret_cast<const float4*>(a.V + goff * k);
+            const float4* gs = reinterpret_cast<const float4*>(a.S + goff * k);
+            const int n4 = 64 * k, k4 = k / 4;
+            for (int base = 0; base < n4; base += 256 * 8) {
+              float4 xv[8], xs[8];
+#pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                const int el = base + gt + 256 * u;
+                if (el < n4) {
+                  xv[u] = __ldcg(gv + el);
+                  xs[u] = __ldcg(gs + el);
+                }
+              }
+#pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                const int el = base + gt + 256 * u;
+                if (el < n4) {
+                  const int row = el / k4, i = 4 * (el - row * k4);
+                  *reinterpret_cast<float4*>(vs + row * kRS + i) = xv[u];
+                  *reinterpret_cast<float4*>(ss + row * kRS + i) = xs[u];
+                }
+              }
+            }
+          } else {
+            for (int el = gt; el < 256 * k; el += 256) {
+              const int row = el / k, i = el - row * k;
+              vs[row * kRS + i] = __ldcg(a.V + goff * k + el);
+              ss[row * kRS + i] = __ldcg(a.S + goff * k + el);
+            }
+          }
+          for (int el = gt; el < 256 * (kKP - k); el += 256) {
+            const int row = el / (kKP - k), i = k + el % (kKP - k);
+            vs[row * kRS + i] = 0.f;
+            ss[row * kRS + i] = 0.f;
+          }
+          named_barrier(4, 256);
+          {
+            const int i = gt & 31, g = gt >> 5;
+#pragma unroll 8
+            for (int row = 32 * g; row < 32 * g + 32; ++row) s2 = fmaf(vs[row * kRS + i], vs[row * kRS + i], s2);
+          }
+#pragma unroll 4
+          for (int it = 0; it < 64; ++it) {
+            const int row = 4 * it + rq;
+            const float4 v = *reinterpret_cast<const float4*>(vs + row * kRS + i0);
+            const float4 t = *reinterpret_cast<const float4*>(ss + row * kRS + l0);
+            const float vv4[4] = {v.x, v.y, v.z, v.w}, tt[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+              for (int r2 = 0; r2 < 4; ++r2) u[p][r2] = fmaf(vv4[p], tt[r2], u[p][r2]);
+          }
+          named_barrier(4, 256);  // the next slice overwrites the rows
+        }
+        if (!alive) break;
+        float* ub = a.ubuf + (size_t)(e % 3) * kTerms;
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int r2 = 0; r2 < 4; ++r2) {
+            u[p][r2] += __shfl_xor_sync(0xffffffffu, u[p][r2], 8);
+            u[p][r2] += __shfl_xor_sync(0xffffffffu, u[p][r2], 16);
+          }
+        if (rq == 0) {
+#pragma unroll
+          for (int p = 0; p < 4; ++p)
+            if (i0 + p < k)
+              atomicAdd(reinterpret_cast<float4*>(ub + kKP + (i0 + p) * kKP + l0),
+                        make_float4(u[p][0], u[p][1], u[p][2], u[p][3]));
+        }
+        red8[(gt >> 5) * kKP + (gt & 31)] = s2;
+        named_barrier(4, 256);
+        if (gt < k) {
+          float t2 = 0.f;
+#pragma unroll
+          for (int g = 0; g < 8; ++g) t2 += red8[g * kKP + gt];
+          atomicAdd(ub + gt, t2);
+        }
+        __threadfence();
+        named_barrier(4, 256);
+        if (gt == 0) red_release_add(a.grams_done, 1u);
+        hstamp(s, 2);
+      }
+    } else if (warp >= 8) {
       // ---- builders: summed rows -> BF16 hi/lo operand, then the row-side terms ----
       const int bt = tid - 256;
       const int k = a.k;
@@ -762,8 +935,17 @@ __global__ void __launch_bounds__(kThreads, 1)
           __threadfence();
           named_barrier(2, 128);  // staging is reused by the next item
           if (bt == 0) {
-            red_release_add(a.terms_done, 1u);
+            // the builder whose item completes the step's count computes the coefficients
+            const unsigned before = atom_add_acq_rel(a.terms_done, 1u);
+            *bld_last = before + 1 == (e + 1) * (unsigned)(2 * nrt) ? 1 : 0;
             if ((item & 1) == 0) cstamp(s, rt / kRT, kEvTerms);
+          }
+          named_barrier(2, 128);
+          if (*bld_last && !build_coefficients(a, s, e, bt, reinterpret_cast<float*>(VT) + 2 * kStgRows * 32,
+                                               bld_ok)) {
+            if (bt == 0) fail();
+            alive = false;
+            break;
           }
         }
       }
@@ -789,6 +971,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           const int row0 = (int)((int64_t)s * a.b) + (c * kRT + p_rtl) * 128;
           cstamp(s, c, kEvIssue);
+          if (s > 0 && c == 0) {
+            // the step's first two tiles into L2 while the previous step's update runs (the
+            // stages hold only half a tile, and HBM is idle during the update)
+            for (int cc = 0; cc < 2 && cc < nchunk; ++cc)
+              for (int ks = 0; ks < nks; ++ks)
+                tma_prefetch_2d(mZ, (int)(p_col0 + 64 * ks), (int)((int64_t)s * a.b) + (cc * kRT + p_rtl) * 128);
+          }
           for (int ks = 0; ks < nks; ++ks, ++i) {
             const int st = i % kPS;
             if (i >= kPS && !mbar_wait(p_empty + st, ((i / kPS) - 1) & 1)) {
@@ -1074,9 +1263,11 @@ int tc_stream_max_steps() { return kMaxSteps; }
 
 static size_t counters_len(const Ctx& c) {
   const size_t nrt = (size_t)c.cfg.max_b / 128;
-  // [nrt] contributions | [2 nrt] operand flags | terms | barrier | updates | [num_sms] per-CTA updates
-  return 3 * nrt + 3 + (size_t)c.num_sms;
+  // [nrt] contributions | [2 nrt] operand flags | terms | barrier | Grams | coefficients |
+  // [num_sms] per-CTA operands | [num_sms] per-CTA rows
+  return 3 * nrt + 4 + 2 * (size_t)c.num_sms;
 }
+constexpr size_t kTermFloats = 6 * (size_t)kTerms + 2 * (size_t)kCoef;  // abbuf | ubuf | cbuf
 
 int tc_stream_setup(Ctx& c) {
   c.tc_st_ok = 0;
@@ -1092,8 +1283,8 @@ int tc_stream_setup(Ctx& c) {
   }
   SGEP_CUDA_TRY(cudaMalloc((void**)&c.tc_st_cnt, counters_len(c) * sizeof(unsigned)));
   SGEP_CUDA_TRY(cudaMemset(c.tc_st_cnt, 0, counters_len(c) * sizeof(unsigned)));
-  SGEP_CUDA_TRY(cudaMalloc((void**)&c.tc_st_terms, 6 * (size_t)kTerms * sizeof(float)));
-  SGEP_CUDA_TRY(cudaMemset(c.tc_st_terms, 0, 6 * (size_t)kTerms * sizeof(float)));
+  SGEP_CUDA_TRY(cudaMalloc((void**)&c.tc_st_terms, kTermFloats * sizeof(float)));
+  SGEP_CUDA_TRY(cudaMemset(c.tc_st_terms, 0, kTermFloats * sizeof(float)));
   c.tc_st_last_b = 0;
   // tuning knobs: SGEP_TC_LAG (chunks the projection may run ahead, 2..8; each chunk is
   // 256 rows of the minibatch kept in L2) and SGEP_TC_HELPERS (builder CTAs, 1..24)
@@ -1107,7 +1298,7 @@ int tc_stream_setup(Ctx& c) {
   c.tc_pq_dirty = 1;
   const char* tr = getenv("SGEP_TRACE");
   if (tr && tr[0] == '1') {
-    const size_t n = (size_t)c.num_sms * ((size_t)c.cfg.max_b / kR + 2) * kEv;
+    const size_t n = (size_t)c.num_sms * ((size_t)c.cfg.max_b / kR + 2) * kEv + (size_t)c.num_sms * 16;
     SGEP_CUDA_TRY(cudaMalloc((void**)&c.tc_st_trace, n * sizeof(unsigned long long)));
     SGEP_CUDA_TRY(cudaMemset(c.tc_st_trace, 0, n * sizeof(unsigned long long)));
   }
@@ -1141,10 +1332,11 @@ int tc_stream_steps(Ctx& c, const void* X, const void* Y, int64_t b, int nsteps,
   // and term slots) after an aborted launch, when the size changes and before they could wrap
   if (c.tc_st_reset || c.tc_st_epoch + (unsigned)nsteps >= (1u << 20) || b != c.tc_st_last_b) {
     SGEP_CUDA_TRY(cudaMemsetAsync(c.tc_st_cnt, 0, counters_len(c) * sizeof(unsigned), s));
-    SGEP_CUDA_TRY(cudaMemsetAsync(c.tc_st_terms, 0, 6 * (size_t)kTerms * sizeof(float), s));
+    SGEP_CUDA_TRY(cudaMemsetAsync(c.tc_st_terms, 0, kTermFloats * sizeof(float), s));
     c.tc_st_last_b = b;
     c.tc_st_epoch = 0;
     c.tc_st_launch = 0;
+    c.tc_st_grams = 0;
     c.tc_st_reset = 0;
     c.tc_pq_dirty = 1;
   }
@@ -1198,11 +1390,16 @@ int tc_stream_steps(Ctx& c, const void* X, const void* Y, int64_t b, int nsteps,
   sa.wready = c.tc_st_cnt + nrt_max;
   sa.terms_done = c.tc_st_cnt + 3 * nrt_max;
   sa.bar = sa.terms_done + 1;
-  sa.upd_cnt = sa.terms_done + 2;
-  sa.upd_done = sa.terms_done + 3;
+  sa.grams_done = sa.terms_done + 2;
+  sa.coef_ready = sa.terms_done + 3;
+  sa.grams_base = c.tc_st_grams;
+  sa.H = H;
+  sa.upd_done = sa.terms_done + 4;
+  sa.rows_done = sa.upd_done + c.num_sms;
   sa.bar_target = (c.tc_st_launch + 1) * (unsigned)G;
   sa.abbuf = c.tc_st_terms;
   sa.ubuf = c.tc_st_terms + 3 * kTerms;
+  sa.cbuf = c.tc_st_terms + 6 * kTerms;
   sa.V = c.V;
   sa.S = c.S;
   sa.G0 = t0.G;
@@ -1217,10 +1414,13 @@ int tc_stream_steps(Ctx& c, const void* X, const void* Y, int64_t b, int nsteps,
   sa.grad_out = dbg ? c.grad : nullptr;
   sa.dflag = c.dflag;
   sa.trace = c.tc_st_trace;
+  sa.trace2 = c.tc_st_trace ? c.tc_st_trace + (size_t)c.num_sms * ((size_t)c.cfg.max_b / kR + 2) * kEv : nullptr;
   c.tc_st_nchunk = sa.nchunk;
   if (c.tc_st_trace)
     SGEP_CUDA_TRY(cudaMemsetAsync(c.tc_st_trace, 0,
-                                  (size_t)c.num_sms * ((size_t)c.cfg.max_b / kR + 2) * kEv * sizeof(unsigned long long), s));
+                                  ((size_t)c.num_sms * ((size_t)c.cfg.max_b / kR + 2) * kEv + (size_t)c.num_sms * 16) *
+                                      sizeof(unsigned long long),
+                                  s));
   c.tc_st_grid = G + H;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(G + H));
@@ -1234,6 +1434,7 @@ int tc_stream_steps(Ctx& c, const void* X, const void* Y, int64_t b, int nsteps,
   cfg.numAttrs = 1;
   SGEP_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_tc_stream, mX, mY, mX64, mY64, mVt, mPt, mQt, sa));
   c.tc_st_epoch += (unsigned)nsteps;
+  c.tc_st_grams += (unsigned)((nsteps - 1) * std::min(H, G));  // one release per step by each slice owner
   ++c.tc_st_launch;
   c.tc_acc_stale = dbg ? 0 : 1;
   c.tc_chain = 1;
@@ -1271,6 +1472,33 @@ void tc_stream_trace_report(Ctx& c) {
   row(nc, upd, 4, 8);
   std::fprintf(stderr, "[sgep trace]   update, step before:");
   row(nc + 1, upd, 4, 8);
+  {
+    std::vector<unsigned long long> t2((size_t)n * 16);
+    const size_t off = (size_t)c.num_sms * ((size_t)c.cfg.max_b / kR + 2) * kEv;
+    if (cudaMemcpy(t2.data(), c.tc_st_trace + off, t2.size() * 8, cudaMemcpyDeviceToHost) == cudaSuccess) {
+      std::fprintf(stderr, "[sgep trace]   row work quarters (start, issued, waited, stored), CTA 0:");
+      for (int ev = 0; ev < 16; ++ev)
+        std::fprintf(stderr, " %.2f", t2[ev] >= g0 ? ((double)t2[ev] - (double)g0) / 1e3 : -1.0);
+      std::fprintf(stderr, "\n");
+    }
+  }
+  {
+    std::vector<unsigned long long> t2((size_t)n * 16);
+    const size_t off = (size_t)c.num_sms * ((size_t)c.cfg.max_b / kR + 2) * kEv;
+    const int G = (int)(c.d_x / 128);
+    if (cudaMemcpy(t2.data(), c.tc_st_trace + off, t2.size() * 8, cudaMemcpyDeviceToHost) == cudaSuccess) {
+      const char* hn[3] = {"step", "first slice", "released"};
+      std::fprintf(stderr, "[sgep trace]   helper Grams, last step:");
+      for (int ev = 0; ev < 3; ++ev) {
+        std::vector<double> v;
+        for (int b = G; b < n; ++b)
+          if (t2[(size_t)b * 16 + ev] >= g0) v.push_back(((double)t2[(size_t)b * 16 + ev] - (double)g0) / 1e3);
+        std::sort(v.begin(), v.end());
+        if (!v.empty()) std::fprintf(stderr, " %s %.2f/%.2f", hn[ev], v[v.size() / 2], v.back());
+      }
+      std::fprintf(stderr, "\n");
+    }
+  }
   const char* names[8] = {"issue", "mma", "release", "build0", "built", "Wseen", "bpdone", "terms"};
   for (int ch : {0, 1, 2, nc / 2, nc - 2, nc - 1}) {
     if (ch < 0 || ch >= nc) continue;
