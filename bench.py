@@ -2,7 +2,7 @@
 
 Default workload: activation-like CCA, d_x = d_y = 16384 (d = 32768), k = 32 players,
 minibatch b = 4096 rows in BF16 (268 MB per minibatch), power-law noise spectrum with 64
-planted shared directions. A pool of 65,536 rows (16 minibatches, 4.3 GB) is generated on
+planted shared directions. A pool of 131,072 rows (32 minibatches, 8.6 GB) is generated on
 the device before timing; timed steps stream consecutive minibatches through it, so the
 inputs exceed L2 and every step reads fresh rows from HBM. The other workloads (the
 1024-dim FP32 CCA with its time-to-1e-3 runs, the FP32 form of the large problem, the
@@ -39,7 +39,7 @@ WORKLOADS = {
     # name: (synth config function, dtype, pool rows)
     "cca_d1024_k16_b1024_f32": ("config_c2", "f32", 1_000_000),
     "cca_d64_k4_b256_f32": ("config_c1", "f32", 10_000),
-    # activation-like CCA, d_x = d_y = 16384, k = 32, b = 4096, BF16 rows (16 minibatches = 4.3 GB)
+    # activation-like CCA, d_x = d_y = 16384, k = 32, b = 4096, BF16 rows (32 minibatches = 8.6 GB)
     "cca_d32768_k32_b4096_bf16": ("config_c3", "bf16", 65_536),
     "cca_d32768_k32_b4096_f32": ("config_c3", "f32", 16_384),
 }
@@ -68,7 +68,11 @@ def parse():
 # DRAM bytes (read + write) per step of the dominant kernel from one ncu capture of the
 # current kernel (profiles/); an entry is removed whenever the kernel changes until it is
 # captured again.
-TRAFFIC_BYTES = {}
+TRAFFIC_BYTES = {
+    # k_tc_stream: (645.3 MB read + 20.1 MB written) in one launch of 2 steps, from the ncu
+    # capture summarised under profiles/
+    "cca_d32768_k32_b4096_bf16": 332_700_928,
+}
 
 
 def world_max(value: float, world: int, device=None) -> float:
@@ -584,15 +588,20 @@ def measure_warm(dev, seed=0, n_train=128, n_eval=16, max_steps=8000, check_ever
            "train_loss": [first, last], "train_seconds_host": train_s,
            "warm_start_inference_ms_per_instance": {"wall": infer_ms, "device": infer_dev_ms},
            "target": target, "truth": "exact solution of each held-out instance's resident row pool"}
+    # Both starts run the same number of batched steps (max_steps); an instance's steps to the
+    # target are read off its error every check_every steps, and the device time to the target
+    # is those steps times the measured time per batched step divided by the batch size (the
+    # batch runs all instances at once), so neither start is charged for the other instances.
     for name, init in (("cold", None), ("warm", V0)):
         ss = solvers(n_eval, init)
         reached = [None] * n_eval
         err0 = [gen_subspace_error(Vt, s_.V().astype(np.float64), B) for s_, (Vt, B) in zip(ss, truths)]
         dev_ms = 0.0
         curve = []
+        err_at = {}
         with Batch(ss) as bt:
             t = 0
-            while t < max_steps and any(r is None for r in reached):
+            while t < max_steps:
                 e0.record()
                 run(bt, hp, t, check_every)
                 e1.record()
@@ -605,13 +614,20 @@ def measure_warm(dev, seed=0, n_train=128, n_eval=16, max_steps=8000, check_ever
                     errs.append(e)
                     if reached[i] is None and e <= target:
                         reached[i] = t
+                if t in (200, 1000, max_steps):
+                    err_at[t] = float(np.median(errs))
                 if t % (5 * check_every) == 0:
                     curve.append([t, round(float(np.median(errs)), 6)])
             bt.sync()
+        ms_per_step = dev_ms / t
         steps = [r for r in reached if r is not None]
+        med = float(np.median([r if r is not None else np.inf for r in reached]))
         out[name] = {"initial_error_median": float(np.median(err0)), "reached": len(steps), "of": n_eval,
-                     "median_steps": float(np.median(steps)) if steps else None,
-                     "device_seconds_all_instances": dev_ms / 1e3, "steps_run": t, "median_error_curve": curve}
+                     "median_steps_to_target": med if np.isfinite(med) else None,
+                     "median_device_seconds_to_target_per_instance":
+                         med * ms_per_step / 1e3 / n_eval if np.isfinite(med) else None,
+                     "median_error_at_steps": err_at, "steps_run": t,
+                     "batched_step_ms": ms_per_step, "median_error_curve": curve}
         for s_ in ss:
             s_.close()
     ws.close()
@@ -767,6 +783,7 @@ def run_native(args):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak,
                 "traffic": TRAFFIC_BYTES.get(args.workload) if one_kernel else None,
+                "traffic_unit": "DRAM bytes read + written per step (one ncu capture)",
                 "kernel": kernels[solver.path] if one_kernel else f"whole step, path {solver.path}",
                 "peak_source": peak_kind, "alg_bytes_per_step": alg_bytes,
                 "alg_bytes_formula": "b d (element bytes) + 16 d k",
@@ -782,15 +799,35 @@ def run_native(args):
         for i in range(4):
             Xh[i].copy_(X[i * b:(i + 1) * b])
             Yh[i].copy_(Y[i * b:(i + 1) * b])
-        Xd = torch.empty((b, dx), dtype=X.dtype, device=dev)
-        Yd = torch.empty((b, dy), dtype=Y.dtype, device=dev)
+        # two device buffers: the copies of step i + 1 (X and Y on their own copy streams) run
+        # while step i computes; every step's V is read back to the host before the next step
+        Xd = [torch.empty((b, dx), dtype=X.dtype, device=dev) for _ in range(2)]
+        Yd = [torch.empty((b, dy), dtype=Y.dtype, device=dev) for _ in range(2)]
+        cs = [torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)]
+        ready = [[torch.cuda.Event(), torch.cuda.Event()] for _ in range(2)]
+        freed = [torch.cuda.Event(), torch.cuda.Event()]
         Vh = np.empty((d, k), dtype=np.float32)
+
+        def issue_copy(i):
+            u = i % 2
+            for which, (dst, src) in enumerate(((Xd[u], Xh[i % 4]), (Yd[u], Yh[i % 4]))):
+                with torch.cuda.stream(cs[which]):
+                    if i >= 2:
+                        cs[which].wait_event(freed[u])  # the step that read this buffer is done
+                    dst.copy_(src, non_blocking=True)
+                    ready[u][which].record(cs[which])
+
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        issue_copy(0)
         for i in range(ne):
-            Xd.copy_(Xh[i % 4], non_blocking=True)
-            Yd.copy_(Yh[i % 4], non_blocking=True)
-            solver.step(Xd, Yd)
+            u = i % 2
+            stream.wait_event(ready[u][0])
+            stream.wait_event(ready[u][1])
+            solver.step(Xd[u], Yd[u])
+            freed[u].record(stream)
+            if i + 1 < ne:
+                issue_copy(i + 1)
             sgep.sgep_get_V(solver.h, Vh, False, stream.cuda_stream)
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
