@@ -104,6 +104,7 @@ struct Ctx {
   float* tc_st_terms = nullptr;    // [3] row-side term slots a | b, then [3] slots |v'|^2 | U
   unsigned tc_st_launch = 0;       // streamed launches since the counters were last cleared
   unsigned tc_st_grams = 0;        // helper Gram contributions since then
+  int tc_st_bp_groups = 0;         // the last streamed launch loaded its back-projection rows in one copy per step
   int tc_st_updated = 0;           // the most recent streamed launch applied the step's update
   int64_t tc_st_last_b = 0;        // minibatch size the counters were last used with
   int tc_acc_stale = 0;            // acc does not hold the last step's products (not kept)
@@ -231,6 +232,10 @@ int generic_rayleigh_sums(Ctx& c, int64_t n, cudaStream_t s);
 // 2-D BF16 row-major tensor map, 128-byte swizzle, box_rows x box_cols (box_cols * 2 == 128).
 int make_map_bf16(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows,
                   int box_cols);
+// The same matrix viewed as (64 columns, rows, column groups): a box of box_rows x `groups`
+// groups lands as `groups` consecutive 2-D boxes of 64 columns (one copy).
+int make_map_bf16_groups(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows,
+                         int groups);
 bool tc_supported(const Ctx& c, const char** why);
 int tc_alloc(Ctx& c);
 void tc_free(Ctx& c);

@@ -59,6 +59,24 @@ int make_map_bf16(CUtensorMap* map, const void* base, int64_t rows, int64_t cols
   return SGEP_OK;
 }
 
+// 3-D view of a BF16 row-major matrix [rows][cols] (row stride `ld` elements) as (64 columns,
+// rows, cols / 64 column groups): one box of box_rows rows x `groups` groups lands as `groups`
+// consecutive [box_rows][64] sub-boxes with 128-byte swizzle, the layout of that many 2-D boxes
+// of 64 columns, in one copy. Returns SGEP_ECUDA when the driver does not take the view.
+int make_map_bf16_groups(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows,
+                         int groups) {
+  auto fn = encode_fn();
+  if (!fn || cols % 64) return SGEP_ECUDA;
+  cuuint64_t dims[3] = {64, (cuuint64_t)rows, (cuuint64_t)(cols / 64)};
+  cuuint64_t strides[2] = {(cuuint64_t)ld * 2, 128};
+  cuuint32_t box[3] = {64, (cuuint32_t)box_rows, (cuuint32_t)groups};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? SGEP_OK : SGEP_ECUDA;
+}
+
 namespace {
 
 using namespace tc;

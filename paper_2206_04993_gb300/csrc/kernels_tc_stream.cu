@@ -101,6 +101,7 @@ struct StreamArgs {
   int lag;                  // chunks the projection may run ahead of the CTA's back-projection
   int nsteps;               // consecutive minibatches of this launch (rows s*b .. s*b + b - 1)
   int serial;               // the next step's projection also waits for the CTA's own update
+  int bp_groups;            // mapX64 / mapY64 are 3-D views: one copy per 64-row back-projection step
   unsigned e0;              // steps streamed since the counters were cleared (epoch of step 0)
   float inv_nA, inv_nB;
   float rho, gamma, eps_B;
@@ -1092,9 +1093,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint8_t* sa = BR + st * kBStage;
             mbar_arrive_expect_tx(b_full + st, kBStage);
             const int rg = (int)((int64_t)s * a.b) + r0;
+            if (a.bp_groups)  // the four 64-column boxes in one copy (3-D view of the rows)
+              tma_load_3d_hint(sa, mZ, 0, rg, (int)(b_c0 / 64), b_full + st, once);
+            else
 #pragma unroll
-            for (int jb = 0; jb < 4; ++jb)
-              tma_load_2d_hint(sa + jb * 8192, mZ, (int)(b_c0 + 64 * jb), rg, b_full + st, once);
+              for (int jb = 0; jb < 4; ++jb)
+                tma_load_2d_hint(sa + jb * 8192, mZ, (int)(b_c0 + 64 * jb), rg, b_full + st, once);
             tma_load_2d(sa + 32768, r0 < a.nA ? mWA : mWB, r0, 0, b_full + st);
           }
         }
@@ -1348,8 +1352,15 @@ int tc_stream_steps(Ctx& c, const void* X, const void* Y, int64_t b, int nsteps,
   CUtensorMap mX, mY, mX64, mY64, mVt, mPt, mQt;
   int rc = make_map_bf16(&mX, X, rows, c.d_x, c.d_x, 128, 64);
   if (!rc) rc = make_map_bf16(&mY, Y, rows, c.d_y, c.d_y, 128, 64);
-  if (!rc) rc = make_map_bf16(&mX64, X, rows, c.d_x, c.d_x, 64, 64);
-  if (!rc) rc = make_map_bf16(&mY64, Y, rows, c.d_y, c.d_y, 64, 64);
+  // the back-projection's 64-row steps: one copy of 64 rows x 256 columns through a 3-D view
+  // where the driver takes it (SGEP_TC_BP_GROUPS=0 keeps four 2-D boxes per step)
+  const char* bg = getenv("SGEP_TC_BP_GROUPS");
+  int bp_groups = !(bg && bg[0] == '0') && make_map_bf16_groups(&mX64, X, rows, c.d_x, c.d_x, 64, 4) == SGEP_OK &&
+                  make_map_bf16_groups(&mY64, Y, rows, c.d_y, c.d_y, 64, 4) == SGEP_OK;
+  if (!bp_groups) {
+    if (!rc) rc = make_map_bf16(&mX64, X, rows, c.d_x, c.d_x, 64, 64);
+    if (!rc) rc = make_map_bf16(&mY64, Y, rows, c.d_y, c.d_y, 64, 64);
+  }
   if (!rc) rc = make_map_bf16(&mVt, c.tc_Vt, 2 * 32, c.d, c.d, 64, 64);
   if (!rc) rc = make_map_bf16(&mPt, c.tc_Pt, 2 * 32, b, c.cfg.max_b, 64, 64);
   if (!rc) rc = make_map_bf16(&mQt, c.tc_Qt, 2 * 32, b, c.cfg.max_b, 64, 64);
@@ -1363,6 +1374,8 @@ int tc_stream_steps(Ctx& c, const void* X, const void* Y, int64_t b, int nsteps,
   sa.G = G;
   sa.lag = c.tc_st_lag;
   sa.nsteps = nsteps;
+  sa.bp_groups = bp_groups;
+  c.tc_st_bp_groups = bp_groups;
   {
     const char* se = getenv("SGEP_TC_SERIAL");
     sa.serial = (se && se[0] == '1') ? 1 : 0;
@@ -1464,8 +1477,8 @@ void tc_stream_trace_report(Ctx& c) {
     std::fprintf(stderr, "\n");
   };
   const char* tot[4] = {"start", "proj", "end", "exit"};
-  std::fprintf(stderr, "[sgep trace] streamed steps, %d CTAs (%d helpers), %d chunks (us, median/max):", n,
-               n - (int)(c.d_x / 128), nc);
+  std::fprintf(stderr, "[sgep trace] streamed steps, %d CTAs (%d helpers), %d chunks, back-projection copies %s (us, median/max):",
+               n, n - (int)(c.d_x / 128), nc, c.tc_st_bp_groups ? "3-D" : "2-D");
   row(nc, tot, 0, 4);
   const char* upd[8] = {"entry", "terms", "coef", "T", "rows", "operand/grams", "bar", "done"};
   std::fprintf(stderr, "[sgep trace]   update, last step:");
