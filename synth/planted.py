@@ -226,8 +226,10 @@ def config_c1(seed: int = 0):
     model = planted_cca(32, 32, rhos, sigma=0.5, seed=seed)
     X, Y = draw_rows(model, 10_000, batch=_STREAM_FINITE)
     return {"name": "cca_d64_k4_b256", "model": model, "X": X, "Y": Y, "k": 4, "b": 256,
-            "steps": 2000, "eta0": 0.2, "gamma0": 0.3, "rho": 1e-6,
-            "schedule": 1, "t_c": 100, "T": 2000, "eta_T": 0.2 * 120.0 / 2020.0}
+            # hold 0.3 for 300 steps, then harmonic down to 0.3 * 0.012 at step 2000 (the best
+            # point of a sweep of eta0, t_c and eta_T / eta0 on the oracle: error floor ~8.6e-4)
+            "steps": 2000, "eta0": 0.3, "gamma0": 0.3, "rho": 1e-6,
+            "schedule": 1, "t_c": 300, "T": 2000, "eta_T": 0.3 * 0.012}
 
 
 def config_c2(seed: int = 0):

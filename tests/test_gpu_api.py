@@ -107,14 +107,14 @@ def test_initial_V_has_unit_columns_and_S_equals_V():
 
 @pytest.mark.parametrize("path", PATHS, ids=IDS)
 def test_small_cca_workload_converges_to_exact_solution(path):
-    """Alg. 2 on the finite 10,000-row CCA set (d = 64, k = 4, b = 256, 6000 steps of
+    """Alg. 2 on the finite 10,000-row CCA set (d = 64, k = 4, b = 256, 2000 steps of
     with-replacement minibatches): generalized subspace error below 1e-3 and eigenvalue
     error below 1e-3 against Cholesky + Jacobi on the finite-sample A, B."""
     cfg = synth.config_c1()
     X, Y = cfg["X"], cfg["Y"]
     A, B = gep.form_cca_AB(X, Y)
     lam, Vs = gep.gep_topk(A, B, 4)
-    steps = 6000
+    steps = cfg["steps"]
     idx = np.concatenate([synth.finite_dataset_indices(10_000, 256, t) for t in range(1, steps + 1)])
     Xd, Yd = _dev(X), _dev(Y)
     it = torch.from_numpy(idx).cuda()
