@@ -677,6 +677,139 @@ def measure_warm(dev, seed=0, n_train=128, n_eval=16, max_steps=8000, check_ever
     return out
 
 
+def planted_cca_truth(model, k):
+    """Population top-k solution of the planted CCA model with orthonormal mixing columns
+    (Qx, Qy), latent scales s and isotropic noise sigma: Cxx = Qx S^2 Qx^T + sigma^2 I,
+    Cxy = Qx S^2 Qy^T. In the bases Qx, Qy every block is diagonal, so the pencil's top
+    vectors are v_i = [Qx e_i; Qy e_i] / sqrt(2) with lambda_i = s_i^2 / (s_i^2 + sigma^2).
+    Returns (V*, lambda, B-apply)."""
+    s2, n2 = model.s ** 2, model.sigma ** 2
+    Vt = np.concatenate([model.Qx[:, :k], model.Qy[:, :k]]) / np.sqrt(2.0)
+    dx = model.d_x
+
+    def Bmv(U):
+        ux, uy = U[:dx], U[dx:]
+        return np.concatenate([model.Qx @ (s2[:, None] * (model.Qx.T @ ux)) + n2 * ux,
+                               model.Qy @ (s2[:, None] * (model.Qy.T @ uy)) + n2 * uy])
+    return Vt, s2[:k] / (s2[:k] + n2), Bmv
+
+
+def measure_warm_c5(dev, seed=0, n_train=3000, n_heldout=1096, n_tte=16, train_iters=300, slice_=250,
+                    max_steps=40_000, check_every=512, per=128, target=1e-3):
+    """Learned warm start at full size: 4096 CCA instances with d_x = d_y = 1024, k = 16 (mixing
+    a smooth function of theta in [-1, 1]^8, 16 latent directions, correlations 0.9..0.3), the
+    sketch of a 2048-row first minibatch, the per-row MLP trained on n_train instances, evaluated
+    on n_heldout. Targets are the plain solver's fixed point, the population solution (closed
+    form); the cold runs below reach it to 1e-3. Time to 1e-3 runs on the first n_tte held-out
+    instances, warm and cold from the same fresh samples (b = 2048 per step, generated outside the
+    timed region) with the same schedule and the same step cap."""
+    import torch
+    from paper_2206_04993_gb300 import Solver, WarmStart, sgep
+    fam = synth.config_c5(seed=seed + 1)
+    dx, k, b = fam["d_x"], fam["k"], 2048
+    d = 2 * dx
+    om = torch.tensor(fam["omega"], dtype=torch.float32, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def sketch_of(model, rseed):
+        X, Y = make_pool({"model": model}, b, "f32", dev, seed=rseed)
+        return WarmStart.sketch(X, Y, om)
+
+    t_data = time.time()
+    sk, tg = [], []
+    for i, th in enumerate(fam["thetas"](n_train, 0)):
+        m = fam["model"](th)
+        sk.append(sketch_of(m, 200_000 + i))
+        tg.append(torch.tensor(planted_cca_truth(m, k)[0], dtype=torch.float32, device=dev))
+    S, V = torch.cat(sk), torch.cat(tg)
+    del sk, tg
+    torch.cuda.synchronize()
+    t_data = time.time() - t_data
+    ws = WarmStart(m=16, k=k, seed=seed + 3)
+    seg_all = [j * d for j in range(n_train + 1)]
+    first = ws.loss_grad(S, V, seg_all)
+    e0.record()
+    for it in range(train_iters):
+        i0 = (it * slice_) % n_train
+        i1 = min(n_train, i0 + slice_)
+        ws.loss_grad(S[i0 * d:i1 * d], V[i0 * d:i1 * d], [j * d for j in range(i1 - i0 + 1)])
+        ws.adam_step(3e-3)
+    e1.record()
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1)
+    last = ws.loss_grad(S, V, seg_all)
+    del S, V
+    # held-out: V0 from the network, and the sketch itself as a 16-column V (its information limit)
+    held = [fam["model"](th) for th in fam["thetas"](n_heldout, 1)]
+    err_net, err_sketch, V0s, inf_ms = [], [], [], 0.0
+    for i, m in enumerate(held):
+        X, Y = make_pool({"model": m}, b, "f32", dev, seed=400_000 + i)
+        torch.cuda.synchronize()
+        e0.record()
+        Sk = WarmStart.sketch(X, Y, om)
+        O = ws.forward(Sk)
+        e1.record()
+        torch.cuda.synchronize()
+        if i > 0:
+            inf_ms += e0.elapsed_time(e1)
+        Vt, _, Bmv = planted_cca_truth(m, k)
+        o = O.double().cpu().numpy()
+        o /= np.linalg.norm(o, axis=0, keepdims=True)
+        err_net.append(gen_subspace_error_op(Vt, o, Bmv))
+        err_sketch.append(gen_subspace_error_op(Vt, Sk.double().cpu().numpy(), Bmv))
+        if i < n_tte:
+            V0s.append(o.astype(np.float32))
+    ws.close()
+    rng_cold = [synth.random_unit_columns(d, k, seed=700 + i).astype(np.float32) for i in range(n_tte)]
+    # hold 0.3 for 200 steps, then eta_t = 40 / (t + Delta): the best of eta t -> 20, 40, 80, 160
+    eta0, t_c, c = 0.3, 200, 40.0
+    delta = c / eta0 - t_c
+    eta_T = eta0 * (t_c + delta) / (max_steps + delta)
+    out = {"scale": f"full: d_x = d_y = {dx}, k = {k}, latent 16, sketch of {b} rows; {n_train} training "
+                    f"instances, {n_heldout} held-out (initial error), first {n_tte} held-out run to {target}",
+           "targets": "population solution of each instance (closed form), the plain solver's fixed point",
+           "train": {"iters": train_iters, "instances_per_iter": slice_, "loss_first_last": [first, last],
+                     "device_ms": train_ms, "data_seconds_host": t_data},
+           "inference_device_ms_per_instance": inf_ms / max(1, n_heldout - 1),
+           "initial_error_median": {"warm": float(np.median(err_net)), "sketch_itself": float(np.median(err_sketch))},
+           "schedule": {"eta0": eta0, "t_c": t_c, "eta_t_late": f"{c} / (t + {delta:.1f})"},
+           "target": target, "max_steps": max_steps}
+    for name, starts in (("cold", rng_cold), ("warm", V0s)):
+        runs = []
+        for i in range(n_tte):
+            m = held[i]
+            Vt, _, Bmv = planted_cca_truth(m, k)
+            s = Solver(kind=sgep.SGEP_CCA, d_x=dx, d_y=dx, k=k, eta0=eta0, gamma0=0.3, rho=1e-6, schedule=1,
+                       t_c=t_c, T=max_steps, eta_T=eta_T, max_b=b, seed=seed)
+            s.set_V(starts[i])
+            err0 = gen_subspace_error_op(Vt, starts[i].astype(np.float64), Bmv)
+            t, ms, hit = 0, 0.0, None
+            while t < max_steps:
+                X, Y = make_pool({"model": m}, b * per, "f32", dev, seed=500_000 + 1000 * i + t // per)
+                torch.cuda.synchronize()
+                e0.record()
+                s.step_many(X, Y, b, per)
+                e1.record()
+                torch.cuda.synchronize()
+                ms += e0.elapsed_time(e1)
+                t += per
+                del X, Y
+                if t % check_every == 0 and gen_subspace_error_op(Vt, s.V().astype(np.float64), Bmv) <= target:
+                    hit = t
+                    break
+            runs.append({"initial_error": round(err0, 4), "steps": hit, "device_seconds": ms / 1e3 if hit else None,
+                         "path": s.path})
+            s.close()
+        steps = sorted(r["steps"] if r["steps"] else np.inf for r in runs)
+        secs = sorted(r["device_seconds"] if r["device_seconds"] else np.inf for r in runs)
+        med = lambda v: float(np.median(v)) if np.isfinite(np.median(v)) else None
+        out[name] = {"reached": sum(r["steps"] is not None for r in runs), "of": n_tte,
+                     "median_steps_to_target": med(steps), "median_device_seconds_to_target": med(secs),
+                     "runs": runs}
+    torch.cuda.empty_cache()
+    return out
+
+
 def measure_c3_error(dev, rank, steps=512, eta=1e3, per=16, every=64, rr_every=128, eval_rows=8192):
     """Error against device time on the activation-like workload (d = 32768, k = 32, b = 4096):
     plain FP32 rows (generic path), BF16 rows (streamed tensor-core steps) and BF16 rows with a
@@ -956,6 +1089,8 @@ def run_native(args):
         forms["batch64_cca_lda_b512_f32"] = measure_batch("f32", 40, 3, dev, seed=rank)
         forms["batch64_cca_lda_b512_bf16"] = measure_batch("bf16", 40, 3, dev, seed=rank)
         forms["warm_start_cca_family"] = measure_warm(dev, seed=rank)
+        if not args.no_tte:
+            forms["warm_start_c5"] = measure_warm_c5(dev, seed=rank)
 
     if rank == 0:
         line = {

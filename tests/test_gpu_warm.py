@@ -157,3 +157,61 @@ def test_trained_network_beats_cold_start():
     assert warm0.mean() < 0.5 * cold0.mean()
     assert warm100.mean() < cold100.mean()
     ws.close()
+
+
+def test_full_size_family_trained_network_reaches_the_sketch_limit():
+    """The full-size family (d_x = d_y = 1024, k = 16, 2048-row sketch), trained on 3000
+    instances with the population solutions as targets: on 16 held-out instances the network's
+    V0 has a lower generalized subspace error than a random start and is within 0.03 of the
+    error of the sketch's own 16 columns (the information the network's input carries)."""
+    import torch
+    from paper_2206_04993_gb300 import WarmStart
+    fam = synth.config_c5(seed=1)
+    d_x, k = fam["d_x"], fam["k"]
+    d = 2 * d_x
+    om = _dev(fam["omega"])
+    dev = torch.device("cuda")
+    g = torch.Generator(device=dev)
+    g.manual_seed(11)
+
+    def sketch(model):
+        Wx = torch.tensor(model.Qx * model.s, dtype=torch.float32, device=dev)
+        Wy = torch.tensor(model.Qy * model.s, dtype=torch.float32, device=dev)
+        z = torch.randn(2048, model.s.size, device=dev, generator=g)
+        X = z @ Wx.T + model.sigma * torch.randn(2048, d_x, device=dev, generator=g)
+        Y = z @ Wy.T + model.sigma * torch.randn(2048, d_x, device=dev, generator=g)
+        return WarmStart.sketch(X, Y, om)
+
+    def error(model, V):
+        _, Vt = gep.cca_truth_planted(model, k)
+        return gep.subspace_error(Vt, V, lambda U: gep.cca_B_apply(model, U))
+
+    sk, tg = [], []
+    for th in fam["thetas"](3000, 0):
+        mdl = fam["model"](th)
+        sk.append(sketch(mdl))
+        tg.append(_dev(gep.cca_truth_planted(mdl, k)[1]))
+    S_all, T_all = torch.cat(sk), torch.cat(tg)
+    del sk, tg
+    ws = WarmStart(m=16, k=k, seed=3)
+    seg = [i * d for i in range(3001)]
+    first = ws.loss_grad(S_all, T_all, seg)
+    for it in range(300):
+        i0 = (it * 250) % 3000
+        ws.loss_grad(S_all[i0 * d:(i0 + 250) * d], T_all[i0 * d:(i0 + 250) * d], [j * d for j in range(251)])
+        ws.adam_step(3e-3)
+    last = ws.loss_grad(S_all, T_all, seg)
+    assert last < first, (first, last)
+    held = [fam["model"](th) for th in fam["thetas"](16, 1)]
+    warm, limit, cold = [], [], []
+    for i, mdl in enumerate(held):
+        Sk = sketch(mdl)
+        warm.append(error(mdl, ws.forward(Sk).cpu().numpy().astype(np.float64)))
+        limit.append(error(mdl, Sk.cpu().numpy().astype(np.float64)))
+        cold.append(error(mdl, synth.random_unit_columns(d, k, seed=900 + i)))
+    ws.close()
+    print("loss", first, last, "median V0 error: warm", np.median(warm), "sketch", np.median(limit),
+          "cold", np.median(cold))
+    assert np.median(cold) > 0.95
+    assert np.median(warm) < 0.85
+    assert np.median(warm) < np.median(limit) + 0.03
