@@ -72,6 +72,12 @@ struct Ctx {
   float* cl_gram = nullptr;    // 3 slots of k*k + k row-side terms
   int cl_max_clusters = 0;     // co-resident clusters reported by the occupancy API
   int cl_last_grid = 0;        // CTAs of the most recent launch
+  int cl_ms_ok = 0;            // the multi-step kernel is configured
+  int cl_ms_coop = 1;          // it is launched cooperatively
+  size_t cl_ms_smem = 0;       // its shared memory
+  int cl_ms_max_clusters = 0;  // its co-resident clusters
+  unsigned* cl_bar = nullptr;  // its grid-barrier arrival counter
+  unsigned cl_bar_count = 0;   // arrivals so far
   unsigned long long* trace = nullptr;  // SGEP_TRACE=1: per-CTA phase timestamps
   size_t cl_smem = 0;
 
@@ -101,6 +107,7 @@ struct Ctx {
   int tc_st_nchunk = 0;            // chunks of the most recent streamed launch
   int tc_st_grid = 0;              // its CTAs (streaming + builder helpers)
   int tc_st_lag = 5, tc_st_helpers = 24;  // tuning knobs (SGEP_TC_LAG, SGEP_TC_HELPERS)
+  int tc_st_pfn = 3;                       // next-step chunks prefetched into L2 (SGEP_TC_PFN)
   float* tc_st_terms = nullptr;    // [3] row-side term slots a | b, then [3] slots |v'|^2 | U
   unsigned tc_st_launch = 0;       // streamed launches since the counters were last cleared
   unsigned tc_st_grams = 0;        // helper Gram contributions since then
@@ -273,6 +280,10 @@ int cluster_step(Ctx& c, const void* X, const void* Y, int64_t b, float eta, flo
                  cudaStream_t s);
 // Apply a pending update (no new minibatch).
 int cluster_flush(Ctx& c, cudaStream_t s);
+// Several consecutive minibatches in one persistent launch (grid barrier between steps).
+int cluster_steps(Ctx& c, const void* X, const void* Y, int64_t b, int nsteps, cudaStream_t s);
+int cluster_max_steps();
+bool cluster_steps_usable(const Ctx& c);
 // Copy the pending products into acc layout (d x k AV, d x k BV) for debugging.
 int cluster_products(Ctx& c, float* AV, float* BV, cudaStream_t s);
 void tc_update_trace_report(Ctx& c);

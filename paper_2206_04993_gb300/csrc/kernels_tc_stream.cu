@@ -69,6 +69,7 @@ constexpr int kR = 256;         // rows per chunk (16 MB at d = 32768)
 constexpr int kPS = 4;          // projection stages (one 128 x 64 box each)
 constexpr int kBS = 2;          // back-projection stages (four 64 x 64 boxes + the operand box)
 constexpr int kLagDefault = 5;  // chunks the projection may run ahead of the back-projection
+constexpr int kPfNextDefault = 3;  // next-step chunks prefetched into L2 at the end of a step
 constexpr int kMaxHelpers = 24; // builder CTAs on SMs the streaming CTAs leave idle
 constexpr int kAcc = 4;         // projection accumulators in tensor memory (64 columns each)
 constexpr int kVtBoxes = 2 * kR / 64;
@@ -102,6 +103,8 @@ struct StreamArgs {
   int nsteps;               // consecutive minibatches of this launch (rows s*b .. s*b + b - 1)
   int serial;               // the next step's projection also waits for the CTA's own update
   int bp_groups;            // mapX64 / mapY64 are 3-D views: one copy per 64-row back-projection step
+  int pf_next;              // chunks of the next step's projection tile prefetched into L2, one as each of
+                            // this step's last chunks is back-projected (0: two chunks at the step start)
   unsigned e0;              // steps streamed since the counters were cleared (epoch of step 0)
   float inv_nA, inv_nB;
   float rho, gamma, eps_B;
@@ -972,7 +975,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           const int row0 = (int)((int64_t)s * a.b) + (c * kRT + p_rtl) * 128;
           cstamp(s, c, kEvIssue);
-          if (s > 0 && c == 0) {
+          if (s > 0 && c == 0 && a.pf_next == 0) {
             // the step's first two tiles into L2 while the previous step's update runs (the
             // stages hold only half a tile, and HBM is idle during the update)
             for (int cc = 0; cc < 2 && cc < nchunk; ++cc)
@@ -1067,6 +1070,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       const CUtensorMap* mWA = b_view ? &mapPt : &mapQt;
       const CUtensorMap* mWB = b_view ? &mapQt : &mapPt;
       const uint64_t once = policy_evict_first();
+      // the next step's projection tile of chunk cc, into L2 once this step's back-projection
+      // has moved past chunk nchunk - pf_next + cc (the L2 footprint stays at the re-read window)
+      const CUtensorMap* mP = p_view ? &mapY : &mapX;
+      const int pf0 = nchunk - a.pf_next + 1;
+      auto prefetch_next = [&](int s, int c) {
+        const int cc = c - pf0;
+        if (a.pf_next <= 0 || s + 1 >= nsteps || cc < 0 || cc >= nchunk || cc >= a.pf_next) return;
+        const int row = (int)((int64_t)(s + 1) * a.b) + (cc * kRT + p_rtl) * 128;
+        for (int ks = 0; ks < 2 * kR / 64; ++ks) tma_prefetch_2d(mP, (int)(p_col0 + 64 * ks), row);
+      };
       int i = 0;
       bool ok = true;
       for (int s = 0; ok && s < nsteps; ++s) {
@@ -1077,6 +1090,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         for (int c = 0; ok && c < nchunk && !*abort_flag; ++c) {
+          prefetch_next(s, c);
           for (int h = 0; h < kR / 64; ++h, ++i) {
             const int r0 = c * kR + 64 * h;  // row of the step
             if (!spin_until_geq(a.wready + (r0 >> 6), e + 1)) {
@@ -1102,6 +1116,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             tma_load_2d(sa + 32768, r0 < a.nA ? mWA : mWB, r0, 0, b_full + st);
           }
         }
+        if (ok) prefetch_next(s, nchunk);
       }
       if (!ok) fail();
       for (int q = i > kBS ? i - kBS : 0; q < i; ++q) mbar_wait(b_full + (q % kBS), (q / kBS) & 1, 100000000ull);
@@ -1294,6 +1309,9 @@ int tc_stream_setup(Ctx& c) {
   // 256 rows of the minibatch kept in L2) and SGEP_TC_HELPERS (builder CTAs, 1..24)
   const char* lag = getenv("SGEP_TC_LAG");
   c.tc_st_lag = lag ? std::max(2, std::min(8, atoi(lag))) : kLagDefault;
+  // SGEP_TC_PFN: chunks of the next step prefetched into L2 during a step's last chunks (0..8)
+  const char* pfn = getenv("SGEP_TC_PFN");
+  c.tc_st_pfn = pfn ? std::max(0, std::min(8, atoi(pfn))) : kPfNextDefault;
   const char* hl = getenv("SGEP_TC_HELPERS");
   c.tc_st_helpers = hl ? std::max(1, std::min(kMaxHelpers, atoi(hl))) : kMaxHelpers;
   c.tc_st_epoch = 0;
@@ -1375,6 +1393,7 @@ int tc_stream_steps(Ctx& c, const void* X, const void* Y, int64_t b, int nsteps,
   sa.lag = c.tc_st_lag;
   sa.nsteps = nsteps;
   sa.bp_groups = bp_groups;
+  sa.pf_next = c.tc_st_pfn;
   c.tc_st_bp_groups = bp_groups;
   {
     const char* se = getenv("SGEP_TC_SERIAL");

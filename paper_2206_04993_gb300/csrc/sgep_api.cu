@@ -511,6 +511,19 @@ int sgep_step_many(sgep_t h, const void* X, const void* Y, const float* row_scal
     }
     return SGEP_OK;
   }
+  if (c.path == SGEP_PATH_CLUSTER && nsteps > 1 && cluster_steps_usable(c)) {
+    // consecutive minibatches of the cluster path: several steps per persistent launch
+    for (int64_t s0 = 0; s0 < nsteps;) {
+      const int n = (int)std::min<int64_t>(nsteps - s0, cluster_max_steps());
+      const char* xs = (const char*)X + (size_t)s0 * b * c.d_x * esz;
+      const char* ys = Y ? (const char*)Y + (size_t)s0 * b * c.d_y * esz : nullptr;
+      rc = cluster_steps(c, xs, ys, b, n, (cudaStream_t)stream);
+      if (rc) return rc;
+      c.t += n;
+      s0 += n;
+    }
+    return SGEP_OK;
+  }
   for (int64_t s = 0; s < nsteps; ++s) {
     const char* xs = (const char*)X + (size_t)s * b * h->d_x * esz;
     const char* ys = Y ? (const char*)Y + (size_t)s * b * h->d_y * esz : nullptr;
