@@ -74,6 +74,7 @@ struct Ctx {
   int cl_last_grid = 0;        // CTAs of the most recent launch
   int cl_ms_ok = 0;            // the multi-step kernel is configured
   int cl_ms_coop = 1;          // it is launched cooperatively
+  int cl_ms_traced = 0;        // the trace buffer holds a multi-step launch's stamps
   size_t cl_ms_smem = 0;       // its shared memory
   int cl_ms_max_clusters = 0;  // its co-resident clusters
   unsigned* cl_bar = nullptr;  // its grid-barrier arrival counter

@@ -186,10 +186,11 @@ __device__ __forceinline__ void issue_chunk(const ProdGeom& g, const T* Z, T* Xb
 // through distributed shared memory; the row-side k x k terms a_ij = (P^T Q + Q^T P)/n_A,
 // b_i = (|P_i|^2 + |Q_i|^2)/n_B; the back-projection X_chunk^T [Q|P] in registers. Finally the
 // CTA's d-slice of A_t V and B_t V and its share of the k x k terms are added into the slot.
-template <typename T, int CL, typename Mark>
+template <typename T, int CL, typename Mark, typename Hook>
 __device__ __forceinline__ void products_phase(cg::cluster_group& cluster, int rank, const ProdGeom& g, const T* Z,
                                                T* Xb, const float* VP, float* part, float* Wo, float* Wc,
-                                               float* red, Mark mark) {
+                                               float* red, Mark mark, Hook after_first_sync,
+                                               const float* pscale = nullptr) {
   const int tid = threadIdx.x;
   const int k = g.k, kp = g.kp, wp = g.wp, xs = g.xs, w = g.w;
   const int kk = k * k;
@@ -289,10 +290,16 @@ __device__ __forceinline__ void products_phase(cg::cluster_group& cluster, int r
     }
     if (j == 0) mark(9);
     cluster.sync();
-    if (j == 0) mark(10);
+    if (j == 0) {
+      mark(10);
+      after_first_sync();
+      if (pscale) __syncthreads();
+    }
+    // the projections made with unnormalised players are scaled by 1/|v'_i| here
     for (int o = tid; o < nr * kp; o += kThreads) {
-      Wo[o] = cluster_sum<CL>(cluster, pb, o, own_lo, own_hi);
-      Wc[o] = cluster_sum<CL>(cluster, pb, o, cr_lo, cr_hi);
+      const float f = pscale ? pscale[o & (kp - 1)] : 1.f;
+      Wo[o] = cluster_sum<CL>(cluster, pb, o, own_lo, own_hi) * f;
+      Wc[o] = cluster_sum<CL>(cluster, pb, o, cr_lo, cr_hi) * f;
     }
     __syncthreads();
     if (j == 0) mark(11);
@@ -622,7 +629,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_cluster_step(const ClArgs a) {
 
   // ---------------- 2. products of the new minibatch ----------------
   if (products) {
-    products_phase<T, CL>(cluster, rank, g, Z, Xb, VP, part, Wo, Wc, red, [&](int ph) { mark(a, ph, t0); });
+    products_phase<T, CL>(cluster, rank, g, Z, Xb, VP, part, Wo, Wc, red, [&](int ph) { mark(a, ph, t0); },
+                          [] {});
   }
   mark(a, 14, t0);
   // No CTA may leave while others can still read its shared memory.
@@ -665,9 +673,11 @@ struct MsArgs {
   unsigned* bar;            // grid-barrier arrivals (monotone across launches)
   unsigned bar_base;        // its value at the launch
   int* dflag;
+  unsigned long long* trace;  // [grid][kTracePhases] globaltimer stamps of the step before the last, or null
 };
 
-size_t ms_extra_smem(int wp, int kp) { return (size_t)wp * kp * sizeof(float) + 16; }
+// the second [Bv] buffer, its 16-byte alignment and the status word
+size_t ms_extra_smem(int wp, int kp) { return (size_t)wp * kp * sizeof(float) + 32; }
 
 template <typename T, int CLT>
 __global__ void __launch_bounds__(kThreads, 1) k_cluster_steps(const __grid_constant__ MsArgs a) {
@@ -697,15 +707,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_cluster_steps(const __grid_cons
   float* Wc = Wo + a.rs * kp;          // rs*kp
   float* red = Wc + a.rs * kp;         // kRed
   float* Gp = red + kRed;              // k*k + k: partial G | v.v   (read by the cluster)
-  float* np_ = Gp + kk + k;            // k: partial norms^2          (read by the cluster)
-  float* terms = np_ + k;              // 2k*k + k: a | G | b
+  float* rinv = Gp + kk + k;           // k: 1 / |v'_i| of the step's players
+  float* terms = rinv + k;             // 2k*k + k: a | G | b
   float* vv = terms + 2 * kk + k;      // k
   float* Tm = vv + k;                  // k*k
   float* cb = Tm + kk;                 // k
   float* cac = cb + k;                 // k
-  float* nrm = cac + k;                // k
+  float* nrm = cac + k;                // k: |v'_i|^2
   float* scr = nrm + k;                // kThreads
-  float* SA = scr + kThreads;          // wp*kp: [Bv] slice (two buffers, swapped by the update)
+  // wp*kp: [Bv] slice (two buffers, swapped by the update), 16-byte aligned for float4 reads
+  float* SA = reinterpret_cast<float*>(((uintptr_t)(scr + kThreads) + 15) & ~(uintptr_t)15);
   int* dead_s = reinterpret_cast<int*>(SA + wp * kp + wp * kp);
   float* Scur = SA;
   float* Snew = SA + wp * kp;
@@ -771,9 +782,81 @@ __global__ void __launch_bounds__(kThreads, 1) k_cluster_steps(const __grid_cons
     __syncthreads();
   };
   if (a.pend0) gram(Scur);
+  // partial G_ij = sum_c v_ci s_cj and |v_i|^2 over the slice: 4 x 4 register tiles of the
+  // padded kp x kp output, column groups c = cg, cg + ncg, ..., the groups summed in a fixed
+  // order into Gp (the cluster sums are taken at the products' first cluster barrier)
+  // partial tiles stored as float4 rows with row stride kp + 4 (a quarter warp's stores then fall
+  // in distinct banks); the column groups are as many as red and scr hold
+  const int gt_n = (kp / 4) * (kp / 4);             // tiles
+  const int gt_ld = kp + 4, gt_rs = kp * gt_ld;     // row stride, group stride
+  const int gt_cg = min(min(kThreads / gt_n, kThreads / kp), kRed / gt_rs);
+  auto gram_partial = [&](const float* PV, const float* Sc) {
+    const int tile = tid % gt_n, cg = tid / gt_n;
+    const int ti = tile / (kp / 4), tj = tile % (kp / 4);
+    if (cg < gt_cg) {
+      float acc[4][4] = {};
+      float n2[4] = {};
+      for (int c = cg; c < w; c += gt_cg) {
+        const float4 v = *reinterpret_cast<const float4*>(PV + c * kp + 4 * ti);
+        const float4 t = *reinterpret_cast<const float4*>(Sc + c * kp + 4 * tj);
+        const float va[4] = {v.x, v.y, v.z, v.w};
+        const float ta[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+#pragma unroll
+          for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(va[x], ta[y], acc[x][y]);
+          n2[x] = fmaf(va[x], va[x], n2[x]);
+        }
+      }
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        *reinterpret_cast<float4*>(red + cg * gt_rs + (4 * ti + x) * gt_ld + 4 * tj) =
+            make_float4(acc[x][0], acc[x][1], acc[x][2], acc[x][3]);
+        if (tj == 0) scr[cg * kp + 4 * ti + x] = n2[x];
+      }
+    }
+    __syncthreads();
+    for (int p = tid; p < kk + k; p += kThreads) {
+      float sum = 0.f;
+      if (p < kk) {
+        const int o = (p / k) * gt_ld + p % k;
+        for (int u = 0; u < gt_cg; ++u) sum += red[u * gt_rs + o];
+      } else {
+        for (int u = 0; u < gt_cg; ++u) sum += scr[u * kp + p - kk];
+      }
+      Gp[p] = sum;
+    }
+    __syncthreads();
+  };
+  // cluster sums of the partials: |v'_i|^2, 1/|v'_i| and |v_i|^2 of the retracted players
+  // v_i = v'_i / |v'_i|, and <v'_i, [Bv]_j> (its row i is scaled by 1/|v'_i| at the next
+  // update); `scaled` says whether the partials were of unnormalised players
+  bool scaled = false;
+  for (int i = tid; i < k; i += kThreads) rinv[i] = 1.f;
+  __syncthreads();
+  auto gram_sum = [&]() {
+    for (int p = tid; p < kk + k; p += kThreads) {
+      const float sv = cluster_sum<CL>(cluster, Gp, p, 0, CL);
+      if (p < kk) {
+        terms[kk + p] = sv;
+      } else {
+        const int i = p - kk;
+        const float r = scaled ? 1.f / sqrtf(sv) : 1.f;
+        nrm[i] = sv;
+        rinv[i] = r;
+        vv[i] = scaled ? sv * r * r : sv;
+      }
+    }
+  };
 
   bool applied = false;  // an update has changed the resident slices
   for (int s = 0; s < a.nsteps; ++s) {
+    // phase stamps of the step before the last: 0 top, 1 barrier passed, 2 coefficients,
+    // 3 update directions, 4 norms summed, 5 players retracted, 8-14 products, 15 Gram done
+    auto stamp = [&](int ev) {
+      if (a.trace && tid == 0 && s == a.nsteps - 2) a.trace[(size_t)blockIdx.x * kTracePhases + ev] = tc::globaltimer();
+    };
+    stamp(0);
     const bool pend = s > 0 || a.pend0;
     const int pslot = (a.slot0 + s) % 3;  // products waiting for their update
     const int wslot = (pslot + 1) % 3;    // this step's products
@@ -787,6 +870,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_cluster_steps(const __grid_cons
       }
       __syncthreads();
     }
+    stamp(1);
     {
       float* az = a.acc + zslot * 2 * dk;
       float* gz = a.gram + zslot * gk;
@@ -800,19 +884,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_cluster_steps(const __grid_cons
       const float* AVp = a.acc + pslot * 2 * dk;
       const float* BVp = AVp + dk;
       const float* gp = a.gram + pslot * gk;
-      for (int p = tid; p < kk; p += kThreads) terms[p] = __ldcg(gp + p);
-      for (int i = tid; i < k; i += kThreads)
-        terms[2 * kk + i] = a.b_is_identity ? (1.f + a.eps_B) * vv[i] : fmaf(a.eps_B, vv[i], __ldcg(gp + kk + i));
-      __syncthreads();
-      eg_coefficients(terms, k, a.rho, cb, cac, Tm);
-      __syncthreads();
-      const float eta = a.eta[s], gamma = a.gamma[s];
-      const float e1 = 1.f + a.eps_B;
       const int ne = wp * kp;
-      for (int e0 = 0; e0 < ne; e0 += kEB * kThreads) {
-        float av[kEB], bvr[kEB], pen[kEB];
-        int cu[kEB], iu[kEB];
-        bool oku[kEB];
+      float av[kEB], bvr[kEB], pen[kEB];
+      int cu[kEB], iu[kEB];
+      bool oku[kEB];
+      auto load_block = [&](int e0) {  // A_t V and B_t V of this thread's elements of block e0
 #pragma unroll
         for (int u = 0; u < kEB; ++u) {
           const int e = e0 + u * kThreads + tid;
@@ -824,6 +900,44 @@ __global__ void __launch_bounds__(kThreads, 1) k_cluster_steps(const __grid_cons
           bvr[u] = (oku[u] && !a.b_is_identity) ? __ldcg(BVp + gi) : 0.f;
           pen[u] = 0.f;
         }
+      };
+      load_block(0);  // in flight while the coefficients are built
+      for (int p = tid; p < kk; p += kThreads) {
+        terms[p] = __ldcg(gp + p);
+        terms[kk + p] *= rinv[p / k];  // G of the retracted players
+      }
+      for (int i = tid; i < k; i += kThreads)
+        terms[2 * kk + i] = a.b_is_identity ? (1.f + a.eps_B) * vv[i] : fmaf(a.eps_B, vv[i], __ldcg(gp + kk + i));
+      __syncthreads();
+      // coefficients of Eq. (update): T_ji = b_i a_ij / s_j (j < i), c_i = sum_{j<i} a_ij G_ij / s_j,
+      // with s_j = max(G_jj, rho) inverted once and c_i summed by one warp per player
+      {
+        const float* ta = terms;
+        const float* tG = terms + kk;
+        const float* tb = terms + 2 * kk;
+        for (int j = tid; j < k; j += kThreads) scr[j] = 1.f / fmaxf(tG[j * k + j], a.rho);
+        __syncthreads();
+        for (int p = tid; p < kk; p += kThreads) {
+          const int j = p / k, i = p % k;
+          Tm[p] = j < i ? tb[i] * ta[i * k + j] * scr[j] : 0.f;
+        }
+        const int wid = tid >> 5, ln = tid & 31;
+        for (int i = wid; i < k; i += kThreads / 32) {
+          float c = ln < i ? ta[i * k + ln] * tG[i * k + ln] * scr[ln] : 0.f;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+          if (ln == 0) {
+            cb[i] = tb[i];
+            cac[i] = ta[i * k + i] - c;
+          }
+        }
+      }
+      __syncthreads();
+      stamp(2);
+      const float eta = a.eta[s], gamma = a.gamma[s];
+      const float e1 = 1.f + a.eps_B;
+      for (int e0 = 0; e0 < ne; e0 += kEB * kThreads) {
+        if (e0 > 0) load_block(e0);
         // penalty sum_{j<i} [Bv]_j T_ji; T_ji is zero for j >= i
         for (int j = 0; j < k; ++j) {
 #pragma unroll
@@ -848,9 +962,29 @@ __global__ void __launch_bounds__(kThreads, 1) k_cluster_steps(const __grid_cons
         }
       }
       __syncthreads();
-      colsum_prod(UP, UP, kp, w, k, scr, np_);
+      stamp(3);
+    }
+    // Retraction deferred: the products use v' = v + eta grad, and the partial |v'_i|^2 and
+    // <v'_i, [Bv]'_j> are summed over the cluster at the products' first cluster barrier, where
+    // the gathered projections are scaled by 1/|v'_i| (the projections of the retracted players)
+    const float* PV = pend ? UP : VP;
+    const float* PS = pend ? Snew : Scur;
+    scaled = pend;
+    gram_partial(PV, PS);
+    stamp(5);
+    // ---- products of this step's minibatch ----
+    g.acc_cur = a.acc + wslot * 2 * dk;
+    g.gram_cur = a.gram + wslot * gk;
+    products_phase<T, CL>(cluster, rank, g, Z, Xb, PV, part, Wo, Wc, red, [&](int ph) { stamp(ph); }, gram_sum,
+                          pend ? rinv : nullptr);
+    if (nch == 0) {  // no chunk, so no barrier inside the products (the same in the whole cluster)
       cluster.sync();
-      for (int i = tid; i < k; i += kThreads) nrm[i] = cluster_sum<CL>(cluster, np_, i, 0, CL);
+      gram_sum();
+    }
+    // work that does not depend on the products' atomics, while they complete: the next step's
+    // first rows and the retraction itself
+    if (s + 1 < a.nsteps && nch > 0) issue_chunk<T>(g, Z + (size_t)a.b * (size_t)ld, Xb, 0);
+    if (pend) {
       __syncthreads();
       for (int e = tid; e < wp * kp; e += kThreads) {
         const int c = e / kp, i = e % kp;
@@ -865,23 +999,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_cluster_steps(const __grid_cons
       Scur = Snew;
       Snew = t;
       applied = true;
-      __syncthreads();
     }
-    // ---- products of this step's minibatch ----
-    g.acc_cur = a.acc + wslot * 2 * dk;
-    g.gram_cur = a.gram + wslot * gk;
-    products_phase<T, CL>(cluster, rank, g, Z, Xb, VP, part, Wo, Wc, red, [](int) {});
     if (s + 1 < a.nsteps) {
-      // arrive (this CTA's products and clears are in), then the next step's first rows and
-      // the next update's Gram while the other CTAs arrive
+      // arrive: this CTA's products and clears are in
       __syncthreads();
       if (tid == 0) {
         __threadfence();
         atomicAdd(a.bar, 1u);
       }
-      if (nch > 0) issue_chunk<T>(g, Z + (size_t)a.b * (size_t)ld, Xb, 0);
-      gram(Scur);
+      stamp(15);
     }
+    __syncthreads();
   }
   // the state after the last applied update
   if (applied && cid == 0) {
@@ -1045,7 +1173,10 @@ int run(Ctx& c, const void* X, const void* Y, int64_t b, float eta, float gamma,
   else
     rc = c.cl_size == 16 ? launch<float, 16>(c, a, NC, s) : launch<float, 8>(c, a, NC, s);
   if (rc) return rc;
-  if (X) c.cl_last_grid = NC * c.cl_size;
+  if (X) {
+    c.cl_last_grid = NC * c.cl_size;
+    c.cl_ms_traced = 0;
+  }
   if (pending) {
     c.cl_cur = 1 - c.cl_cur;
     c.debug_valid = c.cfg.debug;
@@ -1235,7 +1366,7 @@ int cluster_flush(Ctx& c, cudaStream_t s) {
 
 int cluster_max_steps() { return kMsMax; }
 
-bool cluster_steps_usable(const Ctx& c) { return c.cl_ms_ok && !c.cfg.debug && !c.trace; }
+bool cluster_steps_usable(const Ctx& c) { return c.cl_ms_ok && !c.cfg.debug; }
 
 // `nsteps` consecutive minibatches X[s b .. s b + b) (and Y) in one launch: the pending
 // update (if any), then per step its products and the next step's update; the last step's
@@ -1295,6 +1426,8 @@ int cluster_steps(Ctx& c, const void* X, const void* Y, int64_t b, int nsteps, c
   a.bar = c.cl_bar;
   a.bar_base = c.cl_bar_count;
   a.dflag = c.dflag;
+  a.trace = nsteps >= 2 ? c.trace : nullptr;
+  if (a.trace) SGEP_CUDA_TRY(cudaMemsetAsync(c.trace, 0, (size_t)4096 * kTracePhases * sizeof(unsigned long long), s));
   int rc;
   if (c.cfg.dtype == SGEP_BF16)
     rc = c.cl_size == 16 ? ms_launch<__nv_bfloat16, 16>(c, a, NC, s) : ms_launch<__nv_bfloat16, 8>(c, a, NC, s);
@@ -1303,6 +1436,7 @@ int cluster_steps(Ctx& c, const void* X, const void* Y, int64_t b, int nsteps, c
   if (rc) return rc;
   c.cl_bar_count += (unsigned)(nsteps - 1) * grid;
   c.cl_last_grid = (int)grid;
+  c.cl_ms_traced = a.trace ? 1 : 0;
   if (c.cl_pending || nsteps > 1) c.cl_cur = 1 - c.cl_cur;  // an update was applied
   c.cl_slot = (c.cl_slot + nsteps) % 3;
   c.cl_pending = 1;
@@ -1327,6 +1461,20 @@ void cluster_trace_report(Ctx& c) {
   }
   std::fprintf(stderr, "[sgep trace] grid %d CTAs (cluster %d, max co-resident clusters %d); CTA start spread %.2f us\n",
                n, c.cl_size, c.cl_max_clusters, (double)(g1 - g0) / 1e3);
+  if (c.cl_ms_traced) {
+    // globaltimer stamps of one step of a multi-step launch, relative to the earliest step start
+    std::fprintf(stderr, "[sgep trace] multi-step launch, the step before the last (us from its earliest start, median / max over CTAs):");
+    for (int ph = 1; ph < kTracePhases; ++ph) {
+      std::vector<double> v;
+      for (int b = 0; b < n; ++b)
+        if (t[(size_t)b * kTracePhases + ph]) v.push_back((double)(t[(size_t)b * kTracePhases + ph] - g0) / 1e3);
+      if (v.empty()) continue;
+      std::sort(v.begin(), v.end());
+      std::fprintf(stderr, " %d:%.2f/%.2f", ph, v[v.size() / 2], v.back());
+    }
+    std::fprintf(stderr, "\n");
+    return;
+  }
   std::fprintf(stderr, "[sgep trace] phase clocks (median / max over CTAs, SM cycles from CTA start):");
   for (int ph = 1; ph < kTracePhases; ++ph) {
     std::vector<unsigned long long> v;
