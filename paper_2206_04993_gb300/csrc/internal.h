@@ -242,6 +242,8 @@ int make_map_bf16(CUtensorMap* map, const void* base, int64_t rows, int64_t cols
                   int box_cols);
 // The same matrix viewed as (64 columns, rows, column groups): a box of box_rows x `groups`
 // groups lands as `groups` consecutive 2-D boxes of 64 columns (one copy).
+int make_map_f32(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows,
+                 int box_cols);
 int make_map_bf16_groups(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows,
                          int groups);
 bool tc_supported(const Ctx& c, const char** why);

@@ -59,6 +59,29 @@ int make_map_bf16(CUtensorMap* map, const void* base, int64_t rows, int64_t cols
   return SGEP_OK;
 }
 
+// FP32 row-major matrix [rows][cols], boxes of box_rows x box_cols (box_cols * 4 <= 128 bytes)
+// with 128-byte swizzle.
+int make_map_f32(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows,
+                 int box_cols) {
+  auto fn = encode_fn();
+  if (!fn) {
+    set_error("cuTensorMapEncodeTiled is not available");
+    return SGEP_ECUDA;
+  }
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return SGEP_ECUDA;
+  }
+  return SGEP_OK;
+}
+
 // 3-D view of a BF16 row-major matrix [rows][cols] (row stride `ld` elements) as (64 columns,
 // rows, cols / 64 column groups): one box of box_rows rows x `groups` groups lands as `groups`
 // consecutive [box_rows][64] sub-boxes with 128-byte swizzle, the layout of that many 2-D boxes
@@ -1047,6 +1070,321 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (warp == 1) tmem_dealloc(tmem, 256);
 }
 
+// ---------------------------------------------------------------------------
+// FP32 minibatches on the tensor cores. Each FP32 tile that TMA lands (boxes of 32 columns,
+// 128-byte swizzle) is split by converter warps into BF16 hi = bf16(x) and lo = bf16(x - hi),
+// written in the layout TMA gives BF16 boxes of 64 columns; x - hi is exact in FP32, so hi + lo
+// keeps about 16 significant bits of x. The MMAs add X_hi [V_hi | V_lo] + X_lo V_hi (the
+// X_lo V_lo term is below the pairs' resolution), the same accumulator columns as the BF16 path.
+
+constexpr int kF32Stages = 3;
+constexpr int kF32Threads = 320;  // warps 0: TMA, 1: MMA, 2-5: epilogue, 6-9: converters
+constexpr int kF32Conv = 128;     // converter threads
+
+// FP32 tile of R rows x C columns (C / 32 boxes of [R][32]) into hi and lo (C / 64 boxes of
+// [R][64] BF16 each); thread t of nthr. Consecutive threads take consecutive rows of one
+// 8-column group, so a quarter warp's 16-byte accesses fall in distinct banks.
+__device__ __forceinline__ void split_f32_tile(const uint8_t* src, uint8_t* hi, uint8_t* lo, int R, int C, int t,
+                                               int nthr) {
+  const int ngrp = C / 8;
+  for (int it = t; it < R * ngrp; it += nthr) {
+    const int r = it % R, c = 8 * (it / R);
+    const int rr = r & 7;
+    const uint8_t* sb = src + (size_t)(c / 32) * (R * 128) + (r >> 3) * 1024 + rr * 128;
+    const int q = (c & 31) >> 2;
+    const float4 x0 = *reinterpret_cast<const float4*>(sb + ((q ^ rr) << 4));
+    const float4 x1 = *reinterpret_cast<const float4*>(sb + (((q + 1) ^ rr) << 4));
+    const float xs[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const __nv_bfloat162 hv = __floats2bfloat162_rn(xs[2 * u], xs[2 * u + 1]);
+      const __nv_bfloat162 lv =
+          __floats2bfloat162_rn(xs[2 * u] - __low2float(hv), xs[2 * u + 1] - __high2float(hv));
+      h[u] = *reinterpret_cast<const uint32_t*>(&hv);
+      l[u] = *reinterpret_cast<const uint32_t*>(&lv);
+    }
+    const size_t toff = (size_t)(c / 64) * (R * 128) + (r >> 3) * 1024 + rr * 128 + ((((c & 63) >> 3) ^ rr) << 4);
+    *reinterpret_cast<uint4*>(hi + toff) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(lo + toff) = make_uint4(l[0], l[1], l[2], l[3]);
+  }
+}
+
+// P = X V_x, Q = Y V_y from FP32 rows. grid: (b/128 row tiles, 2 views, splits). A stage is
+// [X: two 128 x 32 FP32 boxes][V^T box 64 x 64][hi 128 x 64][lo 128 x 64].
+__global__ void __launch_bounds__(kF32Threads, 1)
+    k_tc_project_f32(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapY,
+                     const __grid_constant__ CUtensorMap mapVt, const TcProjArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = align1024(smem_raw);
+  constexpr int kX = 32768, kV = 8192, kH = 16384, kStage = kX + kV + 2 * kH;
+  uint64_t* full = (uint64_t*)(base + kF32Stages * kStage);
+  uint64_t* conv = full + kF32Stages;
+  uint64_t* empty = conv + kF32Stages;
+  uint64_t* done = empty + kF32Stages;
+  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  int* abort_flag = (int*)(tmem_slot + 1);
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid & 31;
+  const int view = blockIdx.y;
+  const int64_t row0 = (int64_t)blockIdx.x * 128;
+  const int64_t c0 = (int64_t)blockIdx.z * a.cols_per_split;
+  const int nk = (int)(a.cols_per_split / 64);
+  const CUtensorMap* mZ = view ? &mapY : &mapX;
+  const int64_t voff = view ? a.d_x : 0;
+
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, 64);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    for (int s = 0; s < kF32Stages; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(conv + s, kF32Conv / 32);
+      mbar_init(empty + s, 1);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+    prefetch_tensormap(mZ);
+    prefetch_tensormap(&mapVt);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    const uint64_t keep = policy_evict_last();
+    for (int ks = 0; ks < nk; ++ks) {
+      const int st = ks % kF32Stages;
+      if (ks >= kF32Stages && !mbar_wait(empty + st, ((ks / kF32Stages) - 1) & 1)) {
+        atomicOr(a.dflag, kFlagTimeout);
+        *(volatile int*)abort_flag = 1;
+        break;
+      }
+      if (*(volatile int*)abort_flag) break;
+      uint8_t* sa = base + st * kStage;
+      mbar_arrive_expect_tx(full + st, kX + kV);
+      tma_load_2d(sa, mZ, (int)(c0 + (int64_t)ks * 64), (int)row0, full + st);
+      tma_load_2d(sa + kX / 2, mZ, (int)(c0 + (int64_t)ks * 64 + 32), (int)row0, full + st);
+      tma_load_2d_hint(sa + kX, &mapVt, (int)(voff + c0 + (int64_t)ks * 64), 0, full + st, keep);
+    }
+  } else if (warp >= 6) {
+    // converters: each landed FP32 tile into its hi / lo BF16 tiles
+    const int t = tid - 192;
+    for (int ks = 0; ks < nk; ++ks) {
+      const int st = ks % kF32Stages;
+      if (!mbar_wait(full + st, (ks / kF32Stages) & 1)) {
+        if (lane == 0) atomicOr(a.dflag, kFlagTimeout);
+        *(volatile int*)abort_flag = 1;
+        break;
+      }
+      if (*(volatile int*)abort_flag) break;
+      uint8_t* sa = base + st * kStage;
+      split_f32_tile(sa, sa + kX + kV, sa + kX + kV + kH, 128, 64, t, kF32Conv);
+      fence_proxy_async_smem();  // the tiles are read by the tensor cores (async proxy)
+      __syncwarp();
+      if (lane == 0) mbar_arrive(conv + st);
+    }
+  } else if (warp == 1 && lane == 0) {
+    const uint32_t id64 = idesc_bf16(128, 64, 0, 0), id32 = idesc_bf16(128, 32, 0, 0);
+    bool ok = true;
+    for (int ks = 0; ks < nk; ++ks) {
+      const int st = ks % kF32Stages;
+      if (!mbar_wait(conv + st, (ks / kF32Stages) & 1) || *(volatile int*)abort_flag) {
+        atomicOr(a.dflag, kFlagTimeout);
+        *(volatile int*)abort_flag = 1;
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      uint8_t* sa = base + st * kStage;
+      const uint8_t* vt = sa + kX;
+      const uint8_t* xh = sa + kX + kV;
+      const uint8_t* xl = xh + kH;
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        mma_bf16(tmem, desc_sw128(xh + kk * 32, 16, 1024), desc_sw128(vt + kk * 32, 16, 1024), id64,
+                 (ks | kk) ? 1u : 0u);
+        mma_bf16(tmem, desc_sw128(xl + kk * 32, 16, 1024), desc_sw128(vt + kk * 32, 16, 1024), id32, 1u);
+      }
+      mma_commit(empty + st);
+    }
+    if (ok) mma_commit(done);
+    else mbar_arrive(done);
+  } else if (warp >= 2 && warp < 6) {
+    const bool ready = mbar_wait(done, 0);
+    tc_fence_after();
+    if (!ready) {
+      if (lane == 0) atomicOr(a.dflag, kFlagTimeout);
+    } else if (!*(volatile int*)abort_flag) {
+      const int q = warp & 3;
+      const int r = 32 * q + lane;
+      float hi[32], lo[32];
+      tmem_ld32(tmem + ((uint32_t)(32 * q) << 16), hi);
+      tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + 32, lo);
+      float* out = (view ? a.Q : a.P) + (row0 + r) * kTcKP;
+      if (row0 + r < a.b) {
+#pragma unroll
+        for (int i = 0; i < kTcKP; i += 4)
+          atomicAdd(reinterpret_cast<float4*>(out + i),
+                    make_float4(hi[i] + lo[i], hi[i + 1] + lo[i + 1], hi[i + 2] + lo[i + 2], hi[i + 3] + lo[i + 3]));
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) tmem_dealloc(tmem, 64);
+}
+
+// A_t V and B_t V from FP32 rows. grid: d/256 column slices (X slices first). Rows in 64-row
+// blocks streamed last-first (the rows the projection read last are still in L2), each block
+// in two stages of 128 columns: [X: four 64 x 32 FP32 boxes][operand 64 x 64][hi 2 x 64 x 64]
+// [lo 2 x 64 x 64].
+__global__ void __launch_bounds__(kF32Threads, 1)
+    k_tc_backproject_f32(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapY,
+                         const __grid_constant__ CUtensorMap mapPt, const __grid_constant__ CUtensorMap mapQt,
+                         const TcBackArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* base = align1024(smem_raw);
+  constexpr int kX = 32768, kW = 8192, kH = 16384, kStage = kX + kW + 2 * kH;
+  uint64_t* full = (uint64_t*)(base + kF32Stages * kStage);
+  uint64_t* conv = full + kF32Stages;
+  uint64_t* empty = conv + kF32Stages;
+  uint64_t* done = empty + kF32Stages;
+  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  int* abort_flag = (int*)(tmem_slot + 1);
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid & 31;
+  const bool isY = (int)blockIdx.x >= a.nslice_x;
+  const int64_t c0 = (int64_t)(isY ? blockIdx.x - a.nslice_x : blockIdx.x) * 256;
+  const int64_t goff = (isY ? a.d_x : 0) + c0;
+  const CUtensorMap* mZ = isY ? &mapY : &mapX;
+  const CUtensorMap* mWA = isY ? &mapPt : &mapQt;
+  const CUtensorMap* mWB = isY ? &mapQt : &mapPt;
+  const int nrb = (int)(a.b / 64);
+  const int nst = 2 * nrb;  // (row block, column half) steps
+
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, 256);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    for (int s = 0; s < kF32Stages; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(conv + s, kF32Conv / 32);
+      mbar_init(empty + s, 1);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+    prefetch_tensormap(mZ);
+    prefetch_tensormap(mWA);
+    prefetch_tensormap(mWB);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    const uint64_t once = policy_evict_first();
+    for (int s = 0; s < nst; ++s) {
+      const int st = s % kF32Stages;
+      const int64_t r0 = (int64_t)(nrb - 1 - s / 2) * 64;
+      const int h = s & 1;
+      if (s >= kF32Stages && !mbar_wait(empty + st, ((s / kF32Stages) - 1) & 1)) {
+        atomicOr(a.dflag, kFlagTimeout);
+        *(volatile int*)abort_flag = 1;
+        break;
+      }
+      if (*(volatile int*)abort_flag) break;
+      uint8_t* sa = base + st * kStage;
+      const bool rowA = !a.split || r0 < a.nA;
+      mbar_arrive_expect_tx(full + st, kX + kW);
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        tma_load_2d_hint(sa + j * 8192, mZ, (int)(c0 + 128 * h + 32 * j), (int)r0, full + st, once);
+      tma_load_2d(sa + kX, rowA ? mWA : mWB, (int)r0, 0, full + st);
+    }
+  } else if (warp >= 6) {
+    const int t = tid - 192;
+    for (int s = 0; s < nst; ++s) {
+      const int st = s % kF32Stages;
+      if (!mbar_wait(full + st, (s / kF32Stages) & 1)) {
+        if (lane == 0) atomicOr(a.dflag, kFlagTimeout);
+        *(volatile int*)abort_flag = 1;
+        break;
+      }
+      if (*(volatile int*)abort_flag) break;
+      uint8_t* sa = base + st * kStage;
+      split_f32_tile(sa, sa + kX + kW, sa + kX + kW + kH, 64, 128, t, kF32Conv);
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(conv + st);
+    }
+  } else if (warp == 1 && lane == 0) {
+    const uint32_t id64 = idesc_bf16(128, 64, 1, 0), id32 = idesc_bf16(128, 32, 1, 0);
+    bool ok = true;
+    bool usedA[2] = {false, false}, usedB[2] = {false, false};
+    for (int s = 0; s < nst; ++s) {
+      const int st = s % kF32Stages;
+      const int64_t r0 = (int64_t)(nrb - 1 - s / 2) * 64;
+      const int h = s & 1;
+      if (!mbar_wait(conv + st, (s / kF32Stages) & 1) || *(volatile int*)abort_flag) {
+        atomicOr(a.dflag, kFlagTimeout);
+        *(volatile int*)abort_flag = 1;
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      uint8_t* sa = base + st * kStage;
+      const uint8_t* w = sa + kX;
+      const uint8_t* xh = sa + kX + kW;
+      const uint8_t* xl = xh + kH;
+      const bool rowA = !a.split || r0 < a.nA;
+      const uint32_t dcol = tmem + (rowA ? 0u : 128u) + 64 * h;
+      const bool used = rowA ? usedA[h] : usedB[h];
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        mma_bf16(dcol, desc_sw128(xh + kk * 2048, 8192, 1024), desc_sw128(w + kk * 32, 16, 1024), id64,
+                 (used || kk) ? 1u : 0u);
+        mma_bf16(dcol, desc_sw128(xl + kk * 2048, 8192, 1024), desc_sw128(w + kk * 32, 16, 1024), id32, 1u);
+      }
+      if (rowA) usedA[h] = true;
+      else usedB[h] = true;
+      mma_commit(empty + st);
+    }
+    if (ok) mma_commit(done);
+    else mbar_arrive(done);
+  } else if (warp >= 2 && warp < 6) {
+    const bool ready = mbar_wait(done, 0);
+    tc_fence_after();
+    if (!ready) {
+      if (lane == 0) atomicOr(a.dflag, kFlagTimeout);
+    } else if (!*(volatile int*)abort_flag) {
+      const int q = warp & 3;
+      const int k = a.k;
+#pragma unroll 1
+      for (int which = 0; which < 2; ++which) {
+        float* out = which == 0 ? a.AV : a.BV;
+        const float sc = which == 0 ? a.inv_nA : a.inv_nB;
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+          float hi[32], lo[32];
+          const uint32_t t = tmem + (uint32_t)(which * 128 + 64 * h) + ((uint32_t)(32 * q) << 16);
+          tmem_ld32(t, hi);
+          tmem_ld32(t + 32, lo);
+          const int64_t col = goff + 128 * h + 32 * q + lane;
+          for (int i = 0; i < k; ++i) out[col * k + i] = (hi[i] + lo[i]) * sc;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) tmem_dealloc(tmem, 256);
+}
+
 }  // namespace
 }  // namespace sgep
 
@@ -1069,7 +1407,7 @@ TcTerms tc_terms(const Ctx& c, int slot) {
 
 bool tc_supported(const Ctx& c, const char** why) {
   const char* w = nullptr;
-  if (c.cfg.dtype != SGEP_BF16) w = "needs BF16 minibatches";
+  if (c.cfg.dtype != SGEP_BF16 && c.cfg.dtype != SGEP_F32) w = "needs BF16 or FP32 minibatches";
   else if (c.cfg.kind != SGEP_CCA) w = "tensor-core path supports CCA";
   else if (!c.cfg.split_AB) w = "tensor-core path needs split A/B batches";
   else if (c.d_x != c.d_y) w = "tensor-core path needs d_x == d_y";
@@ -1120,11 +1458,19 @@ int tc_alloc(Ctx& c) {
                      : 0;
     cudaGetLastError();
   }
-  const size_t sp = kP_Stages * 24576 + 1024 + 256, sb = kB_Stages * 40960 + 1024 + 256;
-  SGEP_CUDA_TRY(cudaFuncSetAttribute(k_tc_project, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp));
-  SGEP_CUDA_TRY(cudaFuncSetAttribute(k_tc_backproject, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb));
-  c.tc_smem_p = sp;
-  c.tc_smem_b = sb;
+  if (c.cfg.dtype == SGEP_F32) {
+    // FP32 rows: three stages of [FP32 tile | operand box | BF16 hi | BF16 lo]
+    const size_t sf = kF32Stages * 73728 + 1024 + 256;
+    SGEP_CUDA_TRY(cudaFuncSetAttribute(k_tc_project_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf));
+    SGEP_CUDA_TRY(cudaFuncSetAttribute(k_tc_backproject_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf));
+    c.tc_smem_p = c.tc_smem_b = sf;
+  } else {
+    const size_t sp = kP_Stages * 24576 + 1024 + 256, sb = kB_Stages * 40960 + 1024 + 256;
+    SGEP_CUDA_TRY(cudaFuncSetAttribute(k_tc_project, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp));
+    SGEP_CUDA_TRY(cudaFuncSetAttribute(k_tc_backproject, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb));
+    c.tc_smem_p = sp;
+    c.tc_smem_b = sb;
+  }
   // The streamed one-read kernel is the default where the shape allows it
   // (SGEP_TC_STREAM=0 keeps the two-pass products).
   return tc_stream_setup(c);
@@ -1190,11 +1536,19 @@ int tc_products(Ctx& c, const void* X, const void* Y, int64_t b, cudaStream_t s,
     return rc;
   }
   CUtensorMap mX1, mY1, mVt, mX2, mY2, mPt, mQt;
-  rc = make_map_bf16(&mX1, X, b, c.d_x, c.d_x, 128, 64);
-  if (!rc) rc = make_map_bf16(&mY1, Y, b, c.d_y, c.d_y, 128, 64);
+  const bool f32 = c.cfg.dtype == SGEP_F32;
+  if (f32) {
+    rc = make_map_f32(&mX1, X, b, c.d_x, c.d_x, 128, 32);
+    if (!rc) rc = make_map_f32(&mY1, Y, b, c.d_y, c.d_y, 128, 32);
+    if (!rc) rc = make_map_f32(&mX2, X, b, c.d_x, c.d_x, 64, 32);
+    if (!rc) rc = make_map_f32(&mY2, Y, b, c.d_y, c.d_y, 64, 32);
+  } else {
+    rc = make_map_bf16(&mX1, X, b, c.d_x, c.d_x, 128, 64);
+    if (!rc) rc = make_map_bf16(&mY1, Y, b, c.d_y, c.d_y, 128, 64);
+    if (!rc) rc = make_map_bf16(&mX2, X, b, c.d_x, c.d_x, 64, 64);
+    if (!rc) rc = make_map_bf16(&mY2, Y, b, c.d_y, c.d_y, 64, 64);
+  }
   if (!rc) rc = make_map_bf16(&mVt, c.tc_Vt, 2 * kTcKP, c.d, c.d, 64, 64);
-  if (!rc) rc = make_map_bf16(&mX2, X, b, c.d_x, c.d_x, 64, 64);
-  if (!rc) rc = make_map_bf16(&mY2, Y, b, c.d_y, c.d_y, 64, 64);
   if (rc) return rc;
   c.tc_pq_dirty = 1;  // the kernels below leave P and Q non-zero
   rc = make_map_bf16(&mPt, c.tc_Pt, 2 * kTcKP, b, c.cfg.max_b, 64, 64);
@@ -1217,7 +1571,8 @@ int tc_products(Ctx& c, const void* X, const void* Y, int64_t b, cudaStream_t s,
     pa.Q = Q;
     pa.dflag = c.dflag;
     dim3 grid((unsigned)(b / 128), 2, (unsigned)splits);
-    k_tc_project<<<grid, kTcThreads, c.tc_smem_p, s>>>(mX1, mY1, mVt, pa);
+    if (f32) k_tc_project_f32<<<grid, kF32Threads, c.tc_smem_p, s>>>(mX1, mY1, mVt, pa);
+    else k_tc_project<<<grid, kTcThreads, c.tc_smem_p, s>>>(mX1, mY1, mVt, pa);
     SGEP_CUDA_TRY(cudaGetLastError());
   }
   // 3. P, Q split into BF16 pairs (transposed), row-side terms a and b
@@ -1240,7 +1595,8 @@ int tc_products(Ctx& c, const void* X, const void* Y, int64_t b, cudaStream_t s,
     ba.AV = c.acc;
     ba.BV = c.acc + c.d * c.k;
     ba.dflag = c.dflag;
-    k_tc_backproject<<<(unsigned)(c.d / 256), kTcThreads, c.tc_smem_b, s>>>(mX2, mY2, mPt, mQt, ba);
+    if (f32) k_tc_backproject_f32<<<(unsigned)(c.d / 256), kF32Threads, c.tc_smem_b, s>>>(mX2, mY2, mPt, mQt, ba);
+    else k_tc_backproject<<<(unsigned)(c.d / 256), kTcThreads, c.tc_smem_b, s>>>(mX2, mY2, mPt, mQt, ba);
     SGEP_CUDA_TRY(cudaGetLastError());
   }
   c.launches += 3;

@@ -1274,7 +1274,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 // per (view, CTA) pair), one resident CTA per 256 columns, minibatches of whole chunks and
 // Alg. 2's plain step (Adam and Alg. 3 take the two-pass products).
 bool tc_stream_supported(const Ctx& c, int64_t b) {
-  return c.tc_st_ok && c.d_x == c.d_y && c.d_x % (2 * kR) == 0 && c.d_x / 128 < c.num_sms && b % 256 == 0 &&
+  return c.tc_st_ok && c.cfg.dtype == SGEP_BF16 && c.d_x == c.d_y && c.d_x % (2 * kR) == 0 && c.d_x / 128 < c.num_sms && b % 256 == 0 &&
          b > 0 && b <= c.cfg.max_b && c.cfg.split_AB && c.k <= 32 && !c.adam_m && !c.z;
 }
 
@@ -1292,6 +1292,7 @@ int tc_stream_setup(Ctx& c) {
   c.tc_st_ok = 0;
   const char* env = getenv("SGEP_TC_STREAM");
   if (env && env[0] == '0') return SGEP_OK;
+  if (c.cfg.dtype != SGEP_BF16) return SGEP_OK;  // the streamed kernel reads BF16 rows
   if (c.d_x != c.d_y || c.d_x % (2 * kR) != 0 || c.d_x / 128 >= c.num_sms) return SGEP_OK;
   int per_sm = 0;
   SGEP_CUDA_TRY(cudaFuncSetAttribute(k_tc_stream, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem));

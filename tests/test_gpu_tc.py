@@ -29,10 +29,58 @@ from gpu_util import assert_within, step_errors  # noqa: E402
 TC_TOL = 5e-5
 
 
-def _tc_solver(dx, k, **kw):
+def _tc_solver(dx, k, dtype=None, **kw):
     from paper_2206_04993_gb300 import Solver
-    return Solver(kind=S.SGEP_CCA, d_x=dx, d_y=dx, k=k, dtype=S.SGEP_BF16, path=S.SGEP_PATH_TC,
-                  debug=1, **kw)
+    return Solver(kind=S.SGEP_CCA, d_x=dx, d_y=dx, k=k, dtype=S.SGEP_BF16 if dtype is None else dtype,
+                  path=S.SGEP_PATH_TC, debug=1, **kw)
+
+
+# FP32 rows on the tensor cores: each row value is split into a BF16 pair as well (hi + lo keeps
+# about 16 significant bits, |x - hi - lo| <= 2^-16 |x|), and the products add
+# X_hi [V_hi | V_lo] + X_lo V_hi. A product term now carries two pair errors near 2^-17 each
+# (the row's and V's, or the row's and P's) where a BF16 row carries one, so the products, the
+# k x k terms and the update direction get twice the BF16 bar. The update itself, V' and [Bv]'
+# (whose change is eta times the direction), keeps the FP32 path's 1e-5.
+TC_F32_TOL = 2 * TC_TOL
+F32_STEP_TOL = 1e-5
+
+
+def _assert_f32_step(err):
+    upd = {key: v for key, v in err.items() if key[0] in "VS"}
+    rest = {key: v for key, v in err.items() if key[0] not in "VS"}
+    assert_within(upd, F32_STEP_TOL)
+    assert_within(rest, TC_F32_TOL)
+
+
+@pytest.mark.parametrize("dx,k,b", [(256, 32, 128), (512, 8, 384), (768, 17, 256), (1024, 32, 512)])
+def test_tc_f32_rows_single_step_matches_oracle(dx, k, b):
+    model = synth.planted_cca(dx, dx, np.linspace(0.9, 0.3, 8), seed=dx + k + 1)
+    X, Y = synth.draw_rows(model, b, batch=4)
+    V0 = synth.random_unit_columns(2 * dx, k, seed=k + 2)
+    S0 = 0.8 * V0 + 0.05 * synth.random_unit_columns(2 * dx, k, seed=k + 3)
+    with _tc_solver(dx, k, dtype=S.SGEP_F32, eta0=0.3, gamma0=0.4, rho=1e-3, max_b=512) as s:
+        assert s.path == S.SGEP_PATH_TC
+        err = step_errors(s, V0, S0, X, Y, "cca", 0.3, 0.4, 1e-3, dtype="f32")
+    print(err)
+    _assert_f32_step(err)
+
+
+def test_tc_f32_rows_and_generic_agree_over_steps():
+    """Fifty steps of FP32 rows on the tensor cores and on the generic SIMT path."""
+    from paper_2206_04993_gb300 import Solver
+    model = synth.planted_cca(512, 512, np.linspace(0.9, 0.3, 16), seed=6)
+    X, Y = synth.draw_rows(model, 256 * 50, batch=2)
+    Xd = torch.from_numpy(X.astype(np.float32)).cuda()
+    Yd = torch.from_numpy(Y.astype(np.float32)).cuda()
+    V0 = synth.random_unit_columns(1024, 16, seed=3).astype(np.float32)
+    out = []
+    for path in (S.SGEP_PATH_GENERIC, S.SGEP_PATH_TC):
+        with Solver(kind=S.SGEP_CCA, d_x=512, d_y=512, k=16, dtype=S.SGEP_F32, path=path,
+                    eta0=0.2, gamma0=0.5, max_b=256) as s:
+            s.set_V(V0)
+            s.step_many(Xd, Yd, 256, 50)
+            out.append(s.V())
+    assert np.linalg.norm(out[1] - out[0]) / np.linalg.norm(out[0]) < 1e-3
 
 
 @pytest.mark.parametrize("dx,k,b", [(256, 32, 128), (512, 32, 256), (512, 8, 384), (768, 17, 256)])
@@ -84,6 +132,20 @@ def test_tc_full_size_step_matches_oracle():
         assert s.launches - l0 == 1
     print(err)
     assert_within(err, TC_TOL)
+
+
+@pytest.mark.slow
+def test_tc_f32_rows_full_size_step_matches_oracle():
+    """FP32 rows at the full activation-like shape (d_x = d_y = 16384, k = 32, b = 4096)."""
+    cfg = synth.config_c3()
+    X, Y = synth.draw_rows(cfg["model"], 4096, batch=1, dtype=np.float32)
+    V0 = synth.random_unit_columns(32768, 32, seed=2)
+    S0 = 0.8 * V0 + 0.05 * synth.random_unit_columns(32768, 32, seed=3)
+    with _tc_solver(16384, 32, dtype=S.SGEP_F32, eta0=0.3, gamma0=0.3, rho=1e-6, max_b=4096) as s:
+        assert s.path == S.SGEP_PATH_TC
+        err = step_errors(s, V0, S0, X, Y, "cca", 0.3, 0.3, 1e-6, dtype="f32")
+    print(err)
+    _assert_f32_step(err)
 
 
 # Shapes the streamed steps take (d_x a multiple of 512, b of 256): one and several 256-row
