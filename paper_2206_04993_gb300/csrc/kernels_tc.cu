@@ -1077,51 +1077,66 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 // keeps about 16 significant bits of x. The MMAs add X_hi [V_hi | V_lo] + X_lo V_hi (the
 // X_lo V_lo term is below the pairs' resolution), the same accumulator columns as the BF16 path.
 
-constexpr int kF32Stages = 3;
-constexpr int kF32Threads = 320;  // warps 0: TMA, 1: MMA, 2-5: epilogue, 6-9: converters
-constexpr int kF32Conv = 128;     // converter threads
+// Four landing slots [FP32 tile 32 KB | operand box 8 KB] keep three tiles in flight from HBM;
+// two conversion slots [BF16 hi 16 KB | BF16 lo 16 KB] take the converted tiles to the MMAs.
+constexpr int kF32Land = 4, kF32ConvSlots = 2;
+constexpr int kF32LandB = 40960, kF32ConvB = 32768;
+constexpr size_t kF32Smem = (size_t)kF32Land * kF32LandB + (size_t)kF32ConvSlots * kF32ConvB + 1024 + 256;
+constexpr int kF32Threads = 448;  // warps 0: TMA, 1: MMA, 2-5: epilogue, 6-13: converters
+constexpr int kF32Conv = 256;     // converter threads
 
 // FP32 tile of R rows x C columns (C / 32 boxes of [R][32]) into hi and lo (C / 64 boxes of
-// [R][64] BF16 each); thread t of nthr. Consecutive threads take consecutive rows of one
-// 8-column group, so a quarter warp's 16-byte accesses fall in distinct banks.
-__device__ __forceinline__ void split_f32_tile(const uint8_t* src, uint8_t* hi, uint8_t* lo, int R, int C, int t,
-                                               int nthr) {
-  const int ngrp = C / 8;
-  for (int it = t; it < R * ngrp; it += nthr) {
-    const int r = it % R, c = 8 * (it / R);
-    const int rr = r & 7;
-    const uint8_t* sb = src + (size_t)(c / 32) * (R * 128) + (r >> 3) * 1024 + rr * 128;
+// [R][64] BF16 each); converter thread t of kF32Conv. Consecutive threads take consecutive rows
+// of one 8-column group, so a quarter warp's 16-byte accesses fall in distinct banks. Each
+// thread's items are unrolled with all their loads issued first.
+template <int R, int C>
+__device__ __forceinline__ void split_f32_tile(const uint8_t* src, uint8_t* hi, uint8_t* lo, int t) {
+  constexpr int kItems = R * (C / 8) / kF32Conv;
+  static_assert(R * (C / 8) % kF32Conv == 0, "items split evenly over the converter threads");
+  float4 x0[kItems], x1[kItems];
+#pragma unroll
+  for (int u = 0; u < kItems; ++u) {
+    const int it = t + u * kF32Conv;
+    const int r = it % R, c = 8 * (it / R), rr = r & 7;
+    const uint8_t* sb = src + (c / 32) * (R * 128) + (r >> 3) * 1024 + rr * 128;
     const int q = (c & 31) >> 2;
-    const float4 x0 = *reinterpret_cast<const float4*>(sb + ((q ^ rr) << 4));
-    const float4 x1 = *reinterpret_cast<const float4*>(sb + (((q + 1) ^ rr) << 4));
-    const float xs[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+    x0[u] = *reinterpret_cast<const float4*>(sb + ((q ^ rr) << 4));
+    x1[u] = *reinterpret_cast<const float4*>(sb + (((q + 1) ^ rr) << 4));
+  }
+#pragma unroll
+  for (int u = 0; u < kItems; ++u) {
+    const int it = t + u * kF32Conv;
+    const int r = it % R, c = 8 * (it / R), rr = r & 7;
+    const float xs[8] = {x0[u].x, x0[u].y, x0[u].z, x0[u].w, x1[u].x, x1[u].y, x1[u].z, x1[u].w};
     uint32_t h[4], l[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const __nv_bfloat162 hv = __floats2bfloat162_rn(xs[2 * u], xs[2 * u + 1]);
+    for (int v = 0; v < 4; ++v) {
+      const __nv_bfloat162 hv = __floats2bfloat162_rn(xs[2 * v], xs[2 * v + 1]);
       const __nv_bfloat162 lv =
-          __floats2bfloat162_rn(xs[2 * u] - __low2float(hv), xs[2 * u + 1] - __high2float(hv));
-      h[u] = *reinterpret_cast<const uint32_t*>(&hv);
-      l[u] = *reinterpret_cast<const uint32_t*>(&lv);
+          __floats2bfloat162_rn(xs[2 * v] - __low2float(hv), xs[2 * v + 1] - __high2float(hv));
+      h[v] = *reinterpret_cast<const uint32_t*>(&hv);
+      l[v] = *reinterpret_cast<const uint32_t*>(&lv);
     }
-    const size_t toff = (size_t)(c / 64) * (R * 128) + (r >> 3) * 1024 + rr * 128 + ((((c & 63) >> 3) ^ rr) << 4);
+    const int toff = (c / 64) * (R * 128) + (r >> 3) * 1024 + rr * 128 + ((((c & 63) >> 3) ^ rr) << 4);
     *reinterpret_cast<uint4*>(hi + toff) = make_uint4(h[0], h[1], h[2], h[3]);
     *reinterpret_cast<uint4*>(lo + toff) = make_uint4(l[0], l[1], l[2], l[3]);
   }
 }
 
-// P = X V_x, Q = Y V_y from FP32 rows. grid: (b/128 row tiles, 2 views, splits). A stage is
-// [X: two 128 x 32 FP32 boxes][V^T box 64 x 64][hi 128 x 64][lo 128 x 64].
+// P = X V_x, Q = Y V_y from FP32 rows. grid: (b/128 row tiles, 2 views, splits). A landing
+// slot is [X: two 128 x 32 FP32 boxes][V^T box 64 x 64], a conversion slot [hi 128 x 64][lo 128 x 64].
 __global__ void __launch_bounds__(kF32Threads, 1)
     k_tc_project_f32(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapY,
                      const __grid_constant__ CUtensorMap mapVt, const TcProjArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = align1024(smem_raw);
-  constexpr int kX = 32768, kV = 8192, kH = 16384, kStage = kX + kV + 2 * kH;
-  uint64_t* full = (uint64_t*)(base + kF32Stages * kStage);
-  uint64_t* conv = full + kF32Stages;
-  uint64_t* empty = conv + kF32Stages;
-  uint64_t* done = empty + kF32Stages;
+  constexpr int kX = 32768, kH = 16384;
+  uint8_t* cbase = base + kF32Land * kF32LandB;
+  uint64_t* full = (uint64_t*)(cbase + kF32ConvSlots * kF32ConvB);  // [kF32Land] tile and operand landed
+  uint64_t* lempty = full + kF32Land;                                // [kF32Land] MMAs done with the operand
+  uint64_t* cfull = lempty + kF32Land;                               // [kF32ConvSlots] tile converted
+  uint64_t* cempty = cfull + kF32ConvSlots;                          // [kF32ConvSlots] MMAs done with it
+  uint64_t* done = cempty + kF32ConvSlots;
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
   int* abort_flag = (int*)(tmem_slot + 1);
   const int tid = threadIdx.x, warp = tid / 32, lane = tid & 31;
@@ -1137,10 +1152,13 @@ __global__ void __launch_bounds__(kF32Threads, 1)
     tmem_relinquish();
   }
   if (tid == 0) {
-    for (int s = 0; s < kF32Stages; ++s) {
+    for (int s = 0; s < kF32Land; ++s) {
       mbar_init(full + s, 1);
-      mbar_init(conv + s, kF32Conv / 32);
-      mbar_init(empty + s, 1);
+      mbar_init(lempty + s, 1);
+    }
+    for (int s = 0; s < kF32ConvSlots; ++s) {
+      mbar_init(cfull + s, kF32Conv / 32);
+      mbar_init(cempty + s, 1);
     }
     mbar_init(done, 1);
     *abort_flag = 0;
@@ -1156,15 +1174,15 @@ __global__ void __launch_bounds__(kF32Threads, 1)
   if (warp == 0 && lane == 0) {
     const uint64_t keep = policy_evict_last();
     for (int ks = 0; ks < nk; ++ks) {
-      const int st = ks % kF32Stages;
-      if (ks >= kF32Stages && !mbar_wait(empty + st, ((ks / kF32Stages) - 1) & 1)) {
+      const int st = ks % kF32Land;
+      if (ks >= kF32Land && !mbar_wait(lempty + st, ((ks / kF32Land) - 1) & 1)) {
         atomicOr(a.dflag, kFlagTimeout);
         *(volatile int*)abort_flag = 1;
         break;
       }
       if (*(volatile int*)abort_flag) break;
-      uint8_t* sa = base + st * kStage;
-      mbar_arrive_expect_tx(full + st, kX + kV);
+      uint8_t* sa = base + st * kF32LandB;
+      mbar_arrive_expect_tx(full + st, kF32LandB);
       tma_load_2d(sa, mZ, (int)(c0 + (int64_t)ks * 64), (int)row0, full + st);
       tma_load_2d(sa + kX / 2, mZ, (int)(c0 + (int64_t)ks * 64 + 32), (int)row0, full + st);
       tma_load_2d_hint(sa + kX, &mapVt, (int)(voff + c0 + (int64_t)ks * 64), 0, full + st, keep);
@@ -1173,34 +1191,34 @@ __global__ void __launch_bounds__(kF32Threads, 1)
     // converters: each landed FP32 tile into its hi / lo BF16 tiles
     const int t = tid - 192;
     for (int ks = 0; ks < nk; ++ks) {
-      const int st = ks % kF32Stages;
-      if (!mbar_wait(full + st, (ks / kF32Stages) & 1)) {
+      const int st = ks % kF32Land, cs = ks % kF32ConvSlots;
+      if (!mbar_wait(full + st, (ks / kF32Land) & 1) ||
+          (ks >= kF32ConvSlots && !mbar_wait(cempty + cs, ((ks / kF32ConvSlots) - 1) & 1))) {
         if (lane == 0) atomicOr(a.dflag, kFlagTimeout);
         *(volatile int*)abort_flag = 1;
         break;
       }
       if (*(volatile int*)abort_flag) break;
-      uint8_t* sa = base + st * kStage;
-      split_f32_tile(sa, sa + kX + kV, sa + kX + kV + kH, 128, 64, t, kF32Conv);
+      uint8_t* cb = cbase + cs * kF32ConvB;
+      split_f32_tile<128, 64>(base + st * kF32LandB, cb, cb + kH, t);
       fence_proxy_async_smem();  // the tiles are read by the tensor cores (async proxy)
       __syncwarp();
-      if (lane == 0) mbar_arrive(conv + st);
+      if (lane == 0) mbar_arrive(cfull + cs);
     }
   } else if (warp == 1 && lane == 0) {
     const uint32_t id64 = idesc_bf16(128, 64, 0, 0), id32 = idesc_bf16(128, 32, 0, 0);
     bool ok = true;
     for (int ks = 0; ks < nk; ++ks) {
-      const int st = ks % kF32Stages;
-      if (!mbar_wait(conv + st, (ks / kF32Stages) & 1) || *(volatile int*)abort_flag) {
+      const int st = ks % kF32Land, cs = ks % kF32ConvSlots;
+      if (!mbar_wait(cfull + cs, (ks / kF32ConvSlots) & 1) || *(volatile int*)abort_flag) {
         atomicOr(a.dflag, kFlagTimeout);
         *(volatile int*)abort_flag = 1;
         ok = false;
         break;
       }
       tc_fence_after();
-      uint8_t* sa = base + st * kStage;
-      const uint8_t* vt = sa + kX;
-      const uint8_t* xh = sa + kX + kV;
+      const uint8_t* vt = base + st * kF32LandB + kX;
+      const uint8_t* xh = cbase + cs * kF32ConvB;
       const uint8_t* xl = xh + kH;
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) {
@@ -1208,7 +1226,8 @@ __global__ void __launch_bounds__(kF32Threads, 1)
                  (ks | kk) ? 1u : 0u);
         mma_bf16(tmem, desc_sw128(xl + kk * 32, 16, 1024), desc_sw128(vt + kk * 32, 16, 1024), id32, 1u);
       }
-      mma_commit(empty + st);
+      mma_commit(cempty + cs);
+      mma_commit(lempty + st);
     }
     if (ok) mma_commit(done);
     else mbar_arrive(done);
@@ -1239,19 +1258,21 @@ __global__ void __launch_bounds__(kF32Threads, 1)
 
 // A_t V and B_t V from FP32 rows. grid: d/256 column slices (X slices first). Rows in 64-row
 // blocks streamed last-first (the rows the projection read last are still in L2), each block
-// in two stages of 128 columns: [X: four 64 x 32 FP32 boxes][operand 64 x 64][hi 2 x 64 x 64]
-// [lo 2 x 64 x 64].
+// in two steps of 128 columns: landing slot [X: four 64 x 32 FP32 boxes][operand 64 x 64],
+// conversion slot [hi 2 x 64 x 64][lo 2 x 64 x 64].
 __global__ void __launch_bounds__(kF32Threads, 1)
     k_tc_backproject_f32(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapY,
                          const __grid_constant__ CUtensorMap mapPt, const __grid_constant__ CUtensorMap mapQt,
                          const TcBackArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = align1024(smem_raw);
-  constexpr int kX = 32768, kW = 8192, kH = 16384, kStage = kX + kW + 2 * kH;
-  uint64_t* full = (uint64_t*)(base + kF32Stages * kStage);
-  uint64_t* conv = full + kF32Stages;
-  uint64_t* empty = conv + kF32Stages;
-  uint64_t* done = empty + kF32Stages;
+  constexpr int kX = 32768, kH = 16384;
+  uint8_t* cbase = base + kF32Land * kF32LandB;
+  uint64_t* full = (uint64_t*)(cbase + kF32ConvSlots * kF32ConvB);  // [kF32Land] tile and operand landed
+  uint64_t* lempty = full + kF32Land;                                // [kF32Land] MMAs done with the operand
+  uint64_t* cfull = lempty + kF32Land;                               // [kF32ConvSlots] tile converted
+  uint64_t* cempty = cfull + kF32ConvSlots;                          // [kF32ConvSlots] MMAs done with it
+  uint64_t* done = cempty + kF32ConvSlots;
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
   int* abort_flag = (int*)(tmem_slot + 1);
   const int tid = threadIdx.x, warp = tid / 32, lane = tid & 31;
@@ -1269,10 +1290,13 @@ __global__ void __launch_bounds__(kF32Threads, 1)
     tmem_relinquish();
   }
   if (tid == 0) {
-    for (int s = 0; s < kF32Stages; ++s) {
+    for (int s = 0; s < kF32Land; ++s) {
       mbar_init(full + s, 1);
-      mbar_init(conv + s, kF32Conv / 32);
-      mbar_init(empty + s, 1);
+      mbar_init(lempty + s, 1);
+    }
+    for (int s = 0; s < kF32ConvSlots; ++s) {
+      mbar_init(cfull + s, kF32Conv / 32);
+      mbar_init(cempty + s, 1);
     }
     mbar_init(done, 1);
     *abort_flag = 0;
@@ -1289,18 +1313,18 @@ __global__ void __launch_bounds__(kF32Threads, 1)
   if (warp == 0 && lane == 0) {
     const uint64_t once = policy_evict_first();
     for (int s = 0; s < nst; ++s) {
-      const int st = s % kF32Stages;
+      const int st = s % kF32Land;
       const int64_t r0 = (int64_t)(nrb - 1 - s / 2) * 64;
       const int h = s & 1;
-      if (s >= kF32Stages && !mbar_wait(empty + st, ((s / kF32Stages) - 1) & 1)) {
+      if (s >= kF32Land && !mbar_wait(lempty + st, ((s / kF32Land) - 1) & 1)) {
         atomicOr(a.dflag, kFlagTimeout);
         *(volatile int*)abort_flag = 1;
         break;
       }
       if (*(volatile int*)abort_flag) break;
-      uint8_t* sa = base + st * kStage;
+      uint8_t* sa = base + st * kF32LandB;
       const bool rowA = !a.split || r0 < a.nA;
-      mbar_arrive_expect_tx(full + st, kX + kW);
+      mbar_arrive_expect_tx(full + st, kF32LandB);
 #pragma unroll
       for (int j = 0; j < 4; ++j)
         tma_load_2d_hint(sa + j * 8192, mZ, (int)(c0 + 128 * h + 32 * j), (int)r0, full + st, once);
@@ -1309,37 +1333,37 @@ __global__ void __launch_bounds__(kF32Threads, 1)
   } else if (warp >= 6) {
     const int t = tid - 192;
     for (int s = 0; s < nst; ++s) {
-      const int st = s % kF32Stages;
-      if (!mbar_wait(full + st, (s / kF32Stages) & 1)) {
+      const int st = s % kF32Land, cs = s % kF32ConvSlots;
+      if (!mbar_wait(full + st, (s / kF32Land) & 1) ||
+          (s >= kF32ConvSlots && !mbar_wait(cempty + cs, ((s / kF32ConvSlots) - 1) & 1))) {
         if (lane == 0) atomicOr(a.dflag, kFlagTimeout);
         *(volatile int*)abort_flag = 1;
         break;
       }
       if (*(volatile int*)abort_flag) break;
-      uint8_t* sa = base + st * kStage;
-      split_f32_tile(sa, sa + kX + kW, sa + kX + kW + kH, 64, 128, t, kF32Conv);
+      uint8_t* cb = cbase + cs * kF32ConvB;
+      split_f32_tile<64, 128>(base + st * kF32LandB, cb, cb + kH, t);
       fence_proxy_async_smem();
       __syncwarp();
-      if (lane == 0) mbar_arrive(conv + st);
+      if (lane == 0) mbar_arrive(cfull + cs);
     }
   } else if (warp == 1 && lane == 0) {
     const uint32_t id64 = idesc_bf16(128, 64, 1, 0), id32 = idesc_bf16(128, 32, 1, 0);
     bool ok = true;
     bool usedA[2] = {false, false}, usedB[2] = {false, false};
     for (int s = 0; s < nst; ++s) {
-      const int st = s % kF32Stages;
+      const int st = s % kF32Land, cs = s % kF32ConvSlots;
       const int64_t r0 = (int64_t)(nrb - 1 - s / 2) * 64;
       const int h = s & 1;
-      if (!mbar_wait(conv + st, (s / kF32Stages) & 1) || *(volatile int*)abort_flag) {
+      if (!mbar_wait(cfull + cs, (s / kF32ConvSlots) & 1) || *(volatile int*)abort_flag) {
         atomicOr(a.dflag, kFlagTimeout);
         *(volatile int*)abort_flag = 1;
         ok = false;
         break;
       }
       tc_fence_after();
-      uint8_t* sa = base + st * kStage;
-      const uint8_t* w = sa + kX;
-      const uint8_t* xh = sa + kX + kW;
+      const uint8_t* w = base + st * kF32LandB + kX;
+      const uint8_t* xh = cbase + cs * kF32ConvB;
       const uint8_t* xl = xh + kH;
       const bool rowA = !a.split || r0 < a.nA;
       const uint32_t dcol = tmem + (rowA ? 0u : 128u) + 64 * h;
@@ -1352,7 +1376,8 @@ __global__ void __launch_bounds__(kF32Threads, 1)
       }
       if (rowA) usedA[h] = true;
       else usedB[h] = true;
-      mma_commit(empty + st);
+      mma_commit(cempty + cs);
+      mma_commit(lempty + st);
     }
     if (ok) mma_commit(done);
     else mbar_arrive(done);
@@ -1460,7 +1485,7 @@ int tc_alloc(Ctx& c) {
   }
   if (c.cfg.dtype == SGEP_F32) {
     // FP32 rows: three stages of [FP32 tile | operand box | BF16 hi | BF16 lo]
-    const size_t sf = kF32Stages * 73728 + 1024 + 256;
+    const size_t sf = kF32Smem;
     SGEP_CUDA_TRY(cudaFuncSetAttribute(k_tc_project_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf));
     SGEP_CUDA_TRY(cudaFuncSetAttribute(k_tc_backproject_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf));
     c.tc_smem_p = c.tc_smem_b = sf;
