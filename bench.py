@@ -1084,6 +1084,9 @@ def run_native(args):
         if args.workload != "cca_d32768_k32_b4096_f32":
             # the plain FP32 form of the same problem
             forms["cca_d32768_k32_b4096_f32"] = measure_throughput("cca_d32768_k32_b4096_f32", 8, 3, dev, rank)
+            # the same FP32 rows on the generic SIMT path (register-tiled FMA contractions)
+            forms["cca_d32768_k32_b4096_f32_simt"] = measure_throughput("cca_d32768_k32_b4096_f32", 8, 3, dev, rank,
+                                                                        path=1)
         if args.workload == "cca_d32768_k32_b4096_bf16":
             forms["bf16_vs_f32_step_speedup_d32768"] = forms["cca_d32768_k32_b4096_f32"]["ms_per_step"] / ms_step
         forms["batch64_cca_lda_b512_f32"] = measure_batch("f32", 40, 3, dev, seed=rank)
