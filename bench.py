@@ -400,18 +400,22 @@ def measure_throughput(workload, steps, warmup, dev, rank=0, path=0):
     solver = Solver(kind=sgep.SGEP_CCA, d_x=dx, d_y=dy, k=k,
                     dtype=sgep.SGEP_BF16 if dtype == "bf16" else sgep.SGEP_F32,
                     eta0=cfg["eta0"], gamma0=cfg["gamma0"], rho=cfg["rho"], max_b=b, path=path, seed=rank)
-    for i in range(warmup):
-        j = i % nb
-        solver.step(X[j * b:(j + 1) * b], Y[j * b:(j + 1) * b])
+    def run(start, count):  # consecutive minibatches of the pool, as few sgep_step_many calls as it allows
+        i = 0
+        while i < count:
+            j = (start + i) % nb
+            n = min(count - i, nb - j)
+            solver.step_many(X[j * b:(j + n) * b], Y[j * b:(j + n) * b], b, n)
+            i += n
+
+    run(0, warmup)
     solver.sync()
     torch.cuda.synchronize()
     l0 = solver.launches
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(dev) as clk:
         e0.record()
-        for i in range(steps):
-            j = (warmup + i) % nb
-            solver.step(X[j * b:(j + 1) * b], Y[j * b:(j + 1) * b])
+        run(warmup, steps)
         e1.record()
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
