@@ -186,13 +186,15 @@ __device__ __forceinline__ void reduce_quads(const float (&acc)[4][4], bool acti
 }
 
 // ---------------------------------------------------------------------------
-// Projection of plain FP32 rows through the cp.async ring (same tile and result as
-// project_tile). Stage st holds rows [row0, row0 + 64) x columns [c0, c0 + 32) row-major and
-// V's rows [c0, c0 + 32); a thread owns rows rq + 16a (a < 4) and one player quad, and per
-// column quad reads 4 float4 of rows and 4 float4 of V for 64 FMAs.
+// Projection of FP32 rows through the cp.async ring (same tile and result as project_tile).
+// Stage st holds rows [row0, row0 + 64) x columns [c0, c0 + 32) row-major and V's rows
+// [c0, c0 + 32); a thread owns rows rq + 16a (a < 4) and one player quad, and per column quad
+// reads 4 float4 of rows and 4 float4 of V for 64 FMAs. With `cz`, each landed stage is centred
+// in shared memory (a thread: one row, 8 columns) before it is read.
 __device__ inline void project_tile_ring(const float* __restrict__ X, const float* __restrict__ Y, int64_t n,
                                          int64_t dx, int64_t dy, const float* __restrict__ V, int k, int64_t chunk,
-                                         int nchunk_x, float* __restrict__ PQ, int bx, int by, float* smem) {
+                                         int nchunk_x, float* __restrict__ PQ, int bx, int by, float* smem,
+                                         const Centring* cz = nullptr) {
   constexpr int NS = kProjRing;
   constexpr int kXStage = kProjRows * kPRXS, kVStage = kProjCols * kWS;
   float* Xs = smem;                // [NS][kProjRows][kPRXS]
@@ -265,6 +267,25 @@ __device__ inline void project_tile_ring(const float* __restrict__ X, const floa
     cp_async_commit_all();  // empty groups keep one group per stage
   };
 
+  // centring roles: row cr, columns cc8 .. cc8 + 7 of every stage (the row's label is fixed)
+  static_assert(kProjRows * kProjCols / 8 == kThreads, "one centring item per thread");
+  const int cr = tid / 4, cc8 = 8 * (tid % 4);
+  bool crow = cz && row0 + cr < n;
+  const float* mrow = nullptr;
+  if (crow) {
+    if (cz->labels) {
+      const int lab = cz->labels[row0 + cr];
+      if ((unsigned)lab >= (unsigned)cz->C) {  // flagged; the row stays uncentred
+        atomicOr(cz->dflag, kFlagBadLabel);
+        crow = false;
+      } else {
+        mrow = cz->mean + (int64_t)lab * ld;
+      }
+    } else {
+      mrow = isY ? cz->mean_y : cz->mean;
+    }
+  }
+
   __syncthreads();  // the workspace may still be read by this block's previous tile
   float acc[4][4];
 #pragma unroll
@@ -277,6 +298,16 @@ __device__ inline void project_tile_ring(const float* __restrict__ X, const floa
     cp_async_wait_pending<NS - 2>();
     __syncthreads();       // stage st landed for every thread; stage st - 1 is no longer read
     issue(st + NS - 1);    // into the slot of stage st - 1
+    if (cz) {
+      if (crow) {
+        float* xs = Xs + (st % NS) * kXStage + cr * kPRXS + cc8;
+        const int64_t c0 = c_begin + (int64_t)st * kProjCols + cc8;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (c0 + u < c_end) xs[u] -= mrow[c0 + u];
+      }
+      __syncthreads();
+    }
     if (active) {
       const float* xs = Xs + (st % NS) * kXStage + rq * kPRXS;
       const float* vs = Vs + (st % NS) * kVStage + 4 * pq;
@@ -300,15 +331,16 @@ __device__ inline void project_tile_ring(const float* __restrict__ X, const floa
       [&](int r) { return (row0 + r) * 2 * k + pqoff; }, 1, 16);
 }
 
-// Back-projection of plain FP32 rows through the cp.async ring (same tile and result as
+// Back-projection of FP32 rows through the cp.async ring (same tile and result as
 // backproject_tile): stage st holds rows [r0, r0 + 32) of the 64-column block and their
-// P / Q weights, masked per estimate by zero-filled copies.
+// P / Q weights, masked per estimate by zero-filled copies. With `cz`, each landed stage is
+// centred in shared memory (a thread: one row, 8 columns) before it is read.
 __device__ inline void backproject_tile_ring(const float* __restrict__ X, const float* __restrict__ Y, int64_t b,
                                              int64_t dx, int64_t dy, int64_t nA, int kind, int split,
                                              const float* __restrict__ PQ, int k, int nblk_x,
                                              int64_t rows_per_split, float inv_nA, float inv_nB,
                                              float* __restrict__ AV, float* __restrict__ BV, int bx, int by,
-                                             float* smem) {
+                                             float* smem, const Centring* cz = nullptr) {
   constexpr int NS = kBpRing;
   constexpr int kZStage = kBpRows * kBpZS, kWStage = kBpRows * kWS;
   float* Zs = smem;                      // [NS][kBpRows][kBpZS]
@@ -410,12 +442,37 @@ __device__ inline void backproject_tile_ring(const float* __restrict__ X, const 
     for (int c = 0; c < 4; ++c) accA[a][c] = accB[a][c] = 0.f;
 #pragma unroll
   for (int st = 0; st < NS - 1; ++st) issue(st);
+  static_assert(kBpRows * kBpCols / 8 == kThreads, "one centring item per thread");
+  const int cr = tid / 8, cc8 = 8 * (tid % 8);  // centring roles: row cr, columns cc8 .. cc8 + 7
   for (int st = 0; st < nst; ++st) {
     cp_async_wait_pending<NS - 2>();
     __syncthreads();
     issue(st + NS - 1);
     const int64_t r0 = r_begin + (int64_t)st * kBpRows;
     const int nr = (int)min((int64_t)kBpRows, r_end - r0);
+    if (cz) {
+      const int64_t row = r0 + cr;
+      if (row < r_end) {
+        const float* mrow = isY ? cz->mean_y : cz->mean;
+        bool ok = true;
+        if (cz->labels) {
+          const int lab = cz->labels[row];
+          if ((unsigned)lab >= (unsigned)cz->C) {  // flagged; the row stays uncentred
+            atomicOr(cz->dflag, kFlagBadLabel);
+            ok = false;
+          } else {
+            mrow = cz->mean + (int64_t)lab * ld;
+          }
+        }
+        if (ok) {
+          float* zs = Zs + (st % NS) * kZStage + cr * kBpZS + cc8;
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (col0 + cc8 + u < ld) zs[u] -= mrow[col0 + cc8 + u];
+        }
+      }
+      __syncthreads();
+    }
     const bool useA = wantA && (!splitAB || r0 < nA);
     const bool useB = wantB && (!splitAB || r0 + nr > nA);
     if (active) {
@@ -459,8 +516,8 @@ __device__ void project_tile(const T* __restrict__ X, const T* __restrict__ Y, i
                              int bx, int by, float* smem) {
   static_assert(kProjRows == 64 && kProjRows * kProjCols % (4 * kThreads) == 0, "projection staging");
   if constexpr (std::is_same<T, float>::value) {
-    if (!cz.mean && !rsx && !rsy) {
-      project_tile_ring(X, Y, n, dx, dy, V, k, chunk, nchunk_x, PQ, bx, by, smem);
+    if (!rsx && !rsy) {  // FP32 rows without a row scale: the cp.async ring (centred in shared memory)
+      project_tile_ring(X, Y, n, dx, dy, V, k, chunk, nchunk_x, PQ, bx, by, smem, cz.mean ? &cz : nullptr);
       return;
     }
   }
@@ -573,9 +630,9 @@ __device__ void backproject_tile(const T* __restrict__ X, const T* __restrict__ 
                                  float* smem) {
   static_assert(kBpCols == 64 && kBpRows * kBpCols % kThreads == 0, "back-projection staging");
   if constexpr (std::is_same<T, float>::value) {
-    if (!cz.mean && !rsx && !rsy) {
+    if (!rsx && !rsy) {  // FP32 rows without a row scale: the cp.async ring (centred in shared memory)
       backproject_tile_ring(X, Y, b, dx, dy, nA, kind, split, PQ, k, nblk_x, rows_per_split, inv_nA, inv_nB, AV, BV,
-                            bx, by, smem);
+                            bx, by, smem, cz.mean ? &cz : nullptr);
       return;
     }
   }
