@@ -51,8 +51,12 @@ constexpr int cmax(int a, int b) { return a > b ? a : b; }
 constexpr int kProjRing = 4;
 constexpr int kBpRing = 3;
 constexpr int kPRXS = kProjCols + kPad;
-constexpr int kProjRingSmem = kProjRing * (kProjRows * kPRXS + kProjCols * kWS);
-constexpr int kBpRingSmem = kBpRing * (kBpRows * kBpZS + 2 * kBpRows * kWS);
+// BF16 rows land in their own buffer of each stage (row stride an odd number of 16-byte
+// chunks) and are widened to FP32 into the stage, centred if they are, before it is read.
+constexpr int kPLB = kProjCols + 8;  // BF16 landing row stride of the projection ring
+constexpr int kBLB = kBpCols + 8;    // ... and of the back-projection ring
+constexpr int kProjRingSmem = kProjRing * (kProjRows * kPRXS + kProjCols * kWS + kProjRows * kPLB / 2);
+constexpr int kBpRingSmem = kBpRing * (kBpRows * kBpZS + 2 * kBpRows * kWS + kBpRows * kBLB / 2);
 
 // Shared-memory floats each tile needs (k <= 64, C <= 32). The register path's weights are
 // double-buffered.
@@ -191,19 +195,22 @@ __device__ __forceinline__ void reduce_quads(const float (&acc)[4][4], bool acti
 // [c0, c0 + 32); a thread owns rows rq + 16a (a < 4) and one player quad, and per column quad
 // reads 4 float4 of rows and 4 float4 of V for 64 FMAs. With `cz`, each landed stage is centred
 // in shared memory (a thread: one row, 8 columns) before it is read.
-__device__ inline void project_tile_ring(const float* __restrict__ X, const float* __restrict__ Y, int64_t n,
-                                         int64_t dx, int64_t dy, const float* __restrict__ V, int k, int64_t chunk,
+template <typename T>
+__device__ inline void project_tile_ring(const T* __restrict__ X, const T* __restrict__ Y, int64_t n, int64_t dx,
+                                         int64_t dy, const float* __restrict__ V, int k, int64_t chunk,
                                          int nchunk_x, float* __restrict__ PQ, int bx, int by, float* smem,
                                          const Centring* cz = nullptr) {
+  constexpr bool kB = !std::is_same<T, float>::value;  // BF16 rows: landed, then widened in shared memory
   constexpr int NS = kProjRing;
   constexpr int kXStage = kProjRows * kPRXS, kVStage = kProjCols * kWS;
   float* Xs = smem;                // [NS][kProjRows][kPRXS]
   float* Vs = smem + NS * kXStage;  // [NS][kProjCols][kWS]
+  __nv_bfloat16* Lb = reinterpret_cast<__nv_bfloat16*>(Vs + NS * kVStage);  // [NS][kProjRows][kPLB]
   const int tid = threadIdx.x;
   const int64_t row0 = (int64_t)bx * kProjRows;
   const bool isY = by >= nchunk_x;
   const int cidx = isY ? by - nchunk_x : by;
-  const float* Z = isY ? Y : X;
+  const T* Z = isY ? Y : X;
   const int64_t ld = isY ? dy : dx;
   const int64_t voff = isY ? dx : 0;
   const int64_t c_begin = (int64_t)cidx * chunk;
@@ -219,19 +226,37 @@ __device__ inline void project_tile_ring(const float* __restrict__ X, const floa
   // 16-byte copies when the row pitch and base allow (then a stage's columns are all valid
   // or all past the end together), else 4-byte copies.
   const bool x16 = (ld % 4 == 0) && aligned16(Z);
+  // BF16 rows (the caller checked even rows and 4-byte alignment): 16-byte copies when the rows allow
+  const bool b16 = kB && ld % 8 == 0 && aligned16(Z);
   const bool v16 = (k % 4 == 0) && aligned16(V);
   // staging roles: 16-byte rows xq + 32j, column quad xm (4-byte: rows xr + 8j, column xc);
   // V rows vq + 16j, player quad vm (4-byte: rows vr + 4j, player vi)
   const int xm = tid % 8, xq = tid / 8, xc = tid % kProjCols, xr = tid / kProjCols;
   const int vm = tid % 16, vq = tid / 16, vi = tid % 64, vr = tid / 64;
-  const float* zrow = x16 ? Z + (row0 + xq) * ld + 4 * xm : Z + (row0 + xr) * ld + xc;
+  const T* zrow = x16 ? Z + (row0 + xq) * ld + 4 * xm : Z + (row0 + xr) * ld + xc;
 
   auto issue = [&](int st) {
     if (st < nst) {
       float* xs = Xs + (st % NS) * kXStage;
       float* vs = Vs + (st % NS) * kVStage;
       const int64_t c0 = c_begin + (int64_t)st * kProjCols;
-      if (x16) {
+      if constexpr (kB) {
+        __nv_bfloat16* lb = Lb + (st % NS) * kProjRows * kPLB;
+        if (b16) {  // one 16-byte copy (8 values) per thread: row tid / 4, columns 8 (tid % 4) ..
+          const int r = tid / 4, c = 8 * (tid % 4);
+          const bool v = row0 + r < n && c0 + c < c_end;
+          cp_async16z(reinterpret_cast<float*>(lb + r * kPLB + c),
+                      reinterpret_cast<const float*>(v ? Z + (row0 + r) * ld + c0 + c : Z), v);
+        } else {  // 4-byte copies of value pairs: rows p / 16, columns 2 (p % 16), p = tid + 256 j
+#pragma unroll
+          for (int j = 0; j < kProjRows * kProjCols / (2 * kThreads); ++j) {
+            const int pi = tid + kThreads * j, r = pi / 16, c = 2 * (pi % 16);
+            const bool v = row0 + r < n && c0 + c < c_end;
+            cp_async4(reinterpret_cast<float*>(lb + r * kPLB + c),
+                      reinterpret_cast<const float*>(v ? Z + (row0 + r) * ld + c0 + c : Z), v);
+          }
+        }
+      } else if (x16) {
         const bool cv = c0 + 4 * xm < c_end;
 #pragma unroll
         for (int j = 0; j < kProjRows / 32; ++j) {
@@ -298,7 +323,27 @@ __device__ inline void project_tile_ring(const float* __restrict__ X, const floa
     cp_async_wait_pending<NS - 2>();
     __syncthreads();       // stage st landed for every thread; stage st - 1 is no longer read
     issue(st + NS - 1);    // into the slot of stage st - 1
-    if (cz) {
+    if (kB) {  // widen the landed BF16 row values (and centre them)
+      const uint4 raw = *reinterpret_cast<const uint4*>(Lb + (st % NS) * kProjRows * kPLB + cr * kPLB + cc8);
+      const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&raw);
+      float xv[8];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float2 f = __bfloat1622float2(h2[u]);
+        xv[2 * u] = f.x;
+        xv[2 * u + 1] = f.y;
+      }
+      if (crow) {
+        const int64_t c0 = c_begin + (int64_t)st * kProjCols + cc8;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (c0 + u < c_end) xv[u] -= mrow[c0 + u];
+      }
+      float* xs = Xs + (st % NS) * kXStage + cr * kPRXS + cc8;
+      *reinterpret_cast<float4*>(xs) = make_float4(xv[0], xv[1], xv[2], xv[3]);
+      *reinterpret_cast<float4*>(xs + 4) = make_float4(xv[4], xv[5], xv[6], xv[7]);
+      __syncthreads();
+    } else if (cz) {
       if (crow) {
         float* xs = Xs + (st % NS) * kXStage + cr * kPRXS + cc8;
         const int64_t c0 = c_begin + (int64_t)st * kProjCols + cc8;
@@ -335,21 +380,24 @@ __device__ inline void project_tile_ring(const float* __restrict__ X, const floa
 // backproject_tile): stage st holds rows [r0, r0 + 32) of the 64-column block and their
 // P / Q weights, masked per estimate by zero-filled copies. With `cz`, each landed stage is
 // centred in shared memory (a thread: one row, 8 columns) before it is read.
-__device__ inline void backproject_tile_ring(const float* __restrict__ X, const float* __restrict__ Y, int64_t b,
-                                             int64_t dx, int64_t dy, int64_t nA, int kind, int split,
+template <typename T>
+__device__ inline void backproject_tile_ring(const T* __restrict__ X, const T* __restrict__ Y, int64_t b, int64_t dx,
+                                             int64_t dy, int64_t nA, int kind, int split,
                                              const float* __restrict__ PQ, int k, int nblk_x,
                                              int64_t rows_per_split, float inv_nA, float inv_nB,
                                              float* __restrict__ AV, float* __restrict__ BV, int bx, int by,
                                              float* smem, const Centring* cz = nullptr) {
+  constexpr bool kB = !std::is_same<T, float>::value;  // BF16 rows: landed, then widened in shared memory
   constexpr int NS = kBpRing;
   constexpr int kZStage = kBpRows * kBpZS, kWStage = kBpRows * kWS;
   float* Zs = smem;                      // [NS][kBpRows][kBpZS]
   float* WA = smem + NS * kZStage;       // [NS][kBpRows][kWS]
   float* WB = WA + NS * kWStage;         // [NS][kBpRows][kWS]
+  __nv_bfloat16* Lb = reinterpret_cast<__nv_bfloat16*>(WB + NS * kWStage);  // [NS][kBpRows][kBLB]
   const int tid = threadIdx.x;
   const bool isY = bx >= nblk_x;
   const int bidx = isY ? bx - nblk_x : bx;
-  const float* Z = isY ? Y : X;
+  const T* Z = isY ? Y : X;
   const int64_t ld = isY ? dy : dx;
   const int64_t col0 = (int64_t)bidx * kBpCols;
   const int64_t r_begin = (int64_t)by * rows_per_split;
@@ -371,12 +419,14 @@ __device__ inline void backproject_tile_ring(const float* __restrict__ X, const 
   const int cq = o % 16, pq = o / 16;
   // 16-byte copies when the row pitch and bases allow, else 4-byte copies
   const bool z16 = (ld % 4 == 0) && aligned16(Z);
+  // BF16 rows (the caller checked even rows and 4-byte alignment): 16-byte copies when the rows allow
+  const bool b16 = kB && ld % 8 == 0 && aligned16(Z);
   const bool w16 = (k % 4 == 0) && aligned16(PQ);
   // staging roles: 16-byte rows sq + 16j at column (or player) quad sm; 4-byte rows sr + 4j
   // at column (or player) sc
   const int sm = tid % 16, sq = tid / 16, sc = tid % 64, sr = tid / 64;
   const bool ccol = z16 ? col0 + 4 * sm < ld : col0 + sc < ld;
-  const float* zcol = z16 ? Z + col0 + 4 * sm : Z + col0 + sc;
+  const T* zcol = z16 ? Z + col0 + 4 * sm : Z + col0 + sc;
 
   auto issue = [&](int st) {
     if (st < nst) {
@@ -384,7 +434,23 @@ __device__ inline void backproject_tile_ring(const float* __restrict__ X, const 
       float* zs = Zs + (st % NS) * kZStage;
       float* wa = WA + (st % NS) * kWStage;
       float* wb = WB + (st % NS) * kWStage;
-      if (z16) {
+      if constexpr (kB) {
+        __nv_bfloat16* lb = Lb + (st % NS) * kBpRows * kBLB;
+        if (b16) {  // one 16-byte copy (8 values) per thread: row tid / 8, columns 8 (tid % 8) ..
+          const int r = tid / 8, c = 8 * (tid % 8);
+          const bool v = r0 + r < r_end && col0 + c < ld;
+          cp_async16z(reinterpret_cast<float*>(lb + r * kBLB + c),
+                      reinterpret_cast<const float*>(v ? Z + (r0 + r) * ld + col0 + c : Z), v);
+        } else {  // 4-byte copies of value pairs: rows p / 32, columns 2 (p % 32), p = tid + 256 j
+#pragma unroll
+          for (int j = 0; j < kBpRows * kBpCols / (2 * kThreads); ++j) {
+            const int pi = tid + kThreads * j, r = pi / 32, c = 2 * (pi % 32);
+            const bool v = r0 + r < r_end && col0 + c < ld;
+            cp_async4(reinterpret_cast<float*>(lb + r * kBLB + c),
+                      reinterpret_cast<const float*>(v ? Z + (r0 + r) * ld + col0 + c : Z), v);
+          }
+        }
+      } else if (z16) {
 #pragma unroll
         for (int j = 0; j < kBpRows / 16; ++j) {
           const int64_t row = r0 + sq + 16 * j;
@@ -450,26 +516,43 @@ __device__ inline void backproject_tile_ring(const float* __restrict__ X, const 
     issue(st + NS - 1);
     const int64_t r0 = r_begin + (int64_t)st * kBpRows;
     const int nr = (int)min((int64_t)kBpRows, r_end - r0);
-    if (cz) {
+    if (kB || cz) {
       const int64_t row = r0 + cr;
-      if (row < r_end) {
-        const float* mrow = isY ? cz->mean_y : cz->mean;
-        bool ok = true;
+      const float* mrow = nullptr;
+      if (cz && row < r_end) {
+        mrow = isY ? cz->mean_y : cz->mean;
         if (cz->labels) {
           const int lab = cz->labels[row];
           if ((unsigned)lab >= (unsigned)cz->C) {  // flagged; the row stays uncentred
             atomicOr(cz->dflag, kFlagBadLabel);
-            ok = false;
+            mrow = nullptr;
           } else {
             mrow = cz->mean + (int64_t)lab * ld;
           }
         }
-        if (ok) {
-          float* zs = Zs + (st % NS) * kZStage + cr * kBpZS + cc8;
+      }
+      float* zs = Zs + (st % NS) * kZStage + cr * kBpZS + cc8;
+      if (kB) {  // widen the landed BF16 row values (and centre them)
+        const uint4 raw = *reinterpret_cast<const uint4*>(Lb + (st % NS) * kBpRows * kBLB + cr * kBLB + cc8);
+        const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&raw);
+        float zv[8];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float2 f = __bfloat1622float2(h2[u]);
+          zv[2 * u] = f.x;
+          zv[2 * u + 1] = f.y;
+        }
+        if (mrow) {
 #pragma unroll
           for (int u = 0; u < 8; ++u)
-            if (col0 + cc8 + u < ld) zs[u] -= mrow[col0 + cc8 + u];
+            if (col0 + cc8 + u < ld) zv[u] -= mrow[col0 + cc8 + u];
         }
+        *reinterpret_cast<float4*>(zs) = make_float4(zv[0], zv[1], zv[2], zv[3]);
+        *reinterpret_cast<float4*>(zs + 4) = make_float4(zv[4], zv[5], zv[6], zv[7]);
+      } else if (mrow) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (col0 + cc8 + u < ld) zs[u] -= mrow[col0 + cc8 + u];
       }
       __syncthreads();
     }
@@ -517,7 +600,16 @@ __device__ void project_tile(const T* __restrict__ X, const T* __restrict__ Y, i
   static_assert(kProjRows == 64 && kProjRows * kProjCols % (4 * kThreads) == 0, "projection staging");
   if constexpr (std::is_same<T, float>::value) {
     if (!rsx && !rsy) {  // FP32 rows without a row scale: the cp.async ring (centred in shared memory)
-      project_tile_ring(X, Y, n, dx, dy, V, k, chunk, nchunk_x, PQ, bx, by, smem, cz.mean ? &cz : nullptr);
+      project_tile_ring<float>(X, Y, n, dx, dy, V, k, chunk, nchunk_x, PQ, bx, by, smem, cz.mean ? &cz : nullptr);
+      return;
+    }
+  } else if constexpr (std::is_same<T, __nv_bfloat16>::value) {
+    // BF16 rows through the ring when their value pairs are 4-byte aligned (even rows)
+    const bool isY = by >= nchunk_x;
+    const T* Z = isY ? Y : X;
+    const int64_t ld = isY ? dy : dx;
+    if (!rsx && !rsy && ld % 2 == 0 && chunk % 8 == 0 && ((uintptr_t)Z & 3) == 0) {
+      project_tile_ring<T>(X, Y, n, dx, dy, V, k, chunk, nchunk_x, PQ, bx, by, smem, cz.mean ? &cz : nullptr);
       return;
     }
   }
@@ -631,8 +723,18 @@ __device__ void backproject_tile(const T* __restrict__ X, const T* __restrict__ 
   static_assert(kBpCols == 64 && kBpRows * kBpCols % kThreads == 0, "back-projection staging");
   if constexpr (std::is_same<T, float>::value) {
     if (!rsx && !rsy) {  // FP32 rows without a row scale: the cp.async ring (centred in shared memory)
-      backproject_tile_ring(X, Y, b, dx, dy, nA, kind, split, PQ, k, nblk_x, rows_per_split, inv_nA, inv_nB, AV, BV,
-                            bx, by, smem, cz.mean ? &cz : nullptr);
+      backproject_tile_ring<float>(X, Y, b, dx, dy, nA, kind, split, PQ, k, nblk_x, rows_per_split, inv_nA, inv_nB,
+                                   AV, BV, bx, by, smem, cz.mean ? &cz : nullptr);
+      return;
+    }
+  } else if constexpr (std::is_same<T, __nv_bfloat16>::value) {
+    // BF16 rows through the ring when their value pairs are 4-byte aligned (even rows)
+    const bool isY = bx >= nblk_x;
+    const T* Z = isY ? Y : X;
+    const int64_t ld = isY ? dy : dx;
+    if (!rsx && !rsy && ld % 2 == 0 && ((uintptr_t)Z & 3) == 0) {
+      backproject_tile_ring<T>(X, Y, b, dx, dy, nA, kind, split, PQ, k, nblk_x, rows_per_split, inv_nA, inv_nB, AV,
+                               BV, bx, by, smem, cz.mean ? &cz : nullptr);
       return;
     }
   }
