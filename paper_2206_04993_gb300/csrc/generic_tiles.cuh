@@ -54,7 +54,7 @@ constexpr int kPRXS = kProjCols + kPad;
 // BF16 rows land in their own buffer of each stage (row stride an odd number of 16-byte
 // chunks) and are widened to FP32 into the stage, centred if they are, before it is read.
 constexpr int kPLB = kProjCols + 8;  // BF16 landing row stride of the projection ring
-constexpr int kBLB = kBpCols + 8;    // ... and of the back-projection ring
+constexpr int kBLB = kBpCols + 16;   // ... and of the back-projection ring (also 256 x 5 value pairs)
 constexpr int kProjRingSmem = kProjRing * (kProjRows * kPRXS + kProjCols * kWS + kProjRows * kPLB / 2);
 constexpr int kBpRingSmem = kBpRing * (kBpRows * kBpZS + 2 * kBpRows * kWS + kBpRows * kBLB / 2);
 
@@ -195,6 +195,34 @@ __device__ __forceinline__ void reduce_quads(const float (&acc)[4][4], bool acti
 // [c0, c0 + 32); a thread owns rows rq + 16a (a < 4) and one player quad, and per column quad
 // reads 4 float4 of rows and 4 float4 of V for 64 FMAs. With `cz`, each landed stage is centred
 // in shared memory (a thread: one row, 8 columns) before it is read.
+// The 8 BF16 values at element a, a + 1, .. of a matrix of `total` values, widened, from the
+// five aligned value pairs staged from element a & ~1 on. Values whose column is past `ncols`
+// (columns left in the row from a), or of a row that is not valid, are zero; a pair that
+// reached past the matrix's last value was not staged and is read directly.
+__device__ __forceinline__ void widen_pairs(const uint32_t* slot, const __nv_bfloat16* Z, int64_t a, int64_t total,
+                                            bool row_ok, int64_t ncols, float (&out)[8]) {
+  const int64_t p0 = a & ~(int64_t)1;
+  const int sh = (int)(a - p0);
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int e = u + sh;  // position in the staged pairs
+    float v = 0.f;
+    if (row_ok && u < ncols) {
+      if (p0 + 2 * (e >> 1) + 1 < total) {
+        const uint32_t w = slot[e >> 1];
+        v = __uint_as_float((e & 1) ? (w & 0xffff0000u) : (w << 16));
+      } else {
+        v = __bfloat162float(Z[a + u]);
+      }
+    }
+    out[u] = v;
+  }
+}
+__device__ __forceinline__ void widen_pairs(const uint32_t*, const float*, int64_t, int64_t, bool, int64_t,
+                                            float (&out)[8]) {
+  for (int u = 0; u < 8; ++u) out[u] = 0.f;
+}
+
 template <typename T>
 __device__ inline void project_tile_ring(const T* __restrict__ X, const T* __restrict__ Y, int64_t n, int64_t dx,
                                          int64_t dy, const float* __restrict__ V, int k, int64_t chunk,
@@ -226,7 +254,7 @@ __device__ inline void project_tile_ring(const T* __restrict__ X, const T* __res
   // 16-byte copies when the row pitch and base allow (then a stage's columns are all valid
   // or all past the end together), else 4-byte copies.
   const bool x16 = (ld % 4 == 0) && aligned16(Z);
-  // BF16 rows (the caller checked even rows and 4-byte alignment): 16-byte copies when the rows allow
+  // BF16 rows (the caller checked 4-byte alignment): 16-byte copies when the rows allow
   const bool b16 = kB && ld % 8 == 0 && aligned16(Z);
   const bool v16 = (k % 4 == 0) && aligned16(V);
   // staging roles: 16-byte rows xq + 32j, column quad xm (4-byte: rows xr + 8j, column xc);
@@ -247,13 +275,15 @@ __device__ inline void project_tile_ring(const T* __restrict__ X, const T* __res
           const bool v = row0 + r < n && c0 + c < c_end;
           cp_async16z(reinterpret_cast<float*>(lb + r * kPLB + c),
                       reinterpret_cast<const float*>(v ? Z + (row0 + r) * ld + c0 + c : Z), v);
-        } else {  // 4-byte copies of value pairs: rows p / 16, columns 2 (p % 16), p = tid + 256 j
+        } else {  // the five aligned value pairs holding this thread's 8 values (row tid / 4)
+          const int r = tid / 4, c = 8 * (tid % 4);
+          const int64_t a = (row0 + r) * ld + c0 + c, p0 = a & ~(int64_t)1;
+          const bool v = row0 + r < n && c0 + c < c_end;
+          uint32_t* slot = reinterpret_cast<uint32_t*>(lb) + 5 * tid;
 #pragma unroll
-          for (int j = 0; j < kProjRows * kProjCols / (2 * kThreads); ++j) {
-            const int pi = tid + kThreads * j, r = pi / 16, c = 2 * (pi % 16);
-            const bool v = row0 + r < n && c0 + c < c_end;
-            cp_async4(reinterpret_cast<float*>(lb + r * kPLB + c),
-                      reinterpret_cast<const float*>(v ? Z + (row0 + r) * ld + c0 + c : Z), v);
+          for (int j = 0; j < 5; ++j) {
+            const bool ok = v && p0 + 2 * j + 1 < n * ld;
+            cp_async4(reinterpret_cast<float*>(slot + j), reinterpret_cast<const float*>(ok ? Z + p0 + 2 * j : Z), ok);
           }
         }
       } else if (x16) {
@@ -324,14 +354,20 @@ __device__ inline void project_tile_ring(const T* __restrict__ X, const T* __res
     __syncthreads();       // stage st landed for every thread; stage st - 1 is no longer read
     issue(st + NS - 1);    // into the slot of stage st - 1
     if (kB) {  // widen the landed BF16 row values (and centre them)
-      const uint4 raw = *reinterpret_cast<const uint4*>(Lb + (st % NS) * kProjRows * kPLB + cr * kPLB + cc8);
-      const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&raw);
       float xv[8];
+      if (b16) {
+        const uint4 raw = *reinterpret_cast<const uint4*>(Lb + (st % NS) * kProjRows * kPLB + cr * kPLB + cc8);
+        const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&raw);
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const float2 f = __bfloat1622float2(h2[u]);
-        xv[2 * u] = f.x;
-        xv[2 * u + 1] = f.y;
+        for (int u = 0; u < 4; ++u) {
+          const float2 f = __bfloat1622float2(h2[u]);
+          xv[2 * u] = f.x;
+          xv[2 * u + 1] = f.y;
+        }
+      } else {
+        widen_pairs(reinterpret_cast<const uint32_t*>(Lb + (st % NS) * kProjRows * kPLB) + 5 * tid, Z,
+                    (row0 + cr) * ld + c_begin + (int64_t)st * kProjCols + cc8, n * ld, row0 + cr < n,
+                    c_end - (c_begin + (int64_t)st * kProjCols + cc8), xv);
       }
       if (crow) {
         const int64_t c0 = c_begin + (int64_t)st * kProjCols + cc8;
@@ -419,7 +455,7 @@ __device__ inline void backproject_tile_ring(const T* __restrict__ X, const T* _
   const int cq = o % 16, pq = o / 16;
   // 16-byte copies when the row pitch and bases allow, else 4-byte copies
   const bool z16 = (ld % 4 == 0) && aligned16(Z);
-  // BF16 rows (the caller checked even rows and 4-byte alignment): 16-byte copies when the rows allow
+  // BF16 rows (the caller checked 4-byte alignment): 16-byte copies when the rows allow
   const bool b16 = kB && ld % 8 == 0 && aligned16(Z);
   const bool w16 = (k % 4 == 0) && aligned16(PQ);
   // staging roles: 16-byte rows sq + 16j at column (or player) quad sm; 4-byte rows sr + 4j
@@ -441,13 +477,15 @@ __device__ inline void backproject_tile_ring(const T* __restrict__ X, const T* _
           const bool v = r0 + r < r_end && col0 + c < ld;
           cp_async16z(reinterpret_cast<float*>(lb + r * kBLB + c),
                       reinterpret_cast<const float*>(v ? Z + (r0 + r) * ld + col0 + c : Z), v);
-        } else {  // 4-byte copies of value pairs: rows p / 32, columns 2 (p % 32), p = tid + 256 j
+        } else {  // the five aligned value pairs holding this thread's 8 values (row tid / 8)
+          const int r = tid / 8, c = 8 * (tid % 8);
+          const int64_t a = (r0 + r) * ld + col0 + c, p0 = a & ~(int64_t)1;
+          const bool v = r0 + r < r_end && col0 + c < ld;
+          uint32_t* slot = reinterpret_cast<uint32_t*>(lb) + 5 * tid;
 #pragma unroll
-          for (int j = 0; j < kBpRows * kBpCols / (2 * kThreads); ++j) {
-            const int pi = tid + kThreads * j, r = pi / 32, c = 2 * (pi % 32);
-            const bool v = r0 + r < r_end && col0 + c < ld;
-            cp_async4(reinterpret_cast<float*>(lb + r * kBLB + c),
-                      reinterpret_cast<const float*>(v ? Z + (r0 + r) * ld + col0 + c : Z), v);
+          for (int j = 0; j < 5; ++j) {
+            const bool ok = v && p0 + 2 * j + 1 < b * ld;
+            cp_async4(reinterpret_cast<float*>(slot + j), reinterpret_cast<const float*>(ok ? Z + p0 + 2 * j : Z), ok);
           }
         }
       } else if (z16) {
@@ -533,14 +571,19 @@ __device__ inline void backproject_tile_ring(const T* __restrict__ X, const T* _
       }
       float* zs = Zs + (st % NS) * kZStage + cr * kBpZS + cc8;
       if (kB) {  // widen the landed BF16 row values (and centre them)
-        const uint4 raw = *reinterpret_cast<const uint4*>(Lb + (st % NS) * kBpRows * kBLB + cr * kBLB + cc8);
-        const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&raw);
         float zv[8];
+        if (b16) {
+          const uint4 raw = *reinterpret_cast<const uint4*>(Lb + (st % NS) * kBpRows * kBLB + cr * kBLB + cc8);
+          const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&raw);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const float2 f = __bfloat1622float2(h2[u]);
-          zv[2 * u] = f.x;
-          zv[2 * u + 1] = f.y;
+          for (int u = 0; u < 4; ++u) {
+            const float2 f = __bfloat1622float2(h2[u]);
+            zv[2 * u] = f.x;
+            zv[2 * u + 1] = f.y;
+          }
+        } else {
+          widen_pairs(reinterpret_cast<const uint32_t*>(Lb + (st % NS) * kBpRows * kBLB) + 5 * tid, Z,
+                      row * ld + col0 + cc8, b * ld, row < r_end, ld - (col0 + cc8), zv);
         }
         if (mrow) {
 #pragma unroll
@@ -604,11 +647,11 @@ __device__ void project_tile(const T* __restrict__ X, const T* __restrict__ Y, i
       return;
     }
   } else if constexpr (std::is_same<T, __nv_bfloat16>::value) {
-    // BF16 rows through the ring when their value pairs are 4-byte aligned (even rows)
+    // BF16 rows through the ring (16-byte copies, or the aligned value pairs holding a thread's values)
     const bool isY = by >= nchunk_x;
     const T* Z = isY ? Y : X;
     const int64_t ld = isY ? dy : dx;
-    if (!rsx && !rsy && ld % 2 == 0 && chunk % 8 == 0 && ((uintptr_t)Z & 3) == 0) {
+    if (!rsx && !rsy && chunk % 8 == 0 && ((uintptr_t)Z & 3) == 0) {
       project_tile_ring<T>(X, Y, n, dx, dy, V, k, chunk, nchunk_x, PQ, bx, by, smem, cz.mean ? &cz : nullptr);
       return;
     }
@@ -728,11 +771,11 @@ __device__ void backproject_tile(const T* __restrict__ X, const T* __restrict__ 
       return;
     }
   } else if constexpr (std::is_same<T, __nv_bfloat16>::value) {
-    // BF16 rows through the ring when their value pairs are 4-byte aligned (even rows)
+    // BF16 rows through the ring (16-byte copies, or the aligned value pairs holding a thread's values)
     const bool isY = bx >= nblk_x;
     const T* Z = isY ? Y : X;
     const int64_t ld = isY ? dy : dx;
-    if (!rsx && !rsy && ld % 2 == 0 && ((uintptr_t)Z & 3) == 0) {
+    if (!rsx && !rsy && ((uintptr_t)Z & 3) == 0) {
       backproject_tile_ring<T>(X, Y, b, dx, dy, nA, kind, split, PQ, k, nblk_x, rows_per_split, inv_nA, inv_nB, AV,
                                BV, bx, by, smem, cz.mean ? &cz : nullptr);
       return;
@@ -1105,6 +1148,53 @@ __device__ void lda_stats_tile(const T* __restrict__ X, const float* __restrict_
     labs[tid] = (unsigned)lab < (unsigned)C ? lab : -1;  // bad labels are flagged by the counts tile
     __syncthreads();
     const int nr = (int)min((int64_t)kThreads, b - r0);
+    if constexpr (std::is_same<T, __nv_bfloat16>::value) {
+      if (!rs && ((uintptr_t)X & 3) == 0) {
+        // BF16 rows: each thread stages, by 4-byte cp.async (double-buffered, blocks of kStatsRows
+        // rows), the aligned value pair that holds its column's value and keeps its half (no
+        // barrier: a thread reads only what it copied). A pair that would reach past the
+        // matrix's last value is read directly instead.
+        const int64_t total = b * d;
+        auto issue = [&](int s0, int buf) {
+#pragma unroll
+          for (int q = 0; q < kStatsRows; ++q) {
+            const int64_t a = (r0 + s0 + q) * d + col;
+            const bool ok = col < d && s0 + q < nr && (a | 1) < total;
+            cp_async4(xs + (buf * kStatsRows + q) * kThreads + tid,
+                      reinterpret_cast<const float*>(ok ? X + (a & ~(int64_t)1) : X), ok);
+          }
+          cp_async_commit_all();
+        };
+        if (col >= d) continue;
+        issue(0, 0);
+        int buf = 0;
+        for (int s0 = 0; s0 < nr; s0 += kStatsRows, buf ^= 1) {
+          if (s0 + kStatsRows < nr) {
+            issue(s0 + kStatsRows, buf ^ 1);
+            cp_async_wait_pending<1>();
+          } else {
+            cp_async_wait_all();
+          }
+#pragma unroll
+          for (int q = 0; q < kStatsRows; ++q) {
+            const int lab2 = (s0 + q < nr) ? labs[s0 + q] : -1;
+            if (lab2 >= 0) {
+              const int64_t a = (r0 + s0 + q) * d + col;
+              float v;
+              if ((a | 1) < total) {
+                const __nv_bfloat162 pr =
+                    *reinterpret_cast<const __nv_bfloat162*>(xs + (buf * kStatsRows + q) * kThreads + tid);
+                v = (a & 1) ? __high2float(pr) : __low2float(pr);
+              } else {
+                v = __bfloat162float(X[a]);
+              }
+              acc[lab2 * kThreads + tid] += v;
+            }
+          }
+        }
+        continue;
+      }
+    }
     if (col >= d) continue;
     if constexpr (std::is_same<T, float>::value) {
       if (!rs) {

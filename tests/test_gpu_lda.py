@@ -70,8 +70,11 @@ def test_lda_unsplit_batch():
             assert v <= STEP_TOL, (name, v, e)
 
 
-def test_lda_bf16_rows():
-    for e in _run_steps(512, 8, 10, 256, 3, dtype="bf16", seed=5):
+@pytest.mark.parametrize("d", [512, 301, 250], ids=["d512", "d301_odd", "d250_even"])
+def test_lda_bf16_rows(d):
+    """BF16 rows: 16-byte staging (d a multiple of 8), or the aligned value pairs holding each
+    thread's values (odd d, and even d that is not a multiple of 8)."""
+    for e in _run_steps(d, 8, 10, 256, 3, dtype="bf16", seed=5):
         for name, v in e.items():
             assert v <= STEP_TOL, (name, v, e)
 

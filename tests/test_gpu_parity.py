@@ -111,6 +111,18 @@ def test_single_step_bf16_aligned_shapes(path, dx, dy, k, b):
     assert_within(err, STEP_TOL)
 
 
+@pytest.mark.parametrize("dx,dy,k,b", [(37, 29, 3, 101), (70, 130, 17, 333), (515, 301, 16, 640)])
+def test_single_step_bf16_unaligned_rows(dx, dy, k, b):
+    """BF16 rows whose length is odd or not a multiple of 8, on the generic path: each thread
+    stages the aligned value pairs holding its values; the last pair of the matrix is read
+    directly."""
+    X, Y = _data("cca", dx, dy, b, seed=dx + dy)
+    V0, S0 = _state(dx + dy, k, seed=6, kind="cca")
+    with _solver("cca", dx, dy, k, S.SGEP_PATH_GENERIC, dtype="bf16", eta0=0.3, gamma0=0.5, rho=1e-4) as s:
+        err = step_errors(s, V0, S0, X, Y, "cca", 0.3, 0.5, 1e-4, dtype="bf16")
+    assert_within(err, STEP_TOL)
+
+
 @pytest.mark.parametrize("path", PATHS, ids=["generic", "cluster"])
 def test_single_step_bf16_inputs(path):
     """BF16 minibatch values (the GPU reads bf16, the oracle the same values in FP64);
