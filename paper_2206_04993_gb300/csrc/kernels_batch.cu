@@ -56,6 +56,7 @@ struct BatchHeader {
   int n;
   int total[kPhases];
   unsigned long long bar_base;  // barrier arrivals before this launch
+  unsigned long long work_base[kPhases];  // persistent mode: items claimed per phase before this launch
 };
 
 namespace {
@@ -168,14 +169,33 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch_phase(const BatchHeader* 
   run_phase(h, inst, phase, smem);
 }
 
+// Persistent mode: the blocks claim a phase's items one at a time from a counter (monotone
+// across launches; each block ends a phase with one claim past the last item), so items of
+// uneven cost spread over the blocks as they finish.
+__device__ void run_phase_claimed(const BatchHeader* h, const InstDesc* inst, int phase, float* smem,
+                                  unsigned long long* work, int* it_s) {
+  const int total = h->total[phase];
+  const unsigned long long base = h->work_base[phase];
+  for (;;) {
+    if (threadIdx.x == 0) *it_s = (int)min(atomicAdd(work + phase, 1ull) - base, (unsigned long long)total);
+    __syncthreads();
+    const int it = *it_s;
+    if (it >= total) break;
+    const int i = find_instance(inst, h->n, phase, it);
+    run_item(inst[i], phase, it - inst[i].off[phase], smem);
+    __syncthreads();  // the workspace and the claimed index are reused by the next item
+  }
+}
+
 __global__ void __launch_bounds__(kThreads, 2) k_batch_persistent(const BatchHeader* __restrict__ h,
                                                                const InstDesc* __restrict__ inst,
                                                                unsigned long long* bar, int* dflag) {
   extern __shared__ __align__(16) float smem[];
   __shared__ int ok_s;
+  __shared__ int it_s;
   const unsigned long long base = h->bar_base;
   for (int phase = 0; phase < kPhases; ++phase) {
-    run_phase(h, inst, phase, smem);
+    run_phase_claimed(h, inst, phase, smem, bar + 1, &it_s);
     if (phase + 1 == kPhases) break;
     // bounded grid barrier: arrivals are counted monotonically across launches
     __syncthreads();
@@ -213,8 +233,9 @@ struct BatchCtx {
   size_t tab_bytes = 0;
   cudaEvent_t done[2] = {nullptr, nullptr};
   int cur = 0;
-  unsigned long long* bar = nullptr;
+  unsigned long long* bar = nullptr;  // [1 + kPhases]: grid-barrier arrivals, then the phases' claims
   unsigned long long bar_base = 0;
+  unsigned long long work_base[kPhases] = {};
   int* dflag = nullptr;  // batch-level flag (barrier timeouts)
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int graph_key[2] = {-1, -1};  // launch-shape key the graph was captured for
@@ -259,12 +280,12 @@ int batch_create(Ctx** hs, int n, BatchCtx** out) {
       return SGEP_ENOMEM;
     }
   }
-  if (cudaMalloc((void**)&B->bar, sizeof(unsigned long long)) != cudaSuccess ||
+  if (cudaMalloc((void**)&B->bar, (1 + kPhases) * sizeof(unsigned long long)) != cudaSuccess ||
       cudaMalloc((void**)&B->dflag, sizeof(int)) != cudaSuccess) {
     batch_free(B);
     return SGEP_ENOMEM;
   }
-  cudaMemset(B->bar, 0, sizeof(unsigned long long));
+  cudaMemset(B->bar, 0, (1 + kPhases) * sizeof(unsigned long long));
   cudaMemset(B->dflag, 0, sizeof(int));
   const size_t smem = (size_t)kSmemFloats * sizeof(float);
   cudaFuncSetAttribute(k_batch_phase, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -371,6 +392,7 @@ static int fill_table(BatchCtx& B, char* tab, const void* const* X, const void* 
     }
   }
   hd->bar_base = B.bar_base;
+  for (int p = 0; p < kPhases; ++p) hd->work_base[p] = B.work_base[p];
   int key = B.tune.mode * 7919 + B.tune.blocks_per_sm;
   for (int p = 0; p < kPhases; ++p) key = key * 31 + hd->total[p];
   return key;
@@ -446,7 +468,12 @@ int batch_step(BatchCtx& B, const void* const* X, const void* const* Y, const fl
     if (rc) return rc;
   }
   SGEP_CUDA_TRY(cudaEventRecord(B.done[j], s));
-  if (B.tune.mode == 0) B.bar_base += (unsigned long long)(kPhases - 1) * B.tune.blocks_per_sm * B.num_sms;
+  if (B.tune.mode == 0) {
+    const unsigned long long grid = (unsigned long long)B.tune.blocks_per_sm * B.num_sms;
+    B.bar_base += (unsigned long long)(kPhases - 1) * grid;
+    const auto* hd = reinterpret_cast<const BatchHeader*>(B.host_tab[j]);
+    for (int p = 0; p < kPhases; ++p) B.work_base[p] += (unsigned long long)hd->total[p] + grid;
+  }
   for (auto* c : B.h) {
     c->t += 1;
     c->debug_valid = c->cfg.debug;
@@ -460,8 +487,10 @@ int batch_sync(BatchCtx& B, cudaStream_t s) {
   SGEP_CUDA_TRY(cudaMemcpy(&flag, B.dflag, sizeof(int), cudaMemcpyDeviceToHost));
   if (flag) {
     SGEP_CUDA_TRY(cudaMemset(B.dflag, 0, sizeof(int)));
-    SGEP_CUDA_TRY(cudaMemset(B.bar, 0, sizeof(unsigned long long)));  // the count may be short
+    // the counts may be short
+    SGEP_CUDA_TRY(cudaMemset(B.bar, 0, (1 + kPhases) * sizeof(unsigned long long)));
     B.bar_base = 0;
+    for (auto& w : B.work_base) w = 0;
     return SGEP_ETIMEOUT;
   }
   return SGEP_OK;
