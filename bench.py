@@ -681,6 +681,109 @@ def measure_warm(dev, seed=0, n_train=128, n_eval=16, max_steps=8000, check_ever
     return out
 
 
+def measure_batch_tte(dev, seed=0, n=16, b=512, nmb=32, max_steps=60_000, every=1000, target=1e-3):
+    """Time to 1e-3 of the batching form against the same instances stepped alone. Instances: the
+    CCA half of the batching workload's generator (planted CCA, 16 latent directions with
+    correlations 0.9..0.3, noise 0.5) restricted to d_x = d_y <= 512 and k <= 12, so that the exact
+    FP64 solution of every instance's resident pool (nmb minibatches of b rows) is cheap. Every
+    start runs the same harmonic schedule on the same pool sequence (odd epochs shift the
+    minibatch grid by b / 2 so that every row estimates A and B equally often). Device time of
+    the steps only; the errors are evaluated every `every` steps outside it."""
+    import torch
+    from paper_2206_04993_gb300 import Batch, Solver, sgep
+    rng = np.random.default_rng(seed + 41)
+    insts = []
+    for i in range(n):
+        dx = int(rng.integers(32, 513))
+        k = int(rng.integers(4, 13))
+        insts.append((dx, k, synth.planted_cca(dx, dx, np.linspace(0.9, 0.3, 16), sigma=0.5, seed=9000 + i)))
+    pools, truths = [], []
+    for i, (dx, k, m) in enumerate(insts):
+        X, Y = make_pool({"model": m}, nmb * b, "f32", dev, seed=7000 + i)
+        truths.append(pool_truth(X, Y, k))
+        pools.append((torch.cat([X, X[:b // 2]]).contiguous(), torch.cat([Y, Y[:b // 2]]).contiguous()))
+    sched = dict(eta0=0.2, gamma0=0.3, rho=1e-6, schedule=sgep.SGEP_SCHED_HOLD_HARMONIC, t_c=1, T=20_000,
+                 eta_T=0.2 * 401.0 / 20_400.0)
+
+    def offset(t):  # first row of step t's minibatch in the pool
+        return (t // nmb) % 2 * (b // 2) + (t % nmb) * b
+
+    def mk(i, path):
+        dx, k, _ = insts[i]
+        s_ = Solver(kind=sgep.SGEP_CCA, d_x=dx, d_y=dx, k=k, max_b=b, path=path, seed=100 + i, **sched)
+        s_.set_V(synth.random_unit_columns(2 * dx, k, seed=300 + i).astype(np.float32))
+        return s_
+
+    def err(i, s_):
+        Vs, B, _ = truths[i]
+        return gen_subspace_error(Vs, s_.V().astype(np.float64), B)
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"instances": n, "b": b, "pool_rows": nmb * b, "target": target,
+           "config": "CCA, d_x = d_y uniform in 32..512, k uniform in 4..12, 16 planted directions (0.9..0.3)",
+           "truth": "scipy eigh of each pool's FP64 covariances"}
+    # the batch: every instance advances by one step per batched step until all reach the target
+    ss = [mk(i, sgep.SGEP_PATH_GENERIC) for i in range(n)]
+    reached = [None] * n
+    ms, t = 0.0, 0
+    with Batch(ss) as bt:
+        bt.configure(use_graph=1)
+        while t < max_steps and any(r is None for r in reached):
+            e0.record()
+            for u in range(t, t + every):
+                o = offset(u)
+                bt.step([X[o:o + b] for X, _ in pools], [Y[o:o + b] for _, Y in pools], [b] * n)
+            e1.record()
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            t += every
+            for i in range(n):
+                if reached[i] is None and err(i, ss[i]) <= target:
+                    reached[i] = t
+        bt.sync()
+    final = [round(err(i, ss[i]), 6) for i in range(n)]
+    for s_ in ss:
+        s_.close()
+    out["batched"] = {"reached": sum(r is not None for r in reached), "steps_to_all": t,
+                      "device_seconds_to_all": ms / 1e3, "ms_per_batched_step": ms / t,
+                      "steps_per_instance": reached, "final_error_per_instance": final,
+                      "d_x_per_instance": [it[0] for it in insts], "k_per_instance": [it[1] for it in insts]}
+    # one instance at a time, the same steps: generic handles (as in the batch), and the path the
+    # library picks for a lone instance (the cluster path, several steps per launch)
+    for name, path in (("alone_generic", sgep.SGEP_PATH_GENERIC), ("alone_auto", sgep.SGEP_PATH_AUTO)):
+        total_ms, steps, paths = 0.0, [], set()
+        for i in range(n):
+            s_ = mk(i, path)
+            paths.add(s_.path)
+            X, Y = pools[i]
+            tt, ms_i, hit = 0, 0.0, None
+            while tt < max_steps:
+                e0.record()
+                u = tt
+                while u < tt + every:  # runs of consecutive minibatches within an epoch
+                    m = min(tt + every - u, nmb - u % nmb)
+                    o = offset(u)
+                    s_.step_many(X[o:o + m * b], Y[o:o + m * b], b, m)
+                    u += m
+                e1.record()
+                torch.cuda.synchronize()
+                ms_i += e0.elapsed_time(e1)
+                tt += every
+                if err(i, s_) <= target:
+                    hit = tt
+                    break
+            s_.close()
+            steps.append(hit)
+            total_ms += ms_i
+        out[name] = {"paths": sorted(paths), "reached": sum(h is not None for h in steps),
+                     "device_seconds_all_instances": total_ms / 1e3, "steps_per_instance": steps}
+    bs = out["batched"]["device_seconds_to_all"]
+    out["time_to_target_ratio"] = {k_: out[k_]["device_seconds_all_instances"] / bs for k_ in
+                                   ("alone_generic", "alone_auto")}
+    torch.cuda.empty_cache()
+    return out
+
+
 def planted_cca_truth(model, k):
     """Population top-k solution of the planted CCA model with orthonormal mixing columns
     (Qx, Qy), latent scales s and isotropic noise sigma: Cxx = Qx S^2 Qx^T + sigma^2 I,
@@ -1096,6 +1199,8 @@ def run_native(args):
         forms["batch64_cca_lda_b512_f32"] = measure_batch("f32", 40, 3, dev, seed=rank)
         forms["batch64_cca_lda_b512_bf16"] = measure_batch("bf16", 40, 3, dev, seed=rank)
         forms["warm_start_cca_family"] = measure_warm(dev, seed=rank)
+        if not args.no_tte:
+            forms["batch16_cca_time_to_1e-3"] = measure_batch_tte(dev, seed=rank)
         if not args.no_tte:
             forms["warm_start_c5"] = measure_warm_c5(dev, seed=rank)
 
