@@ -204,7 +204,7 @@ __device__ __forceinline__ void products_phase(cg::cluster_group& cluster, int r
   const float* WA = pca ? Wo : Wc;  // A rows: the other view's projection (CCA, PLS)
   const float* Pm = isY ? Wc : Wo;  // P = X V_x
   const float* Qm = isY ? Wo : Wc;  // Q = Y V_y
-  const int RS = g.rs;               // rows per super-chunk (multiple of 32)
+  const int RS = g.rs;               // rows per super-chunk (multiple of 8)
   const int R4 = RS / 4;
   const int kq = kp >> 2;
   // projection micro-tiles: rows prg + R4*m (m < 4) x players 4*ppq .. 4*ppq+3
@@ -1035,7 +1035,7 @@ size_t smem_bytes(int wp, int kp, int k, int xs, int esz, int rs) {
 }
 
 // Column split (X gets cl_x CTAs of the cluster, Y the rest), padding and the number of
-// minibatch rows a CTA keeps resident (rs, a multiple of 32 chosen to cover the rows one
+// minibatch rows a CTA keeps resident (rs, a multiple of 8 chosen to cover the rows one
 // cluster streams when shared memory allows).
 bool make_plan(const Ctx& c, int CL, int max_clusters, Plan* p) {
   p->CL = CL;
@@ -1059,8 +1059,9 @@ bool make_plan(const Ctx& c, int CL, int max_clusters, Plan* p) {
   p->xs = p->wp + (esz == 4 ? 4 : 8);
   const int nc = std::max(1, std::min(c.num_sms / CL, max_clusters > 0 ? max_clusters : c.num_sms / CL));
   const int64_t rows = (c.cfg.max_b + nc - 1) / nc;
-  int rs = (int)std::min<int64_t>(128, ((rows + 31) / 32) * 32);
-  while (rs > 32 && smem_bytes(p->wp, p->kp, c.k, p->xs, esz, rs) > 227 * 1024) rs -= 32;
+  // resident rows: a multiple of 8 (the micro-tiles need 4), at most 128
+  int rs = (int)std::min<int64_t>(128, ((rows + 7) / 8) * 8);
+  while (rs > 8 && smem_bytes(p->wp, p->kp, c.k, p->xs, esz, rs) > 227 * 1024) rs -= 8;
   p->rs = rs;
   p->smem = smem_bytes(p->wp, p->kp, c.k, p->xs, esz, rs);
   return p->wp <= kMaxW && p->kp <= kMaxKP && p->smem <= 227 * 1024;
