@@ -2,9 +2,9 @@
 
 Default workload: activation-like CCA, d_x = d_y = 16384 (d = 32768), k = 32 players,
 minibatch b = 4096 rows in BF16 (268 MB per minibatch), power-law noise spectrum with 64
-planted shared directions. A pool of 131,072 rows (32 minibatches, 8.6 GB) is generated on
-the device before timing; timed steps stream consecutive minibatches through it, so the
-inputs exceed L2 and every step reads fresh rows from HBM. The other workloads (the
+planted shared directions. A pool of 262,144 rows (64 minibatches, 17.2 GB) is generated on
+the device before timing; timed steps stream consecutive minibatches through it (one launch
+runs up to 64 of them), so the inputs exceed L2 and every step reads fresh rows from HBM. The other workloads (the
 1024-dim FP32 CCA with its time-to-1e-3 runs, the FP32 form of the large problem, the
 batching form, the learned warm start) are reported under `forms`.
 
@@ -39,8 +39,8 @@ WORKLOADS = {
     # name: (synth config function, dtype, pool rows)
     "cca_d1024_k16_b1024_f32": ("config_c2", "f32", 1_000_000),
     "cca_d64_k4_b256_f32": ("config_c1", "f32", 10_000),
-    # activation-like CCA, d_x = d_y = 16384, k = 32, b = 4096, BF16 rows (32 minibatches = 8.6 GB)
-    "cca_d32768_k32_b4096_bf16": ("config_c3", "bf16", 65_536),
+    # activation-like CCA, d_x = d_y = 16384, k = 32, b = 4096, BF16 rows (64 minibatches = 17.2 GB)
+    "cca_d32768_k32_b4096_bf16": ("config_c3", "bf16", 262_144),
     "cca_d32768_k32_b4096_f32": ("config_c3", "f32", 16_384),
 }
 DEFAULT_WORKLOAD = "cca_d32768_k32_b4096_bf16"
@@ -919,7 +919,8 @@ def measure_warm_c5(dev, seed=0, n_train=3000, n_heldout=1096, n_tte=16, train_i
 
 def measure_c3_error(dev, rank, steps=512, eta=1e3, per=16, every=64, rr_every=128, eval_rows=8192):
     """Error against device time on the activation-like workload (d = 32768, k = 32, b = 4096):
-    plain FP32 rows (generic path), BF16 rows (streamed tensor-core steps) and BF16 rows with a
+    plain FP32 rows (tensor-core path, rows split into BF16 pairs), BF16 rows (streamed
+    tensor-core steps) and BF16 rows with a
     Rayleigh-Ritz correction every rr_every steps, from the same random V on the same fresh
     samples (per minibatches drawn at a time, BF16 forms reading the rounded values), the same
     constant step size. Errors: generalized subspace error against the population solution

@@ -218,6 +218,55 @@ def test_tc_stream_multi_step_launch_matches_oracle(dx, k, b, n):
     assert_within(err, n * TC_TOL)
 
 
+
+@pytest.mark.slow
+def test_tc_stream_full_size_64_step_launch_matches_oracle():
+    """The benchmarked launch: 64 steps of the activation-like shape (d_x = d_y = 16384, k = 32,
+    b = 4096, BF16 rows) in one streamed launch, built as the benchmark builds it (no debug
+    copies), against 64 oracle steps on the same BF16 values. Four drawn minibatches are taken
+    in turn (drawing 64 distinct ones on the host takes minutes); the launch reads each step's
+    rows from its own place in device memory either way. Only V and [Bv] are compared, so the
+    chain is held to n times the update's one-step bar (1e-5, the bar V' and [Bv]' keep on the
+    tensor-core path), not the products' 5e-5."""
+    from paper_2206_04993_gb300 import Solver
+    from gpu_util import bf16_round, col_errors, rel
+    from oracle import eg
+    cfg = synth.config_c3()
+    b, k, dx, n, m = 4096, 32, 16384, 64, 4
+    eta, gamma, rho = 0.3, 0.3, 1e-6
+    ops, dev_rows = [], []
+    for j in range(m):
+        X, Y = synth.draw_rows(cfg["model"], b, batch=20 + j, dtype=np.float32)
+        X, Y = bf16_round(X), bf16_round(Y)
+        ops.append(eg.cca_ops(X, Y))
+        dev_rows.append((torch.from_numpy(X).cuda().to(torch.bfloat16), torch.from_numpy(Y).cuda().to(torch.bfloat16)))
+    Xd = torch.empty((n * b, dx), dtype=torch.bfloat16, device="cuda")
+    Yd = torch.empty((n * b, dx), dtype=torch.bfloat16, device="cuda")
+    for t in range(n):
+        Xd[t * b:(t + 1) * b].copy_(dev_rows[t % m][0])
+        Yd[t * b:(t + 1) * b].copy_(dev_rows[t % m][1])
+    del dev_rows
+    V0 = synth.random_unit_columns(2 * dx, k, seed=6).astype(np.float32)
+    S0 = (0.8 * V0 + 0.05 * synth.random_unit_columns(2 * dx, k, seed=7)).astype(np.float32)
+    Vr, Sr = V0.astype(np.float64), S0.astype(np.float64)
+    for t in range(n):
+        Vr, Sr = eg.eg_step(Vr, Sr, *ops[t % m], eta, gamma, rho)
+    with Solver(kind=S.SGEP_CCA, d_x=dx, d_y=dx, k=k, dtype=S.SGEP_BF16, path=S.SGEP_PATH_TC, eta0=eta,
+                gamma0=gamma, rho=rho, max_b=b) as s:
+        s.set_V(V0, S0)
+        l0 = s.launches
+        s.step_many(Xd, Yd, b, n)
+        s.sync()
+        launches = s.launches - l0
+        Vg, Sg = s.V(), s.S()
+    err = {"V": rel(Vg, Vr), "S": rel(Sg, Sr)}
+    err["V_col"], err["V_elem"] = col_errors(Vg, Vr)
+    err["S_col"], err["S_elem"] = col_errors(Sg, Sr)
+    print(launches, err)
+    assert launches <= 2  # the operand of the first step, then the 64 steps in one launch
+    assert np.allclose(np.linalg.norm(Vg, axis=0), 1.0, atol=1e-5)
+    assert_within(err, n * F32_STEP_TOL)
+
 def test_tc_stream_steps_beyond_one_launch_match_single_steps():
     """A chain longer than one launch holds (64 steps) equals the same steps taken one call at
     a time (the same arithmetic; only deferred versus immediate retraction rounds differently)."""
