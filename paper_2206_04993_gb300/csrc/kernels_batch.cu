@@ -81,7 +81,7 @@ __device__ int find_instance(const InstDesc* inst, int n, int phase, int item) {
 }
 
 template <typename T>
-__device__ void run_typed(const InstDesc& I, int phase, int li, float* smem) {
+__device__ __forceinline__ void run_typed(const InstDesc& I, int phase, int li, float* smem) {
   const T* X = static_cast<const T*>(I.X);
   const T* Y = static_cast<const T*>(I.Y);
   const bool lda = I.kind == SGEP_LDA;
@@ -111,7 +111,7 @@ __device__ void run_typed(const InstDesc& I, int phase, int li, float* smem) {
   }
 }
 
-__device__ void run_item(const InstDesc& I, int phase, int li, float* smem) {
+__device__ __forceinline__ void run_item(const InstDesc& I, int phase, int li, float* smem) {
   switch (phase) {
     case 0: {
       if (I.kind == SGEP_LDA && li == I.zero_items) {  // the label counts tile
@@ -154,7 +154,7 @@ __device__ void run_item(const InstDesc& I, int phase, int li, float* smem) {
   }
 }
 
-__device__ void run_phase(const BatchHeader* h, const InstDesc* inst, int phase, float* smem) {
+__device__ __forceinline__ void run_phase(const BatchHeader* h, const InstDesc* inst, int phase, float* smem) {
   const int total = h->total[phase];
   for (int it = blockIdx.x; it < total; it += gridDim.x) {
     const int i = find_instance(inst, h->n, phase, it);
@@ -163,10 +163,30 @@ __device__ void run_phase(const BatchHeader* h, const InstDesc* inst, int phase,
   }
 }
 
+// One launch per phase: one kernel per phase, so each is compiled (registers, spills) for its
+// own tiles only.
+template <int P>
 __global__ void __launch_bounds__(kThreads, 2) k_batch_phase(const BatchHeader* __restrict__ h,
-                                                          const InstDesc* __restrict__ inst, int phase) {
+                                                          const InstDesc* __restrict__ inst) {
   extern __shared__ __align__(16) float smem[];
-  run_phase(h, inst, phase, smem);
+  run_phase(h, inst, P, smem);
+}
+
+template <int P = 0>
+void set_phase_smem(int smem) {
+  if constexpr (P < kPhases) {
+    cudaFuncSetAttribute(k_batch_phase<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    set_phase_smem<P + 1>(smem);
+  }
+}
+
+template <int P = 0>
+void launch_phase(int phase, unsigned grid, size_t smem, cudaStream_t s, const BatchHeader* dh,
+                  const InstDesc* di) {
+  if constexpr (P < kPhases) {
+    if (phase == P) k_batch_phase<P><<<grid, kThreads, smem, s>>>(dh, di);
+    else launch_phase<P + 1>(phase, grid, smem, s, dh, di);
+  }
 }
 
 // Persistent mode: the blocks claim a phase's items one at a time from a counter (monotone
@@ -288,7 +308,7 @@ int batch_create(Ctx** hs, int n, BatchCtx** out) {
   cudaMemset(B->bar, 0, (1 + kPhases) * sizeof(unsigned long long));
   cudaMemset(B->dflag, 0, sizeof(int));
   const size_t smem = (size_t)kSmemFloats * sizeof(float);
-  cudaFuncSetAttribute(k_batch_phase, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  set_phase_smem((int)smem);
   cudaFuncSetAttribute(k_batch_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_persistent, kThreads, smem) != cudaSuccess)
@@ -422,7 +442,7 @@ static int enqueue_step(BatchCtx& B, int j, cudaStream_t s) {
     for (int p = 0; p < kPhases; ++p) {
       if (hd->total[p] == 0) continue;
       const unsigned grid = (unsigned)std::min(hd->total[p], 8 * B.num_sms);
-      k_batch_phase<<<grid, kThreads, smem, s>>>(dh, di, p);
+      launch_phase(p, grid, smem, s, dh, di);
       SGEP_CUDA_TRY(cudaGetLastError());
       ++B.launches;
     }
