@@ -648,9 +648,7 @@ __device__ void project_tile(const T* __restrict__ X, const T* __restrict__ Y, i
     }
   } else if constexpr (std::is_same<T, __nv_bfloat16>::value) {
     // BF16 rows through the ring (16-byte copies, or the aligned value pairs holding a thread's values)
-    const bool isY = by >= nchunk_x;
-    const T* Z = isY ? Y : X;
-    const int64_t ld = isY ? dy : dx;
+    const T* Z = by >= nchunk_x ? Y : X;
     if (!rsx && !rsy && chunk % 8 == 0 && ((uintptr_t)Z & 3) == 0) {
       project_tile_ring<T>(X, Y, n, dx, dy, V, k, chunk, nchunk_x, PQ, bx, by, smem, cz.mean ? &cz : nullptr);
       return;
@@ -772,9 +770,7 @@ __device__ void backproject_tile(const T* __restrict__ X, const T* __restrict__ 
     }
   } else if constexpr (std::is_same<T, __nv_bfloat16>::value) {
     // BF16 rows through the ring (16-byte copies, or the aligned value pairs holding a thread's values)
-    const bool isY = bx >= nblk_x;
-    const T* Z = isY ? Y : X;
-    const int64_t ld = isY ? dy : dx;
+    const T* Z = bx >= nblk_x ? Y : X;
     if (!rsx && !rsy && ((uintptr_t)Z & 3) == 0) {
       backproject_tile_ring<T>(X, Y, b, dx, dy, nA, kind, split, PQ, k, nblk_x, rows_per_split, inv_nA, inv_nB, AV,
                                BV, bx, by, smem, cz.mean ? &cz : nullptr);

@@ -70,6 +70,21 @@ static_assert(kSmemFloats >= gt::kBackprojectSmem && kSmemFloats >= gt::kProject
                   kSmemFloats >= gt::kLdaWSmem,
               "batch workspace");
 
+constexpr int max_update_smem(int k = 1, int m = 0) {
+  return k > gt::kMaxK ? m : max_update_smem(k + 1, gt::cmax(m, gt::update_smem(k)));
+}
+// Shared-memory floats of each phase's tiles: a launch of one phase asks for its own, so the
+// phases with small workspaces keep more blocks resident.
+constexpr int kPhaseSmemFloats[kPhases] = {gt::kLdaCountsSmem,
+                                           gt::lda_stats_smem(kMaxClasses),
+                                           gt::kProjectSmem,
+                                           gt::cmax(gt::kBackprojectSmem, gt::kLdaWSmem),
+                                           gt::kLdaAvSmem,
+                                           gt::gram_smem(gt::kMaxK),
+                                           max_update_smem(),
+                                           0};
+static_assert(gt::gram_smem(gt::kMaxK) >= gt::gram_smem(1), "the k x k terms' workspace grows with k");
+
 __device__ int find_instance(const InstDesc* inst, int n, int phase, int item) {
   int lo = 0, hi = n - 1;  // last instance whose offset <= item
   while (lo < hi) {
@@ -442,7 +457,7 @@ static int enqueue_step(BatchCtx& B, int j, cudaStream_t s) {
     for (int p = 0; p < kPhases; ++p) {
       if (hd->total[p] == 0) continue;
       const unsigned grid = (unsigned)std::min(hd->total[p], 8 * B.num_sms);
-      launch_phase(p, grid, smem, s, dh, di);
+      launch_phase(p, grid, (size_t)kPhaseSmemFloats[p] * sizeof(float), s, dh, di);
       SGEP_CUDA_TRY(cudaGetLastError());
       ++B.launches;
     }
