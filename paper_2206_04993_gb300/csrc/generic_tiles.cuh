@@ -444,8 +444,10 @@ __device__ inline void backproject_tile_ring(const T* __restrict__ X, const T* _
   const bool cca = kind == SGEP_CCA;
   const bool lda = kind == SGEP_LDA;
   const int offA = (kind == SGEP_PCA) ? 0 : cross;
-  const bool wantA = !lda, wantB = cca || lda;
   const bool splitAB = cca && split;
+  // the estimates this tile's rows feed (with split A/B rows, a row split inside one half
+  // feeds one of them: its other weights are not staged and its other sums not reduced)
+  const bool wantA = !lda && (!splitAB || r_begin < nA), wantB = (cca || lda) && (!splitAB || r_end > nA);
   const int kp = (k + 3) & ~3;
   const int nq = kp >> 2;
   const int ot = 16 * nq;           // threads with one (column quad, player quad)
@@ -795,8 +797,9 @@ __device__ void backproject_tile(const T* __restrict__ X, const T* __restrict__ 
   const bool cca = kind == SGEP_CCA;
   const bool lda = kind == SGEP_LDA;
   const int offA = (kind == SGEP_PCA) ? 0 : cross;
-  const bool wantA = !lda, wantB = cca || lda;
   const bool splitAB = cca && split;
+  // the estimates this tile's rows feed (a row split inside one A/B half feeds one of them)
+  const bool wantA = !lda && (!splitAB || r_begin < nA), wantB = (cca || lda) && (!splitAB || r_end > nA);
   const int nq = (k + 3) >> 2;
   const int ot = (kBpCols / 4) * nq;  // threads with one (column quad, player quad)
   const int splits = kThreads / ot;   // row splits
