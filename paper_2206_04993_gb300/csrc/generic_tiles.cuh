@@ -69,7 +69,7 @@ __host__ __device__ constexpr int gram_smem(int k) {
 }
 constexpr int kUpdRows = 4;  // rows per thread per iteration of the update tile
 __host__ __device__ constexpr int update_smem(int k) {
-  return k * k + 4 * k + kUpdRows * (kThreads / k > 1 ? kThreads / k : 1) * k;
+  return k * k + 4 * k + kUpdRows * (kThreads / k > 1 ? kThreads / k : 1) * k + 2 * k * k + k;
 }
 constexpr int kStatsRows = 16;  // rows per cp.async block of the LDA statistics (FP32 rows)
 __host__ __device__ constexpr int lda_stats_smem(int C) { return C * kThreads + kThreads + 2 * kStatsRows * kThreads; }
@@ -953,6 +953,8 @@ __device__ inline void gram_tile(const float* __restrict__ V, const float* __res
         As[o] = xa[u];
         Ss[o] = xs[u];
         Bs[o] = xb[u];
+        // <v_i, B_t v_i>: this thread's rows of player si, summed in registers
+        gb = fmaf(xv[u], b_is_identity ? (1.f + eps_B) * xv[u] : xb[u] + eps_B * xv[u], gb);
       }
     }
     __syncthreads();
@@ -962,15 +964,6 @@ __device__ inline void gram_tile(const float* __restrict__ V, const float* __res
         fma4x4(acc_a, v4, lds4(As + rr * gs + 4 * jq));
         fma4x4(acc_g, v4, lds4(Ss + rr * gs + 4 * jq));
       }
-    }
-    if (tid < k) {
-      float sb = 0.f;
-      for (int rr = 0; rr < nr; ++rr) {
-        const float v = Vs[rr * gs + tid];
-        const float bv = b_is_identity ? (1.f + eps_B) * v : Bs[rr * gs + tid] + eps_B * v;
-        sb = fmaf(v, bv, sb);
-      }
-      gb += sb;
     }
     __syncthreads();
   }
@@ -995,7 +988,7 @@ __device__ inline void gram_tile(const float* __restrict__ V, const float* __res
     }
     __syncthreads();
   }
-  if (tid < k) atomicAdd(&gram[2 * kk + tid], gb);
+  if (si < k) atomicAdd(&gram[2 * kk + si], gb);  // one partial per staging row group
 }
 
 // ---------------------------------------------------------------------------
@@ -1013,11 +1006,12 @@ __device__ inline void update_tile(const float* __restrict__ V, float* __restric
   float* sden = nrm + k;         // k: Alg. 3 denominators
   const int rows = max(1, kThreads / k);
   float* Ss = sden + k;          // kUpdRows * rows x k
-  if (var.z) {
+  float* terms = Ss + kUpdRows * rows * k;  // a | G | b of the step, staged
+  for (int p = threadIdx.x; p < 2 * k * k + k; p += blockDim.x) terms[p] = gram[p];
+  if (var.z)
     for (int j = threadIdx.x; j < k; j += blockDim.x) sden[j] = smooth_den(var.z[j], var.log_rho, var.log_nu);
-    __syncthreads();
-  }
-  eg_coefficients(gram, k, rho, cb, cac, T, var.z ? sden : nullptr);
+  __syncthreads();
+  eg_coefficients(terms, k, rho, cb, cac, T, var.z ? sden : nullptr);
   for (int i = threadIdx.x; i < k; i += blockDim.x) nrm[i] = 0.f;
   __syncthreads();
   const int tid = threadIdx.x;

@@ -84,6 +84,7 @@ constexpr int kPhaseSmemFloats[kPhases] = {gt::kLdaCountsSmem,
                                            max_update_smem(),
                                            0};
 static_assert(gt::gram_smem(gt::kMaxK) >= gt::gram_smem(1), "the k x k terms' workspace grows with k");
+static_assert(kSmemFloats >= max_update_smem(), "the persistent launch holds every phase's workspace");
 
 __device__ int find_instance(const InstDesc* inst, int n, int phase, int item) {
   int lo = 0, hi = n - 1;  // last instance whose offset <= item

@@ -321,6 +321,7 @@ int generic_update(Ctx& c, float eta, float gamma, cudaStream_t s) {
   const int64_t span = (int64_t)rows * gt::kUpdRows;
   const int ublocks = (int)std::min<int64_t>((c.d + span - 1) / span, grid_cap(c, 4));
   const size_t usm = sizeof(float) * gt::update_smem(k);
+  SGEP_CUDA_TRY(smem_optin(k_update, gt::update_smem(k)));
   const UpdVariant var = next_variant(c);
   k_update<<<ublocks, kThreads, usm, s>>>(c.V, c.S, AV, BV, c.gram, c.d, k, eta, gamma, c.cfg.rho,
                                           c.cfg.eps_B, c.b_is_identity ? 1 : 0, c.Vtmp,
@@ -370,6 +371,7 @@ int generic_machines_step(Ctx& c, const void* X, const void* Y, int64_t b, cudaS
   const int ublocks = (int)std::min<int64_t>((c.d + span - 1) / span, grid_cap(c, 4));
   const int gblocks = (int)std::min<int64_t>((c.d + 31) / 32, grid_cap(c, 2));
   const int eblocks = (int)std::min<int64_t>((dk + 255) / 256, grid_cap(c, 4));
+  SGEP_CUDA_TRY(smem_optin(k_update, gt::update_smem(k)));
   for (int m = 0; m < M; ++m) {
     const int64_t r0 = b * m / M, r1 = b * (m + 1) / M;
     const char* xs = (const char*)X + (size_t)r0 * c.d_x * esz;
