@@ -127,6 +127,25 @@ __device__ __forceinline__ void run_typed(const InstDesc& I, int phase, int li, 
   }
 }
 
+// Element type of every instance's rows, fixed at compile time when a batch is uniform (FP32 or
+// BF16 rows: only that type's tiles are compiled into the kernels, which keeps them within their
+// register budget), or kAnyRows: chosen per instance.
+constexpr int kAnyRows = -1;
+
+template <int DT>
+__device__ __forceinline__ void run_rows(const InstDesc& I, int phase, int li, float* smem) {
+  if constexpr (DT == SGEP_F32) {
+    run_typed<float>(I, phase, li, smem);
+  } else if constexpr (DT == SGEP_BF16) {
+    run_typed<__nv_bfloat16>(I, phase, li, smem);
+  } else {
+    if (I.dtype == SGEP_BF16) run_typed<__nv_bfloat16>(I, phase, li, smem);
+    else if (I.dtype == SGEP_FP8E4M3) run_typed<__nv_fp8_e4m3>(I, phase, li, smem);
+    else run_typed<float>(I, phase, li, smem);
+  }
+}
+
+template <int DT>
 __device__ __forceinline__ void run_item(const InstDesc& I, int phase, int li, float* smem) {
   switch (phase) {
     case 0: {
@@ -149,9 +168,7 @@ __device__ __forceinline__ void run_item(const InstDesc& I, int phase, int li, f
     case 1:
     case 2:
     case 3:
-      if (I.dtype == SGEP_BF16) run_typed<__nv_bfloat16>(I, phase, li, smem);
-      else if (I.dtype == SGEP_FP8E4M3) run_typed<__nv_fp8_e4m3>(I, phase, li, smem);
-      else run_typed<float>(I, phase, li, smem);
+      run_rows<DT>(I, phase, li, smem);
       return;
     case 4:
       gt::lda_av_tile(I.lda_M, I.lda_pi, I.lda_W, I.d, I.C, I.k, I.acc, li, I.ldaav_items, smem);
@@ -170,44 +187,49 @@ __device__ __forceinline__ void run_item(const InstDesc& I, int phase, int li, f
   }
 }
 
+template <int DT>
 __device__ __forceinline__ void run_phase(const BatchHeader* h, const InstDesc* inst, int phase, float* smem) {
   const int total = h->total[phase];
   for (int it = blockIdx.x; it < total; it += gridDim.x) {
     const int i = find_instance(inst, h->n, phase, it);
-    run_item(inst[i], phase, it - inst[i].off[phase], smem);
+    run_item<DT>(inst[i], phase, it - inst[i].off[phase], smem);
     __syncthreads();  // the workspace is reused by the next item
   }
 }
 
-// One launch per phase: one kernel per phase, so each is compiled (registers, spills) for its
-// own tiles only.
-template <int P>
+// One launch per phase: one kernel per phase (and, for the phases that read rows, per element
+// type of a uniform batch), so each is compiled (registers, spills) for its own tiles only.
+template <int P, int DT>
 __global__ void __launch_bounds__(kThreads, 2) k_batch_phase(const BatchHeader* __restrict__ h,
                                                           const InstDesc* __restrict__ inst) {
   extern __shared__ __align__(16) float smem[];
-  run_phase(h, inst, P, smem);
+  run_phase<DT>(h, inst, P, smem);
 }
 
-template <int P = 0>
+// only phases 1-3 read rows; the others have one kernel whatever the element type
+constexpr int phase_rows(int P, int DT) { return (P >= 1 && P <= 3) ? DT : kAnyRows; }
+
+template <int DT, int P = 0>
 void set_phase_smem(int smem) {
   if constexpr (P < kPhases) {
-    cudaFuncSetAttribute(k_batch_phase<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    set_phase_smem<P + 1>(smem);
+    cudaFuncSetAttribute(k_batch_phase<P, phase_rows(P, DT)>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    set_phase_smem<DT, P + 1>(smem);
   }
 }
 
-template <int P = 0>
+template <int DT, int P = 0>
 void launch_phase(int phase, unsigned grid, size_t smem, cudaStream_t s, const BatchHeader* dh,
                   const InstDesc* di) {
   if constexpr (P < kPhases) {
-    if (phase == P) k_batch_phase<P><<<grid, kThreads, smem, s>>>(dh, di);
-    else launch_phase<P + 1>(phase, grid, smem, s, dh, di);
+    if (phase == P) k_batch_phase<P, phase_rows(P, DT)><<<grid, kThreads, smem, s>>>(dh, di);
+    else launch_phase<DT, P + 1>(phase, grid, smem, s, dh, di);
   }
 }
 
 // Persistent mode: the blocks claim a phase's items one at a time from a counter (monotone
 // across launches; each block ends a phase with one claim past the last item), so items of
 // uneven cost spread over the blocks as they finish.
+template <int DT>
 __device__ void run_phase_claimed(const BatchHeader* h, const InstDesc* inst, int phase, float* smem,
                                   unsigned long long* work, int* it_s) {
   const int total = h->total[phase];
@@ -218,11 +240,12 @@ __device__ void run_phase_claimed(const BatchHeader* h, const InstDesc* inst, in
     const int it = *it_s;
     if (it >= total) break;
     const int i = find_instance(inst, h->n, phase, it);
-    run_item(inst[i], phase, it - inst[i].off[phase], smem);
+    run_item<DT>(inst[i], phase, it - inst[i].off[phase], smem);
     __syncthreads();  // the workspace and the claimed index are reused by the next item
   }
 }
 
+template <int DT>
 __global__ void __launch_bounds__(kThreads, 2) k_batch_persistent(const BatchHeader* __restrict__ h,
                                                                const InstDesc* __restrict__ inst,
                                                                unsigned long long* bar, int* dflag) {
@@ -231,7 +254,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch_persistent(const BatchHea
   __shared__ int it_s;
   const unsigned long long base = h->bar_base;
   for (int phase = 0; phase < kPhases; ++phase) {
-    run_phase_claimed(h, inst, phase, smem, bar + 1, &it_s);
+    run_phase_claimed<DT>(h, inst, phase, smem, bar + 1, &it_s);
     if (phase + 1 == kPhases) break;
     // bounded grid barrier: arrivals are counted monotonically across launches
     __syncthreads();
@@ -261,6 +284,7 @@ struct BatchTuning {
 struct BatchCtx {
   std::vector<Ctx*> h;
   int n = 0, num_sms = 0, device = 0, max_pers_blocks = 0;
+  int rows_dt = kAnyRows;  // SGEP_F32 or SGEP_BF16 when every instance's rows have that type
   BatchTuning tune;
   int use_graph = 0;
   // pinned descriptor tables (two, alternating) and their device copies
@@ -323,12 +347,27 @@ int batch_create(Ctx** hs, int n, BatchCtx** out) {
   }
   cudaMemset(B->bar, 0, (1 + kPhases) * sizeof(unsigned long long));
   cudaMemset(B->dflag, 0, sizeof(int));
+  B->rows_dt = hs[0]->cfg.dtype;
+  for (int i = 1; i < n; ++i)
+    if (hs[i]->cfg.dtype != B->rows_dt) B->rows_dt = kAnyRows;
+  if (B->rows_dt != SGEP_F32 && B->rows_dt != SGEP_BF16) B->rows_dt = kAnyRows;
   const size_t smem = (size_t)kSmemFloats * sizeof(float);
-  set_phase_smem((int)smem);
-  cudaFuncSetAttribute(k_batch_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_persistent, kThreads, smem) != cudaSuccess)
-    per_sm = 1;
+  cudaError_t occ;
+  if (B->rows_dt == SGEP_F32) {
+    set_phase_smem<SGEP_F32>((int)smem);
+    cudaFuncSetAttribute(k_batch_persistent<SGEP_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    occ = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_persistent<SGEP_F32>, kThreads, smem);
+  } else if (B->rows_dt == SGEP_BF16) {
+    set_phase_smem<SGEP_BF16>((int)smem);
+    cudaFuncSetAttribute(k_batch_persistent<SGEP_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    occ = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_persistent<SGEP_BF16>, kThreads, smem);
+  } else {
+    set_phase_smem<kAnyRows>((int)smem);
+    cudaFuncSetAttribute(k_batch_persistent<kAnyRows>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    occ = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_persistent<kAnyRows>, kThreads, smem);
+  }
+  if (occ != cudaSuccess) per_sm = 1;
   cudaGetLastError();
   B->max_pers_blocks = std::max(1, per_sm);
   B->tune.blocks_per_sm = std::min(2, B->max_pers_blocks);
@@ -452,13 +491,21 @@ static int enqueue_step(BatchCtx& B, int j, cudaStream_t s) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    SGEP_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_batch_persistent, dh, di, B.bar, B.dflag));
+    if (B.rows_dt == SGEP_F32)
+      SGEP_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_batch_persistent<SGEP_F32>, dh, di, B.bar, B.dflag));
+    else if (B.rows_dt == SGEP_BF16)
+      SGEP_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_batch_persistent<SGEP_BF16>, dh, di, B.bar, B.dflag));
+    else
+      SGEP_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_batch_persistent<kAnyRows>, dh, di, B.bar, B.dflag));
     ++B.launches;
   } else {
     for (int p = 0; p < kPhases; ++p) {
       if (hd->total[p] == 0) continue;
       const unsigned grid = (unsigned)std::min(hd->total[p], 8 * B.num_sms);
-      launch_phase(p, grid, (size_t)kPhaseSmemFloats[p] * sizeof(float), s, dh, di);
+      const size_t psm = (size_t)kPhaseSmemFloats[p] * sizeof(float);
+      if (B.rows_dt == SGEP_F32) launch_phase<SGEP_F32>(p, grid, psm, s, dh, di);
+      else if (B.rows_dt == SGEP_BF16) launch_phase<SGEP_BF16>(p, grid, psm, s, dh, di);
+      else launch_phase<kAnyRows>(p, grid, psm, s, dh, di);
       SGEP_CUDA_TRY(cudaGetLastError());
       ++B.launches;
     }
