@@ -1238,7 +1238,7 @@ int ms_launch(Ctx& c, const MsArgs& a, int NC, cudaStream_t s) {
   cfg.numAttrs = c.cl_ms_coop ? 2 : 1;
   cudaError_t e = cudaLaunchKernelEx(&cfg, k_cluster_steps<T, CLT>, a);
   if (e != cudaSuccess && c.cl_ms_coop) {
-    // the driver refused the cooperative attribute with clusters: the grid never exceeds the
+    // the CUDA driver refused the cooperative attribute with clusters: the grid never exceeds the
     // co-resident clusters and every wait is bounded, so launch without it
     cudaGetLastError();
     c.cl_ms_coop = 0;

@@ -85,7 +85,7 @@ int make_map_f32(CUtensorMap* map, const void* base, int64_t rows, int64_t cols,
 // 3-D view of a BF16 row-major matrix [rows][cols] (row stride `ld` elements) as (64 columns,
 // rows, cols / 64 column groups): one box of box_rows rows x `groups` groups lands as `groups`
 // consecutive [box_rows][64] sub-boxes with 128-byte swizzle, the layout of that many 2-D boxes
-// of 64 columns, in one copy. Returns SGEP_ECUDA when the driver does not take the view.
+// of 64 columns, in one copy. Returns SGEP_ECUDA when the CUDA driver does not take the view.
 int make_map_bf16_groups(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows,
                          int groups) {
   auto fn = encode_fn();

@@ -1372,7 +1372,7 @@ int tc_stream_steps(Ctx& c, const void* X, const void* Y, int64_t b, int nsteps,
   int rc = make_map_bf16(&mX, X, rows, c.d_x, c.d_x, 128, 64);
   if (!rc) rc = make_map_bf16(&mY, Y, rows, c.d_y, c.d_y, 128, 64);
   // the back-projection's 64-row steps: one copy of 64 rows x 256 columns through a 3-D view
-  // where the driver takes it (SGEP_TC_BP_GROUPS=0 keeps four 2-D boxes per step)
+  // where the CUDA driver takes it (SGEP_TC_BP_GROUPS=0 keeps four 2-D boxes per step)
   const char* bg = getenv("SGEP_TC_BP_GROUPS");
   int bp_groups = !(bg && bg[0] == '0') && make_map_bf16_groups(&mX64, X, rows, c.d_x, c.d_x, 64, 4) == SGEP_OK &&
                   make_map_bf16_groups(&mY64, Y, rows, c.d_y, c.d_y, 64, 4) == SGEP_OK;
