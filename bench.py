@@ -728,6 +728,10 @@ def measure_batch_tte(dev, seed=0, n=16, b=512, nmb=32, max_steps=60_000, every=
     ms, t = 0.0, 0
     with Batch(ss) as bt:
         bt.configure(use_graph=1)
+        # the launch mode and partition the autotuner picks (it restores every instance's state)
+        out["autotuned"] = dict(zip(["mode", "blocks_per_sm", "chunk_cap", "rows_cap", "use_graph"],
+                                    bt.autotune([X[:b] for X, _ in pools], [Y[:b] for _, Y in pools], [b] * n,
+                                                reps=3)))
         while t < max_steps and any(r is None for r in reached):
             e0.record()
             for u in range(t, t + every):
